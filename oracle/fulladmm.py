@@ -1,0 +1,162 @@
+"""NRTO-FullADMM inner loop (oracle; test infrastructure only).
+
+Sec. IV ("NRTO-FullADMM Framework"), Algorithm 1 and Supplementary Sec. III.
+
+Problem (12): min Q_û(δû) + Q̃(k_v)  s.t.  g^{lin,1}(δû, p) ≤ 0,  ‖F_u δû‖ ≤ r,
+‖ν_j‖ ≤ p̃_j,  p = p̃,  Â_j k_v + b̂_j = ν_j,
+solved by scaled ADMM with block 1 = (ν, p̃) and block 2 = (δû, p, k_v).
+
+Reading used for the Block-2 (δû, p) update (the paper solves it with Jacobi-PCG, which
+cannot carry inequality constraints): the two inequality sets of (12a) are moved into
+block 1 with slack variables,
+    g_j(x̂) + b_jᵀ δû + p_j + w_j = 0,  w ≥ 0          (scaled dual λ_w)
+    F_u δû = e,  ‖e‖ ≤ r                             (scaled dual λ_e)
+so block 1 also projects w onto the orthant and e onto the ball, and block 2 becomes an
+unconstrained quadratic in (δû, p) whose Hessian is fixed per outer step.  The fixed
+point is the same Problem (12) optimum.  The k_v update uses the direct form
+k_v = M ρ Σ_j Â_jᵀ(ν_j - b̂_j - λ_ν,j), M = (Q_v + ρ Σ_j Â_jᵀÂ_j)^{-1}, which equals the
+paper's q + 𝓜 k_v^{prev} + 𝓜̄ ν under the dual invariant it assumes (zero initialization).
+
+The cost Q_û(δû) = Σ_k (û_k+δû_k-u_ref)ᵀ R_u (·) is extended with the state-tracking term
+Σ_{t=1}^T (x̂_t+δx_t-x_goal)ᵀ Q_x (·), δx = F_u δû.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import problem as P
+from . import soc
+
+
+@dataclass
+class FullADMMOptions:
+    rho: float = 10.0
+    r_trust: float = 2.0
+    eps_p: float = 1e-4
+    eps_d: float = 1e-4
+    max_iter: int = 500
+    check: bool = True          # stop at the first iteration meeting both tolerances
+
+
+@dataclass
+class FullADMMState:
+    K: np.ndarray
+    du: np.ndarray
+    dx: np.ndarray
+    p: np.ndarray
+    pt: np.ndarray
+    lam_p: np.ndarray
+    lam_nu: np.ndarray
+    w: np.ndarray
+    lam_w: np.ndarray
+    e: np.ndarray
+    lam_e: np.ndarray
+    nu: np.ndarray = None
+    iters: int = 0
+    r_p: float = np.inf
+    r_d: float = np.inf
+    r_p_paper: float = np.inf
+    r_d_paper: float = np.inf
+    converged: bool = False
+    history: list = field(default_factory=list)
+
+
+def zero_state(lin) -> FullADMMState:
+    """Algorithm 1 initialization: λ_p, λ_ν, k_v, p ← 0 (and δû, w, λ_w, e, λ_e ← 0)."""
+    n_g, T, nu = lin.bvec.shape
+    nx = lin.Psi.shape[1]
+    return FullADMMState(
+        K=np.zeros((T, nu, nx)), du=np.zeros((T, nu)), dx=np.zeros((T + 1, nx)),
+        p=np.zeros(n_g), pt=np.zeros(n_g), lam_p=np.zeros(n_g),
+        lam_nu=np.zeros((n_g, T + 1, nx)), w=np.zeros(n_g), lam_w=np.zeros(n_g),
+        e=np.zeros((T, nx)), lam_e=np.zeros((T, nx)))
+
+
+def warm_state(lin, K0, pt0, lam_p0) -> FullADMMState:
+    """Warm start from a predicted (K, p̃, λ_p): k_v^0 = K0, p^0 = p̃0, λ_p^0 = λ_p0, λ_ν = 0."""
+    s = zero_state(lin)
+    s.K = np.array(K0, dtype=np.float64)
+    s.p = np.array(pt0, dtype=np.float64)
+    s.pt = np.array(pt0, dtype=np.float64)
+    s.lam_p = np.array(lam_p0, dtype=np.float64)
+    return s
+
+
+def block2_matrices(inst, lin, rho):
+    """Hessian of the Block-2 (δû) quadratic after eliminating p (fixed per outer step):
+    2R̄ + F̃ᵀ(2Q̄ + ρI)F̃ + (ρ/2) Σ_j b_j b_jᵀ, F̃ = rows t = 1..T of F_u."""
+    T, nu, nx = inst.T, inst.nu, inst.nx
+    Ft = lin.Fu[nx:, :]
+    Rbar = np.diag(np.tile(inst.Ru, T))
+    Qbar = np.diag(np.tile(inst.Qx, T))
+    Bm = lin.bvec.reshape(lin.bvec.shape[0], T * nu)
+    H = 2.0 * Rbar + Ft.T @ (2.0 * Qbar + rho * np.eye(T * nx)) @ Ft + 0.5 * rho * Bm.T @ Bm
+    return H, Ft, Rbar, Qbar, Bm
+
+
+def block2_solve(inst, lin, rho, mats, pt, lam_p, w, lam_w, e, lam_e):
+    """Block-2 (δû, p) update: argmin_{δû,p} Q_û(δû) + ρ/2‖p - p̃ + λ_p‖²
+    + ρ/2‖g + b_jᵀδû + p + w + λ_w‖² + ρ/2‖F̃δû - e + λ_e‖².
+    p_j is eliminated in closed form, p_j = ½[(p̃_j - λ_p,j) - (g_j + b_jᵀδû + w_j + λ_w,j)],
+    which leaves (ρ/4)(b_jᵀδû + d_j)² with d_j = p̃_j - λ_p,j + g_j + w_j + λ_w,j."""
+    H, Ft, Rbar, Qbar, Bm = mats
+    T, nu, nx = inst.T, inst.nu, inst.nx
+    d = pt - lam_p + lin.g0 + w + lam_w
+    xdev = (lin.x_hat[1:] - inst.x_goal[None, :]).reshape(-1)
+    udev = (lin.u_hat - inst.u_ref[None, :]).reshape(-1)
+    grad = 2.0 * Rbar @ udev + Ft.T @ (2.0 * Qbar @ xdev - rho * (e - lam_e).reshape(-1)) + 0.5 * rho * Bm.T @ d
+    du = -np.linalg.solve(H, grad).reshape(T, nu)
+    dx = P.delta_x(lin, du)
+    l = P.ell(lin, du)
+    p = 0.5 * ((pt - lam_p) - (lin.g0 + l + w + lam_w))
+    return du, dx, p
+
+
+def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None,
+            n_iter: int | None = None) -> FullADMMState:
+    """Run Algorithm 1 for up to n_iter (default opts.max_iter) iterations."""
+    rho = opts.rho
+    s = zero_state(lin) if state is None else state
+    H = P.gain_hessian_blocks(lin, inst, coef=rho)
+    mats = block2_matrices(inst, lin, rho)
+    L = opts.max_iter if n_iter is None else n_iter
+    Y_prev = P.Ahat_apply(lin, s.K) + lin.bhat
+    for it in range(1, L + 1):
+        # Block 1 (13): per-row SOC projection of (Â_j k + b̂_j + λ_ν,j, p_j + λ_p,j);
+        # lifted slacks: orthant for w, ball for e.
+        Y = Y_prev
+        pt_new, nu = soc.project_rows(s.p + s.lam_p, Y + s.lam_nu)
+        l_prev = P.ell(lin, s.du)
+        w = np.maximum(0.0, -(lin.g0 + l_prev + s.p + s.lam_w))
+        e = soc.project_ball((s.dx[1:] + s.lam_e).reshape(-1), opts.r_trust).reshape(s.e.shape)
+        # Block 2b (14b), direct form: k = M ρ Σ_j Â_jᵀ(ν_j - b̂_j - λ_ν,j).
+        K_new = P.gain_solve(H, rho * P.Ahat_T_apply(lin, nu - lin.bhat - s.lam_nu))
+        # Block 2a (14a): (δû, p).
+        du, dx, p = block2_solve(inst, lin, rho, mats, pt_new, s.lam_p, w, s.lam_w, e, s.lam_e)
+        l_new = P.ell(lin, du)
+        Y_new = P.Ahat_apply(lin, K_new) + lin.bhat
+        # Dual updates (15) plus the lifted couplings.
+        lam_p = s.lam_p + (p - pt_new)
+        lam_nu = s.lam_nu + (Y_new - nu)
+        lam_w = s.lam_w + (lin.g0 + l_new + p + w)
+        lam_e = s.lam_e + (dx[1:] - e)
+        # Residuals: every coupling (primal) and the block-2 change mapped through the
+        # couplings (dual); the paper's r_p = ‖p - p̃‖, r_d = ρ‖Δp̃‖ are kept alongside.
+        r_p = np.sqrt(np.sum((p - pt_new) ** 2) + np.sum((Y_new - nu) ** 2)
+                      + np.sum((lin.g0 + l_new + p + w) ** 2) + np.sum((dx[1:] - e) ** 2))
+        dp = p - s.p
+        r_d = rho * np.sqrt(np.sum(dp ** 2) + np.sum((Y_new - Y) ** 2)
+                            + np.sum((l_new - l_prev + dp) ** 2) + np.sum((dx - s.dx) ** 2))
+        r_p_paper = float(np.linalg.norm(p - pt_new))
+        r_d_paper = float(rho * np.linalg.norm(pt_new - s.pt))
+        s = FullADMMState(K=K_new, du=du, dx=dx, p=p, pt=pt_new, lam_p=lam_p, lam_nu=lam_nu,
+                          w=w, lam_w=lam_w, e=e, lam_e=lam_e, nu=nu, iters=s.iters + 1,
+                          r_p=float(r_p), r_d=float(r_d), r_p_paper=r_p_paper, r_d_paper=r_d_paper,
+                          history=s.history + [(float(r_p), float(r_d))])
+        Y_prev = Y_new
+        if opts.check and r_p <= opts.eps_p and r_d <= opts.eps_d:
+            s.converged = True
+            break
+    return s

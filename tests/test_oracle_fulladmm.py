@@ -1,0 +1,163 @@
+"""Pins for the oracle's NRTO-FullADMM loop (Sec. IV, Algorithm 1, Supplementary Sec. III)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fulladmm as F, models, problem as P
+from paper_2603_02642_b300 import workloads as W
+
+from . import ipsolver
+
+RNG = np.random.default_rng(5)
+
+
+def tiny_unicycle(T=6, tau=1.0):
+    inst = W.unicycle(0, T=T, n_obs=1)
+    inst.obs_center = np.array([[0.75, 0.55]])
+    inst.obs_radius = np.array([0.3])
+    inst.u_init = np.tile([1.0, 0.0], (T, 1))
+    inst.tau = tau
+    return inst
+
+
+def problem2_ip(inst, lin, r):
+    """Problem 2 (with the tracking term) as a dense SOCP for the barrier solver."""
+    T, nu, nx = inst.T, inst.nu, inst.nx
+    n1, n2, ng = T * nu, T * nu * nx, lin.g0.shape[0]
+    n = n1 + n2 + ng
+    H, Ft, Rbar, Qbar, Bm = F.block2_matrices(inst, lin, 0.0)
+    Pm = np.zeros((n, n))
+    Pm[:n1, :n1] = H
+    Pm[n1:n1 + n2, n1:n1 + n2] = 2 * np.kron(np.eye(T * nx), np.diag(inst.RK ** 2))
+    q = np.zeros(n)
+    xdev = (lin.x_hat[1:] - inst.x_goal).reshape(-1)
+    udev = (lin.u_hat - inst.u_ref).reshape(-1)
+    q[:n1] = 2 * Rbar @ udev + 2 * Ft.T @ Qbar @ xdev
+    socs = []
+    for j in range(ng):
+        A = np.zeros(((T + 1) * nx, n))
+        A[:, n1:n1 + n2] = P.dense_Ahat(lin, j)
+        c = np.zeros(n)
+        c[n1 + n2 + j] = 1.0
+        socs.append((A, lin.bhat[j].reshape(-1), c, 0.0))
+    At = np.zeros((Ft.shape[0], n))
+    At[:, :n1] = Ft
+    socs.append((At, np.zeros(Ft.shape[0]), np.zeros(n), r))
+    G = np.zeros((ng, n))
+    G[:, :n1] = Bm
+    G[:, n1 + n2:] = np.eye(ng)
+    h = -lin.g0
+    x0 = np.zeros(n)
+    x0[n1 + n2:] = np.linalg.norm(lin.bhat.reshape(ng, -1), axis=1) + 1e-3
+    x = ipsolver.solve(Pm, q, socs, G, h, x0)
+    return x[:n1].reshape(T, nu), P.K_from_kv(x[n1:n1 + n2], T, nu, nx)
+
+
+def test_fixed_point_matches_interior_point():
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    du_ip, K_ip = problem2_ip(inst, lin, r=0.5)
+    s = F.iterate(inst, lin, F.FullADMMOptions(rho=10.0, r_trust=0.5, eps_p=1e-9, eps_d=1e-9, max_iter=30000))
+    assert s.converged
+    assert np.allclose(s.du, du_ip, atol=2e-6)
+    assert np.allclose(s.K, K_ip, atol=2e-6)
+    # The solution touches constraints (otherwise the pin would be weak).
+    act = lin.g0 + P.ell(lin, s.du) + s.p
+    assert np.max(act) > -1e-6
+
+
+def test_block2_stationarity_by_autograd():
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    rho = 7.0
+    ng, T = lin.g0.shape[0], inst.T
+    pt, lam_p, w, lam_w = RNG.normal(size=ng), RNG.normal(size=ng), np.abs(RNG.normal(size=ng)), RNG.normal(size=ng)
+    e, lam_e = RNG.normal(size=(T, inst.nx)), RNG.normal(size=(T, inst.nx))
+    mats = F.block2_matrices(inst, lin, rho)
+    du, dx, p = F.block2_solve(inst, lin, rho, mats, pt, lam_p, w, lam_w, e, lam_e)
+    t = lambda a: torch.tensor(a, dtype=torch.float64)
+    du_t = t(du).requires_grad_(True)
+    p_t = t(p).requires_grad_(True)
+    Fu = t(lin.Fu)
+    dxv = (Fu @ du_t.reshape(-1)).reshape(T + 1, inst.nx)
+    ubar = t(lin.u_hat) + du_t - t(inst.u_ref)
+    xbar = t(lin.x_hat[1:]) + dxv[1:] - t(inst.x_goal)
+    ellv = torch.einsum("jku,ku->j", t(lin.bvec), du_t)
+    obj = (torch.sum(ubar * ubar * t(inst.Ru)) + torch.sum(xbar * xbar * t(inst.Qx))
+           + rho / 2 * torch.sum((p_t - t(pt) + t(lam_p)) ** 2)
+           + rho / 2 * torch.sum((t(lin.g0) + ellv + p_t + t(w) + t(lam_w)) ** 2)
+           + rho / 2 * torch.sum((dxv[1:] - t(e) + t(lam_e)) ** 2))
+    gdu, gp = torch.autograd.grad(obj, [du_t, p_t])
+    assert gdu.abs().max().item() < 1e-9 and gp.abs().max().item() < 1e-9
+
+
+def test_direct_form_equals_paper_closed_form_under_zero_init():
+    """k^l = q + 𝓜 k^{l-1} + 𝓜̄ ν^l (Supplementary Sec. III) vs the direct form used by the loop."""
+    inst = tiny_unicycle(T=4)
+    lin = P.linearize(inst, inst.u_init)
+    rho = 10.0
+    T, nu, nx = inst.T, inst.nu, inst.nx
+    ng = lin.g0.shape[0]
+    Ad = [P.dense_Ahat(lin, j) for j in range(ng)]
+    Qv = 2 * np.kron(np.eye(T * nx), np.diag(inst.RK ** 2))
+    M = np.linalg.inv(Qv + rho * sum(a.T @ a for a in Ad))
+    q = -rho * M @ sum(a.T @ lin.bhat[j].reshape(-1) for j, a in enumerate(Ad))
+    opts = F.FullADMMOptions(rho=rho, r_trust=0.5, check=False)
+    s = F.zero_state(lin)
+    for _ in range(8):
+        k_prev = P.kv_from_K(s.K)
+        s = F.iterate(inst, lin, opts, s, n_iter=1)
+        k_cf = q + M @ Qv @ k_prev + sum(rho * M @ a.T @ s.nu[j].reshape(-1) for j, a in enumerate(Ad))
+        assert np.allclose(k_cf, P.kv_from_K(s.K), atol=1e-11)
+        # The invariant Σ_j ρ Â_jᵀ λ_ν,j + Q_v k = 0 holds at every iterate.
+        inv = rho * sum(a.T @ s.lam_nu[j].reshape(-1) for j, a in enumerate(Ad)) + Qv @ P.kv_from_K(s.K)
+        assert np.abs(inv).max() < 1e-10
+
+
+def test_no_constraints_reduces_to_lqr_tracking():
+    """n_g = 0, trust radius inactive: K = 0 and δû is the finite-horizon LQ tracking
+    solution, computed here by an independent backward Riccati recursion."""
+    inst = W.quadcopter(1, T=8, n_obs=0)
+    inst.u_lo = np.full(4, -np.inf)
+    inst.u_hi = np.full(4, np.inf)
+    u = inst.u_init + 0.05 * RNG.normal(size=inst.u_init.shape)
+    lin = P.linearize(inst, u)
+    assert lin.g0.shape[0] == 0
+    s = F.iterate(inst, lin, F.FullADMMOptions(rho=1.0, r_trust=1e6, eps_p=1e-12, eps_d=1e-12, max_iter=2000))
+    assert np.abs(s.K).max() == 0.0
+    T, nx, nu = inst.T, inst.nx, inst.nu
+    Q = 2 * np.diag(inst.Qx)
+    R = 2 * np.diag(inst.Ru)
+    qv = [Q @ (lin.x_hat[t] - inst.x_goal) for t in range(T + 1)]
+    rv = [R @ (lin.u_hat[k] - inst.u_ref) for k in range(T)]
+    Pn, pn = Q.copy(), qv[T].copy()
+    Ks, ks = [None] * T, [None] * T
+    for k in range(T - 1, -1, -1):
+        A, B = lin.A[k], lin.B[k]
+        Huu = R + B.T @ Pn @ B
+        Hux = B.T @ Pn @ A
+        hu = rv[k] + B.T @ pn
+        Ks[k] = -np.linalg.solve(Huu, Hux)
+        ks[k] = -np.linalg.solve(Huu, hu)
+        Qk = Q if k > 0 else np.zeros_like(Q)
+        qk = qv[k] if k > 0 else np.zeros(nx)
+        Pn = Qk + A.T @ Pn @ A + Hux.T @ Ks[k]
+        pn = qk + A.T @ pn + Hux.T @ ks[k]
+    dx = np.zeros(nx)
+    du = np.zeros((T, nu))
+    for k in range(T):
+        du[k] = Ks[k] @ dx + ks[k]
+        dx = lin.A[k] @ dx + lin.B[k] @ du[k]
+    assert np.allclose(s.du, du, atol=1e-8)
+
+
+def test_iterates_are_deterministic_and_warm_start_shapes():
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    o = F.FullADMMOptions(check=False)
+    a = F.iterate(inst, lin, o, n_iter=5)
+    b = F.iterate(inst, lin, o, n_iter=5)
+    assert np.array_equal(a.K, b.K) and np.array_equal(a.lam_nu, b.lam_nu)
+    ws = F.warm_state(lin, a.K, a.pt, a.lam_p)
+    c = F.iterate(inst, lin, o, ws, n_iter=1)
+    assert c.iters == 1 and np.isfinite(c.r_p)

@@ -1,0 +1,30 @@
+"""Checks of the oracle's successive-linearization loop against its stated definition
+(parity unpinned against the paper: the acceptance constants come from prior work)."""
+import numpy as np
+
+from oracle import fulladmm as F, outer as O, problem as P
+
+from .test_oracle_fulladmm import tiny_unicycle
+
+
+def test_cost_definition():
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    K = np.ones((inst.T, inst.nu, inst.nx))
+    c = O.cost(inst, lin, K)
+    ud = inst.u_init - inst.u_ref
+    xd = lin.x_hat[1:] - inst.x_goal
+    expect = (ud * ud * inst.Ru).sum() + (xd * xd * inst.Qx).sum() + inst.T * inst.nx * (inst.RK ** 2).sum()
+    assert np.isclose(c, expect)
+
+
+def test_accepted_steps_decrease_merit_and_radius_schedule():
+    inst = tiny_unicycle()
+    res = O.solve(inst, O.OuterOptions(n_outer=5), F.FullADMMOptions(max_iter=400))
+    assert len(res.accepted) == 5
+    for i in range(1, 5):
+        r_prev, r = res.radii[i - 1], res.radii[i]
+        expect = min(1.5 * r_prev, 2.0) if res.accepted[i - 1] else max(0.8 * r_prev, 1e-3)
+        assert np.isclose(r, expect)
+    lin0 = P.linearize(inst, inst.u_init)
+    assert res.phi <= O.merit(inst, lin0, np.zeros((inst.T, inst.nu, inst.nx)), 10.0)
