@@ -1,0 +1,194 @@
+/*
+ * libnrto — the data-parallel inner loop of Nonlinear Robust Trajectory Optimization (NRTO) on
+ * NVIDIA B300 (sm_103a): NRTO-FullADMM and NRTO-DR iterations for batches of robust trajectory
+ * problems, with the successive-linearization outer step around them.
+ *
+ * Method: arXiv 2603.02642 ("cuNRTO").  Problem 1 (Sec. II-A) is the robust trajectory problem;
+ * Problem 2 (Sec. II-B) its linearization with second-order-cone rows ‖Â_j k_v + b̂_j‖ ≤ p_j
+ * (Supplementary Sec. I); the inner solvers are NRTO-DR (Sec. III, Supplementary Sec. II) and
+ * NRTO-FullADMM (Sec. IV, Algorithm 1, Supplementary Sec. III).
+ *
+ * Conventions
+ *  - All pointers passed to the functions below are HOST pointers unless stated otherwise.
+ *    Input arrays are read during the call and not retained; the caller keeps ownership.
+ *  - Arrays are row-major float64.  Per-instance arrays of a batch are concatenated in instance order.
+ *  - Gains: K_k is nu×nx, stored row-major per step (k = 0..T-1); the paper's k_v is the
+ *    column-wise vec of the K_k, stacked.
+ *  - Row order of the robust constraints (index j): state rows for t = 1..T — for each t the sphere
+ *    clearance rows (unicycle/quadcopter: obstacle o; arm: link sphere l major, static sphere o minor),
+ *    then state-bound rows (state i ascending, upper before lower, finite bounds only); then control
+ *    rows for k = 0..T-1 (input i ascending, upper before lower, finite bounds only).
+ *  - Ragged row layout (λ_ν, b̂_j): a state row at time t has (t+1)·nx entries (ζ-blocks 0..t); a
+ *    control row at step k has nx entries (ζ-block k).
+ *  - Every call is asynchronous on the problem's stream unless it copies results to host memory, in
+ *    which case it synchronizes that stream.  Functions return a status; C++ exceptions never cross
+ *    the ABI; nrto_last_error() gives the message of the last failure on the calling thread.
+ *  - Device loops are bounded (max_inner / max_dr); a solve never waits unboundedly.
+ */
+#ifndef NRTO_H
+#define NRTO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NRTO_ABI_VERSION 1
+
+typedef enum {
+  NRTO_OK = 0,
+  NRTO_ERR_INVALID = 1,        /* bad argument or descriptor (nothing was changed)            */
+  NRTO_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed                  */
+  NRTO_ERR_NOT_CONVERGED = 3,  /* some instance stopped at its iteration cap                  */
+  NRTO_ERR_NUMERIC = 4,        /* non-finite input, or a non-finite residual in some instance */
+  NRTO_ERR_TIMEOUT = 5,        /* reserved                                                    */
+  NRTO_ERR_STATE = 6           /* call order violated (e.g. solve before linearize)           */
+} nrto_status;
+
+typedef enum { NRTO_DYN_UNICYCLE = 0, NRTO_DYN_QUADCOPTER = 1, NRTO_DYN_ARM = 2 } nrto_dyn_kind;
+typedef enum { NRTO_SOLVER_DR = 0, NRTO_SOLVER_FULLADMM = 1 } nrto_solver_kind;
+typedef enum { NRTO_PREC_FP64 = 0, NRTO_PREC_MIXED = 1 } nrto_precision;
+
+/* One instance of Problem 1 (Sec. II-A).  Dimensions must match the model:
+ * unicycle (3,2), quadcopter (12,4), arm (14,7).  ±INFINITY marks an absent bound. */
+typedef struct {
+  int dyn;                       /* nrto_dyn_kind                                              */
+  int nx, nu, T;                 /* state dim, input dim, horizon (1 <= T <= 256/160/128)     */
+  double dt;                     /* forward-Euler step (> 0)                                   */
+  const double* dyn_params;      /* quadcopter [m, g, Jx, Jy, Jz]; arm DH (a,d,α)×7; unicycle none */
+  int n_dyn_params;
+  const double* x0;              /* nx    nominal initial state x̄_0                            */
+  const double* x_goal;          /* nx    goal of the state-tracking cost                       */
+  const double* u_init;          /* T*nu  initial nominal controls û                            */
+  const double* u_ref;           /* nu    reference of the input cost                           */
+  const double* Sigma;           /* (T+1)*nx*nx  blocks Σ_i = S_i^{-1} (Γ = I, S block diagonal) */
+  double tau;                    /* ellipsoid radius τ >= 0                                     */
+  const double* Qx;              /* nx    diagonal state-tracking weight                        */
+  const double* Ru;              /* nu    diagonal input weight R_u (> 0)                       */
+  const double* RK;              /* nu    diagonal gain weight R_K (> 0)                        */
+  int n_obs, obs_dim;            /* spheres; obs_dim 2 (unicycle) or 3                          */
+  const double* obs_center;      /* n_obs*obs_dim                                               */
+  const double* obs_radius;      /* n_obs                                                       */
+  int n_link;                    /* arm only: link spheres                                      */
+  const double* link_spheres;    /* n_link*5: link index 1..7, offset x,y,z, radius             */
+  const double* u_lo; const double* u_hi;   /* nu                                              */
+  const double* x_lo; const double* x_hi;   /* nx                                              */
+} nrto_problem_desc;
+
+typedef struct {
+  int solver;          /* nrto_solver_kind                                                      */
+  double rho;          /* FullADMM penalty ρ (scaled duals); NRTO-DR: ADMM penalty of Problem 3  */
+  double alpha;        /* DR relaxation α ∈ (0,1)                                                */
+  double r_chi, sigma; /* DR proximal scalings R_χ = r_χ I, R_s = σ I                            */
+  double eps_p, eps_d; /* inner stopping tolerances on the full primal / dual residuals         */
+  double eps_dr;       /* DR stopping tolerance on ‖s̃^l - s̃^{l-1}‖                               */
+  int max_inner;       /* FullADMM iterations / NRTO-DR ADMM iterations cap                      */
+  int max_dr;          /* DR iterations cap per ADMM iteration                                   */
+  int check;           /* 1: stop at tolerance; 0: run exactly max_inner iterations             */
+  double r0, r_min, w_p;  /* outer loop: initial/max trust radius, minimum radius, merit weight   */
+} nrto_solver_opts;
+
+/* Per-instance sizes, for sizing output buffers. */
+typedef struct {
+  int nx, nu, T, n_rows, n_state_rows, n_control_rows;
+  long long n_entries;           /* ragged row entries (state + control rows)                  */
+  long long n_entries_state;
+} nrto_instance_info;
+
+/* Outputs of an inner solve; every pointer may be NULL (skipped).  Host buffers, concatenated
+ * over instances with the sizes of nrto_instance_info. */
+typedef struct {
+  double* du;          /* Σ T*nu       δû                                                        */
+  double* K;           /* Σ T*nu*nx    K_k                                                       */
+  double* p;           /* Σ n_rows     p                                                         */
+  double* ptilde;      /* Σ n_rows     p̃                                                         */
+  int* iters;          /* n            iterations run                                            */
+  double* r_p;         /* n            full primal residual                                      */
+  double* r_d;         /* n            full dual residual                                        */
+  int* status;         /* n            1 converged, 2 iteration cap, 3 non-finite                 */
+} nrto_socp_out;
+
+typedef struct nrto_problem* nrto_problem_t;
+
+/* Create a batch of n_instances problems (descs[0..n-1]) in the given precision on `cuda_stream`
+ * (a cudaStream_t, or NULL for the default stream).  Copies all inputs to the device, allocates all
+ * device memory of the batch, validates every descriptor (dims, finiteness, Σ_i SPD, τ >= 0).
+ * The nominal of each instance is its u_init; the trust radius is 2.0 until set by nrto_solve or
+ * nrto_set_trust_radius. */
+nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n_instances, int precision,
+                                void* cuda_stream, nrto_problem_t* out);
+nrto_status nrto_problem_destroy(nrto_problem_t p);
+nrto_status nrto_problem_info(nrto_problem_t p, int instance, nrto_instance_info* info);
+
+/* Replace the problem data of every instance (same dyn, nx, nu, T, obstacle and bound structure as
+ * at create) and reset the nominal to the new u_init.  Host → device copies only. */
+nrto_status nrto_problem_update(nrto_problem_t p, const nrto_problem_desc* descs, int n_instances);
+
+/* Linearize Problem 1 around the current nominal (Problem 2 data, Supplementary Sec. I): rollout
+ * x̂, Jacobians A_k, B_k, g_j(x̂), ∇g_j, the ragged rows b̂_j and b_j, and the Gram matrices of the
+ * gain Hessian.  u_hat (Σ T*nu, host) replaces the nominal first; NULL keeps it. */
+nrto_status nrto_linearize(nrto_problem_t p, const double* u_hat);
+
+/* Set the trust radius r of Problem 2 per instance (host array of n values). */
+nrto_status nrto_set_trust_radius(nrto_problem_t p, const double* r);
+
+/* One inner solve of Problem 2 at the current linearization for every instance (FullADMM or
+ * NRTO-DR per opts->solver).  Cold start (Algorithm 1 zero initialization) unless a warm start was
+ * set.  out may be NULL (results stay on the device).  Returns NRTO_ERR_NOT_CONVERGED if some
+ * instance hit its cap while opts->check == 1, NRTO_ERR_NUMERIC on non-finite residuals. */
+nrto_status nrto_solve_socp(nrto_problem_t p, const nrto_solver_opts* opts, nrto_socp_out* out);
+
+/* One successive-linearization step: inner solve, candidate ū = û + δû with gains K, linearization
+ * at the candidate, merit test, accept/reject and trust-radius update.  accepted (n ints) may be NULL. */
+nrto_status nrto_outer_step(nrto_problem_t p, const nrto_solver_opts* opts, int* accepted);
+
+/* Full solve: reset to u_init and r = opts->r0, linearize, then n_outer outer steps.  Outputs
+ * (host, may be NULL): u_bar Σ T*nu, K Σ T*nu*nx, merit n. */
+nrto_status nrto_solve(nrto_problem_t p, const nrto_solver_opts* opts, int n_outer,
+                       double* u_bar, double* K, double* merit);
+
+/* Warm start for the next inner solve only: K (Σ T*nu*nx), p̃ and λ_p (Σ n_rows each); λ_ν = 0. */
+nrto_status nrto_set_warm_start(nrto_problem_t p, const double* K, const double* ptilde,
+                                const double* lambda_p);
+
+/* Named internal arrays of one instance, converted to float64 (checkpointing and testing).
+ * field: one of NRTO_F_*; count must equal the field's size for that instance. */
+enum {
+  NRTO_F_XHAT = 0,   /* (T+1)*nx   nominal states of the current linearization               */
+  NRTO_F_UHAT = 1,   /* T*nu       nominal controls                                          */
+  NRTO_F_A = 2,      /* T*nx*nx                                                              */
+  NRTO_F_B = 3,      /* T*nx*nu                                                              */
+  NRTO_F_G0 = 4,     /* n_rows     g_j at the nominal                                        */
+  NRTO_F_BHAT = 5,   /* n_entries_state  b̂ rows (ragged)                                      */
+  NRTO_F_BVEC = 6,   /* Σ_state rows (t+1)*nu  b_{j,m} rows (ragged, block t zero)            */
+  NRTO_F_LAMNU = 7,  /* n_entries  λ_ν (FullADMM) or η̃ (DR) rows (ragged)                     */
+  NRTO_F_K = 8,      /* T*nu*nx    gains of the last inner solve                             */
+  NRTO_F_DU = 9,     /* T*nu       δû of the last inner solve                                */
+  NRTO_F_P = 10,     /* n_rows                                                                */
+  NRTO_F_PT = 11,    /* n_rows     p̃                                                          */
+  NRTO_F_LAMP = 12,  /* n_rows     λ_p (FullADMM, scaled) or λ (NRTO-DR, unscaled)            */
+  NRTO_F_GM = 13,    /* T*nu*nu    Σ_j b_{j,m} b_{j,m}ᵀ                                        */
+  NRTO_F_KACC = 14,  /* T*nu*nx    gains of the accepted nominal (outer loop)                 */
+  NRTO_F_DX = 15,    /* (T+1)*nx   δx of the last inner solve                                */
+  NRTO_F_SCAL = 16,  /* 8: r_p, r_d, r_p(paper), r_d(paper), merit, candidate merit, cost, trust r */
+  NRTO_F_STATS = 17  /* 4, read-only: inner iterations since the last nrto_solve reset, iterations of
+                        the last inner solve, its status, accepted outer steps                     */
+};
+nrto_status nrto_export(nrto_problem_t p, int field, int instance, double* dst, long long count);
+nrto_status nrto_import(nrto_problem_t p, int field, int instance, const double* src, long long count);
+
+/* Solver-kernel timing with CUDA events recorded on the problem's stream around every launch of the
+ * persistent inner-loop kernels.  Returns (and clears) the milliseconds and launch count accumulated
+ * since the previous call, then enables (enable != 0) or disables recording for later solves.
+ * Synchronizes the stream when events are pending. */
+nrto_status nrto_profile(nrto_problem_t p, int enable, double* solver_ms, long long* solver_launches);
+
+/* Number of kernel launches the library issued since create (all of its own kernels). */
+long long nrto_kernel_launches(nrto_problem_t p);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* nrto_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NRTO_H */

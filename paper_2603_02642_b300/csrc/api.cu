@@ -1,0 +1,996 @@
+// Host side of libnrto: the C ABI declared in include/nrto.h.
+//
+// A problem owns every device buffer of its batch.  create() validates the descriptors, builds the
+// row tables (constraint rows, ragged offsets, chunk boundaries for the persistent solver), uploads the
+// parameters and runs the setup kernel; the outer loop and the inner solvers are kernel launches on
+// the problem's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/nrto.h"
+#include "fulladmm.cuh"
+#include "dr.cuh"
+
+using namespace nrto;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct NrtoError : std::runtime_error {
+  nrto_status st;
+  NrtoError(nrto_status s, const std::string& m) : std::runtime_error(m), st(s) {}
+};
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      throw NrtoError(NRTO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+void fail(nrto_status s, const std::string& m) { throw NrtoError(s, m); }
+
+int kind_nx(int k) { return k == KIND_UNICYCLE ? 3 : (k == KIND_QUADCOPTER ? 12 : 14); }
+int kind_nu(int k) { return k == KIND_UNICYCLE ? 2 : (k == KIND_QUADCOPTER ? 4 : 7); }
+int kind_tmax(int k) { return k == KIND_UNICYCLE ? 256 : (k == KIND_QUADCOPTER ? 160 : 128); }
+
+// opt-in shared memory per block on sm_103a is 227 KB; keep 1 KB for static shared variables
+constexpr int SMEM_BUDGET = 227 * 1024 - 1024;
+
+template <typename Real>
+size_t smem_for(int kind, int tmax, int chunk, int max_rows) {
+  if (kind == KIND_UNICYCLE) return FASmem<3, 2, Real>::bytes(tmax, chunk, max_rows);
+  if (kind == KIND_QUADCOPTER) return FASmem<12, 4, Real>::bytes(tmax, chunk, max_rows);
+  return FASmem<14, 7, Real>::bytes(tmax, chunk, max_rows);
+}
+
+struct KindLaunch {
+  int kind = 0, count = 0, order0 = 0, tmax = 0, chunk = 0, max_rows = 0;
+  size_t smem = 0;
+};
+
+// ---- small kernels of the outer loop ----
+__global__ void k_scatter(double* arena, const Inst* inst, const double* stage, const long long* stage_off,
+                          const long long* stage_len, int n) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  double* dst = arena + inst[i].arena0;
+  const double* src = stage + stage_off[i];
+  for (long long q = threadIdx.x; q < stage_len[i]; q += blockDim.x) dst[q] = src[q];
+}
+
+__global__ void k_scatter_uhat(double* slot_arena, const Inst* inst, const double* src, const long long* off, int n) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const Inst I = inst[i];
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  double* dst = slot_arena + I.slot0 + SL.u_hat;
+  for (int q = threadIdx.x; q < I.T * I.nu; q += blockDim.x) dst[q] = src[off[i] + q];
+}
+
+template <typename Real>
+__global__ void k_candidate(Dev<Real> D) {
+  const int i = blockIdx.x;
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  const int cur = D.is[i * NIS + IS_SLOT];
+  const double* src = D.slot[cur].arena + I.slot0 + SL.u_hat;
+  double* dst = D.slot[1 - cur].arena + I.slot0 + SL.u_hat;
+  const double* du = D.arena + I.arena0 + L.du;
+  for (int q = threadIdx.x; q < I.T * I.nu; q += blockDim.x) dst[q] = src[q] + du[q];
+}
+
+template <typename Real>
+__global__ void k_accept(Dev<Real> D, double r0, double r_min) {
+  const int i = blockIdx.x;
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  double* ar = D.arena + I.arena0;
+  double* sc = D.sc + (long long)i * NSC;
+  __shared__ int acc;
+  if (threadIdx.x == 0) {
+    acc = sc[SC_PHI_CAND] < sc[SC_PHI] ? 1 : 0;
+    D.is[i * NIS + IS_ACCEPT] = acc;
+    D.is[i * NIS + IS_NACC] += acc;
+    if (acc) {
+      D.is[i * NIS + IS_SLOT] = 1 - D.is[i * NIS + IS_SLOT];
+      sc[SC_PHI] = sc[SC_PHI_CAND];
+      sc[SC_RTRUST] = fmin(1.5 * sc[SC_RTRUST], r0);
+    } else {
+      sc[SC_RTRUST] = fmax(0.8 * sc[SC_RTRUST], r_min);
+    }
+  }
+  __syncthreads();
+  if (acc)
+    for (int q = threadIdx.x; q < I.T * I.nu * I.nx; q += blockDim.x) ar[L.Kacc + q] = ar[L.K1 + q];
+}
+
+template <typename Real>
+__global__ void k_reset_outer(Dev<Real> D, double r0) {
+  const int i = blockIdx.x;
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  double* ar = D.arena + I.arena0;
+  if (threadIdx.x == 0) {
+    D.is[i * NIS + IS_SLOT] = 0;
+    D.is[i * NIS + IS_CUMITERS] = 0;
+    D.is[i * NIS + IS_NACC] = 0;
+    D.sc[(long long)i * NSC + SC_RTRUST] = r0;
+  }
+  for (int q = threadIdx.x; q < I.T * I.nu * I.nx; q += blockDim.x) ar[L.Kacc + q] = 0.0;
+}
+
+}  // namespace
+
+struct nrto_problem;
+template <typename Real>
+void launch_dr(nrto_problem* P, const nrto_solver_opts& o, SolveParams sp);
+
+// =============================================================================================
+struct nrto_problem {
+  int n = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<Inst> h_inst;
+  std::vector<int4> h_rinfo;
+  std::vector<int> h_order;
+  KindLaunch kl[3];
+  long long n_rows = 0, n_ent = 0, n_bent = 0, arena_total = 0, slot_total = 0, arow_total = 0;
+  long long n_groups_total = 0, n_cb_total = 0;
+  std::vector<long long> stage_off, stage_len, uoff;
+  long long stage_total = 0, u_total = 0;
+  std::vector<void*> allocs;
+  // device
+  Inst* d_inst = nullptr;
+  double* d_arena = nullptr;
+  int4* d_rinfo = nullptr;
+  long long* d_rent = nullptr;
+  long long* d_rbent = nullptr;
+  int* d_cbound = nullptr;
+  int2* d_groups = nullptr;
+  double* d_slot_arena[2] = {nullptr, nullptr};
+  double* d_g0[2] = {nullptr, nullptr};
+  double* d_arow[2] = {nullptr, nullptr};
+  void* d_bhat[2] = {nullptr, nullptr};
+  void* d_bvec[2] = {nullptr, nullptr};
+  void* d_lam = nullptr;
+  double *d_p = nullptr, *d_pt = nullptr, *d_ptn = nullptr, *d_lamp = nullptr, *d_w = nullptr, *d_lamw = nullptr,
+         *d_s = nullptr, *d_ell = nullptr, *d_dd = nullptr, *d_rnorm = nullptr;
+  double* d_sc = nullptr;
+  int* d_is = nullptr;
+  int* d_queue = nullptr;
+  int* d_order = nullptr;
+  double* d_stage = nullptr;
+  long long* d_stage_off = nullptr;
+  long long* d_stage_len = nullptr;
+  long long* d_uoff = nullptr;
+  double* d_ustage = nullptr;
+  bool linearized = false;
+  bool warm_pending = false;
+  long long launches = 0;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;   // around each solver-kernel launch
+  long long prof_launches = 0;
+
+  template <typename T>
+  T* dalloc(size_t count) {
+    void* ptr = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    CK(cudaMalloc(&ptr, bytes));
+    allocs.push_back(ptr);
+    CK(cudaMemsetAsync(ptr, 0, bytes, stream));
+    return static_cast<T*>(ptr);
+  }
+  ~nrto_problem() {
+    for (auto& ev : prof_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+    for (void* a : allocs) cudaFree(a);
+  }
+  template <typename Real>
+  Dev<Real> dev() const {
+    Dev<Real> D;
+    D.n_inst = n;
+    D.inst = d_inst;
+    D.arena = d_arena;
+    D.rinfo = d_rinfo;
+    D.rent = d_rent;
+    D.rbent = d_rbent;
+    D.cbound = d_cbound;
+    D.groups = d_groups;
+    for (int s = 0; s < 2; ++s) {
+      D.slot[s].arena = d_slot_arena[s];
+      D.slot[s].g0 = d_g0[s];
+      D.slot[s].arow = d_arow[s];
+      D.slot[s].bhat = static_cast<Real*>(d_bhat[s]);
+      D.slot[s].bvec = static_cast<Real*>(d_bvec[s]);
+    }
+    D.lam = static_cast<Real*>(d_lam);
+    D.p = d_p; D.pt = d_pt; D.ptn = d_ptn; D.lamp = d_lamp; D.w = d_w; D.lamw = d_lamw; D.s = d_s;
+    D.ell = d_ell; D.dd = d_dd; D.rnorm = d_rnorm;
+    D.sc = d_sc; D.is = d_is; D.queue = d_queue; D.order = d_order;
+    return D;
+  }
+  void check_launch(const char* what) {
+    ++launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) fail(NRTO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+};
+
+namespace {
+
+bool finite_arr(const double* a, long long n) {
+  if (n > 0 && a == nullptr) return false;
+  for (long long i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+void validate(const nrto_problem_desc& d, int idx) {
+  auto bad = [&](const std::string& m) { fail(NRTO_ERR_INVALID, "instance " + std::to_string(idx) + ": " + m); };
+  auto num = [&](const std::string& m) { fail(NRTO_ERR_NUMERIC, "instance " + std::to_string(idx) + ": " + m); };
+  if (d.dyn < 0 || d.dyn > 2) bad("unknown dyn kind");
+  if (d.nx != kind_nx(d.dyn) || d.nu != kind_nu(d.dyn)) bad("nx/nu do not match the dynamics model");
+  if (d.T < 1 || d.T > kind_tmax(d.dyn)) bad("T out of range");
+  if (!(d.dt > 0) || !std::isfinite(d.dt)) bad("dt must be positive");
+  if (!(d.tau >= 0) || !std::isfinite(d.tau)) bad("tau must be >= 0");
+  const int need_dyn = d.dyn == KIND_QUADCOPTER ? 5 : (d.dyn == KIND_ARM ? 21 : 0);
+  if (d.n_dyn_params < need_dyn || d.n_dyn_params > MAX_DYN) bad("wrong number of dyn_params");
+  if (!finite_arr(d.dyn_params, d.n_dyn_params)) bad("dyn_params not finite");
+  if (!finite_arr(d.x0, d.nx) || !finite_arr(d.x_goal, d.nx) || !finite_arr(d.u_ref, d.nu)) bad("x0/x_goal/u_ref");
+  if (!finite_arr(d.u_init, (long long)d.T * d.nu)) num("u_init not finite");
+  if (!finite_arr(d.Sigma, (long long)(d.T + 1) * d.nx * d.nx)) num("Sigma not finite");
+  if (!finite_arr(d.Qx, d.nx) || !finite_arr(d.Ru, d.nu) || !finite_arr(d.RK, d.nu)) bad("weights");
+  for (int i = 0; i < d.nu; ++i)
+    if (!(d.Ru[i] > 0) || !(d.RK[i] > 0)) bad("Ru and RK must be positive");
+  for (int i = 0; i < d.nx; ++i)
+    if (d.Qx[i] < 0) bad("Qx must be >= 0");
+  if (d.n_obs < 0) bad("n_obs < 0");
+  if (d.n_obs > 0) {
+    if (d.dyn == KIND_UNICYCLE ? d.obs_dim != 2 : d.obs_dim != 3) bad("obs_dim");
+    if (!finite_arr(d.obs_center, (long long)d.n_obs * d.obs_dim) || !finite_arr(d.obs_radius, d.n_obs)) bad("obstacles");
+  }
+  if (d.dyn == KIND_ARM) {
+    if (d.n_link < 0 || (d.n_link > 0 && !finite_arr(d.link_spheres, 5LL * d.n_link))) bad("link spheres");
+    for (int l = 0; l < d.n_link; ++l) {
+      int li = (int)d.link_spheres[5 * l];
+      if (li < 1 || li > 7) bad("link index must be 1..7");
+    }
+  } else if (d.n_link != 0) {
+    bad("n_link only for the arm");
+  }
+  if (!d.u_lo || !d.u_hi || !d.x_lo || !d.x_hi) bad("bounds arrays required (use ±inf)");
+  for (int i = 0; i < d.nu; ++i) {
+    if (std::isnan(d.u_lo[i]) || std::isnan(d.u_hi[i])) bad("NaN control bound");
+    if (std::isfinite(d.u_lo[i]) && std::isfinite(d.u_hi[i]) && d.u_lo[i] > d.u_hi[i]) bad("u_lo > u_hi");
+  }
+  for (int i = 0; i < d.nx; ++i)
+    if (std::isnan(d.x_lo[i]) || std::isnan(d.x_hi[i])) bad("NaN state bound");
+  std::vector<double> C(d.nx * d.nx);
+  for (int m = 0; m <= d.T; ++m) {
+    for (int k = 0; k < d.nx * d.nx; ++k) C[k] = d.Sigma[(long long)m * d.nx * d.nx + k];
+    for (int r = 0; r < d.nx; ++r)
+      for (int c = 0; c < r; ++c)
+        if (std::fabs(C[r * d.nx + c] - C[c * d.nx + r]) > 1e-12 * (std::fabs(C[r * d.nx + c]) + 1e-300)) bad("Sigma block not symmetric");
+    if (!chol_inplace(C.data(), d.nx)) bad("Sigma block not positive definite");
+  }
+}
+
+// rows of one instance in the shared row order
+void build_rows(const nrto_problem_desc& d, std::vector<int4>& srows, std::vector<int4>& crows, int& rows_per_t) {
+  srows.clear();
+  crows.clear();
+  rows_per_t = 0;
+  for (int t = 1; t <= d.T; ++t) {
+    size_t before = srows.size();
+    if (d.dyn == KIND_ARM) {
+      for (int l = 0; l < d.n_link; ++l)
+        for (int o = 0; o < d.n_obs; ++o) srows.push_back(make_int4(t, ROW_SPHERE, o, l));
+    } else {
+      for (int o = 0; o < d.n_obs; ++o) srows.push_back(make_int4(t, ROW_SPHERE, o, -1));
+    }
+    for (int i = 0; i < d.nx; ++i) {
+      if (std::isfinite(d.x_hi[i])) srows.push_back(make_int4(t, ROW_XHI, i, -1));
+      if (std::isfinite(d.x_lo[i])) srows.push_back(make_int4(t, ROW_XLO, i, -1));
+    }
+    rows_per_t = (int)(srows.size() - before);
+  }
+  for (int k = 0; k < d.T; ++k)
+    for (int i = 0; i < d.nu; ++i) {
+      if (std::isfinite(d.u_hi[i])) crows.push_back(make_int4(k, ROW_UHI, i, -1));
+      if (std::isfinite(d.u_lo[i])) crows.push_back(make_int4(k, ROW_ULO, i, -1));
+    }
+}
+
+void pack_params(const nrto_problem_desc& d, const Arena& L, double* dst) {
+  auto put = [&](long long off, const double* src, long long n) { for (long long i = 0; i < n; ++i) dst[off + i] = src[i]; };
+  put(L.x0, d.x0, d.nx); put(L.xg, d.x_goal, d.nx); put(L.uref, d.u_ref, d.nu);
+  put(L.Qx, d.Qx, d.nx); put(L.Ru, d.Ru, d.nu); put(L.RK, d.RK, d.nu);
+  put(L.ulo, d.u_lo, d.nu); put(L.uhi, d.u_hi, d.nu); put(L.xlo, d.x_lo, d.nx); put(L.xhi, d.x_hi, d.nx);
+  if (d.n_dyn_params > 0) put(L.dyn, d.dyn_params, d.n_dyn_params);
+  for (int o = 0; o < d.n_obs; ++o) {
+    for (int k = 0; k < 3; ++k) dst[L.obs + 4 * o + k] = (k < d.obs_dim) ? d.obs_center[o * d.obs_dim + k] : 0.0;
+    dst[L.obs + 4 * o + 3] = d.obs_radius[o];
+  }
+  if (d.n_link > 0) put(L.link, d.link_spheres, 5LL * d.n_link);
+  put(L.Sigma, d.Sigma, (long long)(d.T + 1) * d.nx * d.nx);
+}
+
+template <typename Real>
+void launch_setup(nrto_problem* P) {
+  k_setup<Real><<<P->n, 128, 0, P->stream>>>(P->dev<Real>());
+  P->check_launch("k_setup");
+}
+
+// slot_sel: -1 = current slot of each instance, -2 = candidate slot (1 - current)
+template <typename Real>
+void launch_linearize(nrto_problem* P, int slot_sel) {
+  Dev<Real> D = P->dev<Real>();
+  k_rollout_jac<Real><<<P->n, 128, 0, P->stream>>>(D, slot_sel);
+  P->check_launch("k_rollout_jac");
+  k_rows<Real><<<P->n, 256, 0, P->stream>>>(D, slot_sel);
+  P->check_launch("k_rows");
+  k_adjoint<Real><<<P->n, 256, 0, P->stream>>>(D, slot_sel);
+  P->check_launch("k_adjoint");
+  k_gram<Real><<<P->n, 256, 0, P->stream>>>(D, slot_sel);
+  P->check_launch("k_gram");
+}
+
+template <int NX, int NU, typename Real>
+void launch_fa_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
+  auto kern = k_fulladmm<NX, NU, Real>;
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kl.smem));
+  int dev = 0, nsm = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FACfg<NX, NU>::NT, kl.smem));
+  if (per_sm < 1) fail(NRTO_ERR_CUDA, "solver kernel does not fit on an SM");
+  const int grid = std::min(kl.count, nsm * per_sm);
+  sp.chunk = kl.chunk; sp.max_rows = kl.max_rows; sp.tmax = kl.tmax; sp.n_order = kl.count;
+  sp.order0 = kl.order0; sp.queue_idx = kl.kind;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->profiling) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, P->stream));
+  }
+  kern<<<grid, FACfg<NX, NU>::NT, kl.smem, P->stream>>>(P->dev<Real>(), sp);
+  P->check_launch("k_fulladmm");
+  if (P->profiling) {
+    CK(cudaEventRecord(e1, P->stream));
+    P->prof_events.push_back({e0, e1});
+    P->prof_launches++;
+  }
+}
+
+template <typename Real>
+void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
+  Dev<Real> D = P->dev<Real>();
+  SolveParams sp{};
+  sp.rho = o.rho; sp.eps_p = o.eps_p; sp.eps_d = o.eps_d;
+  sp.alpha = o.alpha; sp.r_chi = o.r_chi; sp.sigma = o.sigma; sp.eps_dr = o.eps_dr;
+  sp.max_iter = o.max_inner; sp.check = o.check; sp.warm = P->warm_pending ? 1 : 0; sp.max_dr = o.max_dr;
+  P->warm_pending = false;
+  if (o.solver == NRTO_SOLVER_FULLADMM) {
+    k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.rho, 0.0);
+    P->check_launch("k_gain_factors");
+    k_riccati_factor<Real><<<P->n, 32, 0, P->stream>>>(D, o.rho);
+    P->check_launch("k_riccati_factor");
+    CK(cudaMemsetAsync(P->d_queue, 0, 4 * sizeof(int), P->stream));
+    for (int k = 0; k < 3; ++k) {
+      const KindLaunch& kl = P->kl[k];
+      if (kl.count == 0) continue;
+      if (k == KIND_UNICYCLE) launch_fa_kind<3, 2, Real>(P, kl, sp);
+      else if (k == KIND_QUADCOPTER) launch_fa_kind<12, 4, Real>(P, kl, sp);
+      else launch_fa_kind<14, 7, Real>(P, kl, sp);
+    }
+  } else {
+    launch_dr<Real>(P, o, sp);
+  }
+}
+
+template <typename Real>
+void launch_merit_current(nrto_problem* P, double w_p) {
+  Dev<Real> D = P->dev<Real>();
+  k_gain_to_gt<Real><<<P->n, 256, 0, P->stream>>>(D, 3, 0);
+  P->check_launch("k_gain_to_gt");
+  k_merit<Real><<<P->n, 256, 0, P->stream>>>(D, -1, 3, 0, w_p, SC_PHI);
+  P->check_launch("k_merit");
+}
+
+template <typename Real>
+void launch_outer_step(nrto_problem* P, const nrto_solver_opts& o) {
+  Dev<Real> D = P->dev<Real>();
+  launch_solve<Real>(P, o);
+  k_candidate<Real><<<P->n, 128, 0, P->stream>>>(D);
+  P->check_launch("k_candidate");
+  launch_linearize<Real>(P, -2);
+  k_gain_to_gt<Real><<<P->n, 256, 0, P->stream>>>(D, 1, 1);
+  P->check_launch("k_gain_to_gt");
+  k_merit<Real><<<P->n, 256, 0, P->stream>>>(D, -2, 1, 1, o.w_p, SC_PHI_CAND);
+  P->check_launch("k_merit");
+  k_accept<Real><<<P->n, 128, 0, P->stream>>>(D, o.r0, o.r_min);
+  P->check_launch("k_accept");
+}
+
+template <typename Real>
+void choose_chunk(KindLaunch& kl) {
+  const int nx = kind_nx(kl.kind);
+  const int minc = ((kl.tmax + 1) * nx + 3) & ~3;
+  int chunk = 8192;
+  while (chunk > minc && smem_for<Real>(kl.kind, kl.tmax, chunk, chunk / (2 * nx) + 2) > (size_t)SMEM_BUDGET) chunk -= 256;
+  if (chunk < minc) chunk = minc;
+  kl.chunk = chunk;
+  kl.max_rows = chunk / (2 * nx) + 2;
+  kl.smem = smem_for<Real>(kl.kind, kl.tmax, chunk, kl.max_rows);
+  if (kl.smem > (size_t)SMEM_BUDGET) fail(NRTO_ERR_INVALID, "horizon too long for the shared-memory budget of this precision");
+}
+
+// per-instance arena/slot field copy (device → host) of cnt(I) doubles at off(I)
+void copy_arena_field(nrto_problem* P, int which /*0 arena, 1 current slot*/, long long (*off)(const Inst&),
+                      double* dst, long long (*cnt)(const Inst&)) {
+  std::vector<int> is(P->n * NIS);
+  CK(cudaMemcpyAsync(is.data(), P->d_is, sizeof(int) * is.size(), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  long long o = 0;
+  for (int i = 0; i < P->n; ++i) {
+    const Inst& I = P->h_inst[i];
+    const double* base = which == 0 ? P->d_arena + I.arena0 : P->d_slot_arena[is[i * NIS + IS_SLOT]] + I.slot0;
+    CK(cudaMemcpyAsync(dst + o, base + off(I), sizeof(double) * cnt(I), cudaMemcpyDeviceToHost, P->stream));
+    o += cnt(I);
+  }
+  CK(cudaStreamSynchronize(P->stream));
+}
+
+long long off_du(const Inst& I) { return arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link).du; }
+long long off_k1(const Inst& I) { return arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link).K1; }
+long long off_kacc(const Inst& I) { return arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link).Kacc; }
+long long off_uhat(const Inst& I) { return slot_layout(I.nx, I.nu, I.T).u_hat; }
+long long cnt_u(const Inst& I) { return (long long)I.T * I.nu; }
+long long cnt_k(const Inst& I) { return (long long)I.T * I.nu * I.nx; }
+
+nrto_status handle(const std::exception& e) {
+  if (auto ne = dynamic_cast<const NrtoError*>(&e)) {
+    g_last_error = ne->what();
+    return ne->st;
+  }
+  g_last_error = e.what();
+  return NRTO_ERR_INVALID;
+}
+
+void upload_params(nrto_problem* P, const nrto_problem_desc* descs) {
+  std::vector<double> stage(P->stage_total, 0.0);
+  std::vector<double> ust(P->u_total, 0.0);
+  for (int i = 0; i < P->n; ++i) {
+    const Inst& I = P->h_inst[i];
+    const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+    pack_params(descs[i], L, stage.data() + P->stage_off[i]);
+    std::memcpy(ust.data() + P->uoff[i], descs[i].u_init, sizeof(double) * I.T * I.nu);
+  }
+  CK(cudaMemcpyAsync(P->d_stage, stage.data(), sizeof(double) * stage.size(), cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->d_ustage, ust.data(), sizeof(double) * ust.size(), cudaMemcpyHostToDevice, P->stream));
+  k_scatter<<<P->n, 256, 0, P->stream>>>(P->d_arena, P->d_inst, P->d_stage, P->d_stage_off, P->d_stage_len, P->n);
+  P->check_launch("k_scatter");
+  for (int s = 0; s < 2; ++s) {
+    k_scatter_uhat<<<P->n, 128, 0, P->stream>>>(P->d_slot_arena[s], P->d_inst, P->d_ustage, P->d_uoff, P->n);
+    P->check_launch("k_scatter_uhat");
+  }
+  CK(cudaStreamSynchronize(P->stream));   // host staging vectors go out of scope
+}
+
+void check_opts(const nrto_solver_opts* o) {
+  if (!o) fail(NRTO_ERR_INVALID, "null options");
+  if (o->solver != NRTO_SOLVER_DR && o->solver != NRTO_SOLVER_FULLADMM) fail(NRTO_ERR_INVALID, "unknown solver");
+  if (!(o->rho > 0)) fail(NRTO_ERR_INVALID, "rho must be positive");
+  if (o->max_inner < 0 || o->max_inner > 1000000) fail(NRTO_ERR_INVALID, "max_inner out of range");
+  if (o->solver == NRTO_SOLVER_DR) {
+    if (!(o->alpha > 0 && o->alpha < 2)) fail(NRTO_ERR_INVALID, "alpha must be in (0,2)");
+    if (!(o->r_chi > 0) || !(o->sigma > 0)) fail(NRTO_ERR_INVALID, "r_chi and sigma must be positive");
+    if (o->max_dr < 1 || o->max_dr > 1000000) fail(NRTO_ERR_INVALID, "max_dr out of range");
+  }
+}
+
+nrto_status finish_statuses(nrto_problem* p, const nrto_solver_opts* o, nrto_socp_out* out) {
+  std::vector<int> is(p->n * NIS);
+  std::vector<double> sc(p->n * NSC);
+  CK(cudaMemcpyAsync(is.data(), p->d_is, sizeof(int) * is.size(), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(sc.data(), p->d_sc, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
+  if (out->du) copy_arena_field(p, 0, off_du, out->du, cnt_u);
+  if (out->K) copy_arena_field(p, 0, off_k1, out->K, cnt_k);
+  if (out->p) CK(cudaMemcpyAsync(out->p, p->d_p, sizeof(double) * p->n_rows, cudaMemcpyDeviceToHost, p->stream));
+  if (out->ptilde) CK(cudaMemcpyAsync(out->ptilde, p->d_pt, sizeof(double) * p->n_rows, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  nrto_status st = NRTO_OK;
+  for (int i = 0; i < p->n; ++i) {
+    if (out->iters) out->iters[i] = is[i * NIS + IS_ITERS];
+    if (out->status) out->status[i] = is[i * NIS + IS_STATUS];
+    if (out->r_p) out->r_p[i] = sc[i * NSC + SC_RP];
+    if (out->r_d) out->r_d[i] = sc[i * NSC + SC_RD];
+    if (is[i * NIS + IS_STATUS] == ST_NUMERIC) st = NRTO_ERR_NUMERIC;
+    else if (o->check && is[i * NIS + IS_STATUS] == ST_MAXITER && st == NRTO_OK) st = NRTO_ERR_NOT_CONVERGED;
+  }
+  if (st != NRTO_OK) g_last_error = st == NRTO_ERR_NUMERIC ? "non-finite residual in some instance" : "some instance hit its iteration cap";
+  return st;
+}
+
+long long field_count(const Inst& I, int f) {
+  switch (f) {
+    case NRTO_F_XHAT: case NRTO_F_DX: return (long long)(I.T + 1) * I.nx;
+    case NRTO_F_UHAT: case NRTO_F_DU: return (long long)I.T * I.nu;
+    case NRTO_F_A: return (long long)I.T * I.nx * I.nx;
+    case NRTO_F_B: return (long long)I.T * I.nx * I.nu;
+    case NRTO_F_G0: case NRTO_F_P: case NRTO_F_PT: case NRTO_F_LAMP: return I.n_sr + I.n_cr;
+    case NRTO_F_BHAT: return I.n_ent_state;
+    case NRTO_F_BVEC: return (I.n_ent_state / I.nx) * I.nu;
+    case NRTO_F_LAMNU: return I.n_ent;
+    case NRTO_F_K: case NRTO_F_KACC: return (long long)I.T * I.nu * I.nx;
+    case NRTO_F_GM: return (long long)I.T * I.nu * I.nu;
+    case NRTO_F_SCAL: return 8;
+    case NRTO_F_STATS: return 4;
+  }
+  return -1;
+}
+
+nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long count, bool to_host) {
+  try {
+    if (!p || !buf || i < 0 || i >= p->n) fail(NRTO_ERR_INVALID, "bad problem, instance or buffer");
+    const Inst& I = p->h_inst[i];
+    const long long need = field_count(I, field);
+    if (need < 0) fail(NRTO_ERR_INVALID, "unknown field");
+    if (count != need) fail(NRTO_ERR_INVALID, "count must be " + std::to_string(need));
+    CK(cudaStreamSynchronize(p->stream));
+    int is[NIS];
+    CK(cudaMemcpy(is, p->d_is + i * NIS, sizeof(is), cudaMemcpyDeviceToHost));
+    const int sl = is[IS_SLOT];
+    const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+    const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+    const size_t rs = p->prec == NRTO_PREC_FP64 ? 8 : 4;
+    double* dptr = nullptr;
+    void* rptr = nullptr;   // arrays stored in the compute precision
+    switch (field) {
+      case NRTO_F_XHAT: dptr = p->d_slot_arena[sl] + I.slot0 + SL.x_hat; break;
+      case NRTO_F_UHAT: dptr = p->d_slot_arena[sl] + I.slot0 + SL.u_hat; break;
+      case NRTO_F_A: dptr = p->d_slot_arena[sl] + I.slot0 + SL.A; break;
+      case NRTO_F_B: dptr = p->d_slot_arena[sl] + I.slot0 + SL.B; break;
+      case NRTO_F_GM: dptr = p->d_slot_arena[sl] + I.slot0 + SL.Gm; break;
+      case NRTO_F_G0: dptr = p->d_g0[sl] + I.row0; break;
+      case NRTO_F_P: dptr = p->d_p + I.row0; break;
+      case NRTO_F_PT: dptr = p->d_pt + I.row0; break;
+      case NRTO_F_LAMP: dptr = p->d_lamp + I.row0; break;
+      case NRTO_F_K: dptr = p->d_arena + I.arena0 + L.K1; break;
+      case NRTO_F_KACC: dptr = p->d_arena + I.arena0 + L.Kacc; break;
+      case NRTO_F_DU: dptr = p->d_arena + I.arena0 + L.du; break;
+      case NRTO_F_DX: dptr = p->d_arena + I.arena0 + L.dx; break;
+      case NRTO_F_BHAT: rptr = static_cast<char*>(p->d_bhat[sl]) + rs * I.ent0; break;
+      case NRTO_F_BVEC: rptr = static_cast<char*>(p->d_bvec[sl]) + rs * I.bent0; break;
+      case NRTO_F_LAMNU: rptr = static_cast<char*>(p->d_lam) + rs * I.ent0; break;
+      case NRTO_F_STATS: {
+        if (!to_host) fail(NRTO_ERR_INVALID, "stats are read-only");
+        buf[0] = is[IS_CUMITERS]; buf[1] = is[IS_ITERS]; buf[2] = is[IS_STATUS]; buf[3] = is[IS_NACC];
+        return NRTO_OK;
+      }
+      case NRTO_F_SCAL: {
+        double sc[NSC];
+        CK(cudaMemcpy(sc, p->d_sc + (long long)i * NSC, sizeof(sc), cudaMemcpyDeviceToHost));
+        const int idx[8] = {SC_RP, SC_RD, SC_RPP, SC_RDP, SC_PHI, SC_PHI_CAND, SC_COST, SC_RTRUST};
+        if (to_host) {
+          for (int k = 0; k < 8; ++k) buf[k] = sc[idx[k]];
+        } else {
+          for (int k = 0; k < 8; ++k) sc[idx[k]] = buf[k];
+          CK(cudaMemcpy(p->d_sc + (long long)i * NSC, sc, sizeof(sc), cudaMemcpyHostToDevice));
+        }
+        return NRTO_OK;
+      }
+    }
+    if (dptr) {
+      CK(cudaMemcpy(to_host ? (void*)buf : (void*)dptr, to_host ? (void*)dptr : (void*)buf, sizeof(double) * count,
+                    to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice));
+    } else if (p->prec == NRTO_PREC_FP64) {
+      CK(cudaMemcpy(to_host ? (void*)buf : rptr, to_host ? rptr : (void*)buf, sizeof(double) * count,
+                    to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> tmp(count);
+      if (to_host) {
+        CK(cudaMemcpy(tmp.data(), rptr, sizeof(float) * count, cudaMemcpyDeviceToHost));
+        for (long long k = 0; k < count; ++k) buf[k] = tmp[k];
+      } else {
+        for (long long k = 0; k < count; ++k) tmp[k] = (float)buf[k];
+        CK(cudaMemcpy(rptr, tmp.data(), sizeof(float) * count, cudaMemcpyHostToDevice));
+      }
+    }
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+const char* nrto_last_error(void) { return g_last_error.c_str(); }
+
+nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int precision, void* stream,
+                                nrto_problem_t* out) {
+  nrto_problem* P = nullptr;
+  try {
+    g_last_error.clear();
+    if (!descs || n <= 0 || !out) fail(NRTO_ERR_INVALID, "descs, n > 0 and out are required");
+    if (precision != NRTO_PREC_FP64 && precision != NRTO_PREC_MIXED) fail(NRTO_ERR_INVALID, "unknown precision");
+    for (int i = 0; i < n; ++i) validate(descs[i], i);
+    P = new nrto_problem();
+    P->n = n;
+    P->prec = precision;
+    P->stream = static_cast<cudaStream_t>(stream);
+    for (int k = 0; k < 3; ++k) P->kl[k].kind = k;
+    for (int i = 0; i < n; ++i) {
+      KindLaunch& kl = P->kl[descs[i].dyn];
+      kl.count++;
+      kl.tmax = std::max(kl.tmax, descs[i].T);
+    }
+    for (int k = 0; k < 3; ++k)
+      if (P->kl[k].count > 0) {
+        if (precision == NRTO_PREC_FP64) choose_chunk<double>(P->kl[k]);
+        else choose_chunk<float>(P->kl[k]);
+      }
+    std::vector<long long> rent, rbent;
+    std::vector<int> cbound;
+    std::vector<int2> groups;
+    std::vector<int4> srows, crows;
+    long long row = 0, ent = 0, bent = 0, arena = 0, slot = 0, arow = 0, grp = 0, stage = 0, uo = 0;
+    int cb = 0;
+    P->h_inst.resize(n);
+    for (int i = 0; i < n; ++i) {
+      const nrto_problem_desc& d = descs[i];
+      int rpt = 0;
+      build_rows(d, srows, crows, rpt);
+      Inst I{};
+      I.kind = d.dyn; I.nx = d.nx; I.nu = d.nu; I.T = d.T;
+      I.n_sr = (int)srows.size(); I.n_cr = (int)crows.size(); I.rows_per_t = rpt;
+      I.n_obs = d.n_obs; I.obs_dim = d.obs_dim; I.n_link = d.n_link; I.n_dyn = d.n_dyn_params;
+      I.row0 = row; I.ent0 = ent; I.bent0 = bent; I.arena0 = arena; I.slot0 = slot; I.arow0 = arow;
+      I.grp0 = grp; I.cb0 = cb;
+      I.dt = d.dt; I.tau = d.tau; I.sqrt_tau = std::sqrt(d.tau);
+      for (const int4& r : srows) {
+        P->h_rinfo.push_back(r);
+        rent.push_back(ent);
+        rbent.push_back(bent);
+        ent += (long long)(r.x + 1) * d.nx;
+        bent += (long long)(r.x + 1) * d.nu;
+      }
+      I.n_ent_state = ent - I.ent0;
+      int ng = 0;
+      for (size_t q = 0; q < crows.size(); ++q) {
+        const long long R = row + I.n_sr + (long long)q;
+        if (q == 0 || crows[q].x != crows[q - 1].x || crows[q].z != crows[q - 1].z) {
+          groups.push_back(make_int2((int)R, 1));
+          ++ng;
+        } else {
+          groups.back().y += 1;
+        }
+        P->h_rinfo.push_back(crows[q]);
+        rent.push_back(ent);
+        rbent.push_back(-1);
+        ent += d.nx;
+      }
+      I.n_groups = ng;
+      if (ng > 0 && ng % d.T != 0) fail(NRTO_ERR_INVALID, "internal: control groups not uniform over steps");
+      I.n_ent = ent - I.ent0;
+      // chunks of whole state rows for the persistent solver
+      const int chunk = P->kl[d.dyn].chunk;
+      int nch = 0;
+      cbound.push_back(0);
+      long long accn = 0;
+      for (int r = 0; r < I.n_sr; ++r) {
+        const long long len = (long long)(srows[r].x + 1) * d.nx;
+        if (accn + len > chunk && accn > 0) { cbound.push_back(r); ++nch; accn = 0; }
+        accn += len;
+      }
+      if (I.n_sr > 0) { cbound.push_back(I.n_sr); ++nch; }
+      I.n_chunks = nch;
+      cb += nch + 1;
+      const Arena L = arena_layout(d.nx, d.nu, d.T, d.n_obs, d.n_link);
+      const SlotL SL = slot_layout(d.nx, d.nu, d.T);
+      P->stage_off.push_back(stage);
+      P->stage_len.push_back(L.Psi);
+      stage += L.Psi;
+      P->uoff.push_back(uo);
+      uo += (long long)d.T * d.nu;
+      arena += L.total; slot += SL.total; arow += (long long)I.n_sr * d.nx;
+      row += I.n_sr + I.n_cr; grp += ng;
+      P->h_inst[i] = I;
+    }
+    P->n_rows = row; P->n_ent = ent; P->n_bent = bent; P->arena_total = arena; P->slot_total = slot;
+    P->arow_total = arow; P->n_groups_total = grp; P->n_cb_total = cb;
+    P->stage_total = stage; P->u_total = uo;
+    // instance order per kind: largest row count first (work-queue balance)
+    for (int k = 0, o = 0; k < 3; ++k) {
+      P->kl[k].order0 = o;
+      std::vector<int> ids;
+      for (int i = 0; i < n; ++i)
+        if (P->h_inst[i].kind == k) ids.push_back(i);
+      std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return P->h_inst[a].n_ent > P->h_inst[b].n_ent; });
+      for (int id : ids) P->h_order.push_back(id);
+      o += (int)ids.size();
+    }
+    const size_t rs = precision == NRTO_PREC_FP64 ? sizeof(double) : sizeof(float);
+    P->d_inst = P->dalloc<Inst>(n);
+    P->d_arena = P->dalloc<double>(arena);
+    P->d_rinfo = P->dalloc<int4>(row);
+    P->d_rent = P->dalloc<long long>(row);
+    P->d_rbent = P->dalloc<long long>(row);
+    P->d_cbound = P->dalloc<int>(cb);
+    P->d_groups = P->dalloc<int2>(grp);
+    for (int s = 0; s < 2; ++s) {
+      P->d_slot_arena[s] = P->dalloc<double>(slot);
+      P->d_g0[s] = P->dalloc<double>(row);
+      P->d_arow[s] = P->dalloc<double>(arow);
+      P->d_bhat[s] = P->dalloc<char>(rs * ent);
+      P->d_bvec[s] = P->dalloc<char>(rs * bent);
+    }
+    P->d_lam = P->dalloc<char>(rs * ent);
+    P->d_p = P->dalloc<double>(row); P->d_pt = P->dalloc<double>(row); P->d_ptn = P->dalloc<double>(row);
+    P->d_lamp = P->dalloc<double>(row); P->d_w = P->dalloc<double>(row); P->d_lamw = P->dalloc<double>(row);
+    P->d_s = P->dalloc<double>(row); P->d_ell = P->dalloc<double>(row); P->d_dd = P->dalloc<double>(row);
+    P->d_rnorm = P->dalloc<double>(row);
+    P->d_sc = P->dalloc<double>((size_t)n * NSC);
+    P->d_is = P->dalloc<int>((size_t)n * NIS);
+    P->d_queue = P->dalloc<int>(8);
+    P->d_order = P->dalloc<int>(n);
+    P->d_stage = P->dalloc<double>(stage);
+    P->d_stage_off = P->dalloc<long long>(n);
+    P->d_stage_len = P->dalloc<long long>(n);
+    P->d_uoff = P->dalloc<long long>(n);
+    P->d_ustage = P->dalloc<double>(uo);
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+      if (bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, P->stream));
+    };
+    up(P->d_inst, P->h_inst.data(), sizeof(Inst) * n);
+    up(P->d_rinfo, P->h_rinfo.data(), sizeof(int4) * row);
+    up(P->d_rent, rent.data(), sizeof(long long) * row);
+    up(P->d_rbent, rbent.data(), sizeof(long long) * row);
+    up(P->d_cbound, cbound.data(), sizeof(int) * cb);
+    up(P->d_groups, groups.data(), sizeof(int2) * grp);
+    up(P->d_order, P->h_order.data(), sizeof(int) * n);
+    up(P->d_stage_off, P->stage_off.data(), sizeof(long long) * n);
+    up(P->d_stage_len, P->stage_len.data(), sizeof(long long) * n);
+    up(P->d_uoff, P->uoff.data(), sizeof(long long) * n);
+    upload_params(P, descs);
+    if (precision == NRTO_PREC_FP64) {
+      launch_setup<double>(P);
+      k_reset_outer<double><<<n, 128, 0, P->stream>>>(P->dev<double>(), 2.0);
+    } else {
+      launch_setup<float>(P);
+      k_reset_outer<float><<<n, 128, 0, P->stream>>>(P->dev<float>(), 2.0);
+    }
+    P->check_launch("k_reset_outer");
+    CK(cudaStreamSynchronize(P->stream));
+    *out = P;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    delete P;
+    return handle(e);
+  }
+}
+
+nrto_status nrto_problem_destroy(nrto_problem_t p) {
+  if (!p) return NRTO_OK;
+  cudaStreamSynchronize(p->stream);
+  delete p;
+  return NRTO_OK;
+}
+
+nrto_status nrto_problem_info(nrto_problem_t p, int i, nrto_instance_info* info) {
+  try {
+    if (!p || !info || i < 0 || i >= p->n) fail(NRTO_ERR_INVALID, "bad problem, instance or info");
+    const Inst& I = p->h_inst[i];
+    info->nx = I.nx; info->nu = I.nu; info->T = I.T;
+    info->n_rows = I.n_sr + I.n_cr; info->n_state_rows = I.n_sr; info->n_control_rows = I.n_cr;
+    info->n_entries = I.n_ent; info->n_entries_state = I.n_ent_state;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_problem_update(nrto_problem_t p, const nrto_problem_desc* descs, int n) {
+  try {
+    if (!p || !descs || n != p->n) fail(NRTO_ERR_INVALID, "update needs the same number of instances");
+    for (int i = 0; i < n; ++i) {
+      validate(descs[i], i);
+      const Inst& I = p->h_inst[i];
+      if (descs[i].dyn != I.kind || descs[i].T != I.T || descs[i].n_obs != I.n_obs || descs[i].n_link != I.n_link)
+        fail(NRTO_ERR_INVALID, "instance " + std::to_string(i) + ": structure differs from create");
+      std::vector<int4> sr, cr;
+      int rpt = 0;
+      build_rows(descs[i], sr, cr, rpt);
+      if ((int)sr.size() != I.n_sr || (int)cr.size() != I.n_cr) fail(NRTO_ERR_INVALID, "row structure differs from create");
+      if (descs[i].tau != I.tau || descs[i].dt != I.dt) fail(NRTO_ERR_INVALID, "dt/tau differ from create");
+    }
+    upload_params(p, descs);
+    if (p->prec == NRTO_PREC_FP64) launch_setup<double>(p); else launch_setup<float>(p);
+    p->linearized = false;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_linearize(nrto_problem_t p, const double* u_hat) {
+  try {
+    if (!p) fail(NRTO_ERR_INVALID, "null problem");
+    if (u_hat) {
+      if (!finite_arr(u_hat, p->u_total)) fail(NRTO_ERR_NUMERIC, "u_hat not finite");
+      std::vector<int> is(p->n * NIS);
+      CK(cudaMemcpyAsync(is.data(), p->d_is, sizeof(int) * is.size(), cudaMemcpyDeviceToHost, p->stream));
+      CK(cudaStreamSynchronize(p->stream));
+      for (int i = 0; i < p->n; ++i) {
+        const Inst& I = p->h_inst[i];
+        const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+        CK(cudaMemcpyAsync(p->d_slot_arena[is[i * NIS + IS_SLOT]] + I.slot0 + SL.u_hat, u_hat + p->uoff[i],
+                           sizeof(double) * I.T * I.nu, cudaMemcpyHostToDevice, p->stream));
+      }
+      CK(cudaStreamSynchronize(p->stream));
+    }
+    if (p->prec == NRTO_PREC_FP64) launch_linearize<double>(p, -1); else launch_linearize<float>(p, -1);
+    p->linearized = true;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_set_trust_radius(nrto_problem_t p, const double* r) {
+  try {
+    if (!p || !r) fail(NRTO_ERR_INVALID, "null argument");
+    std::vector<double> sc(p->n * NSC);
+    CK(cudaMemcpyAsync(sc.data(), p->d_sc, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    for (int i = 0; i < p->n; ++i) {
+      if (!(r[i] > 0) || !std::isfinite(r[i])) fail(NRTO_ERR_INVALID, "trust radius must be positive");
+      sc[i * NSC + SC_RTRUST] = r[i];
+    }
+    CK(cudaMemcpyAsync(p->d_sc, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_solve_socp(nrto_problem_t p, const nrto_solver_opts* o, nrto_socp_out* out) {
+  try {
+    if (!p) fail(NRTO_ERR_INVALID, "null problem");
+    check_opts(o);
+    if (!p->linearized) fail(NRTO_ERR_STATE, "nrto_linearize must be called before nrto_solve_socp");
+    if (p->prec == NRTO_PREC_FP64) launch_solve<double>(p, *o); else launch_solve<float>(p, *o);
+    if (out) return finish_statuses(p, o, out);
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_outer_step(nrto_problem_t p, const nrto_solver_opts* o, int* accepted) {
+  try {
+    if (!p) fail(NRTO_ERR_INVALID, "null problem");
+    check_opts(o);
+    if (!p->linearized) fail(NRTO_ERR_STATE, "nrto_linearize must be called before nrto_outer_step");
+    if (p->prec == NRTO_PREC_FP64) launch_outer_step<double>(p, *o); else launch_outer_step<float>(p, *o);
+    if (accepted) {
+      std::vector<int> is(p->n * NIS);
+      CK(cudaMemcpyAsync(is.data(), p->d_is, sizeof(int) * is.size(), cudaMemcpyDeviceToHost, p->stream));
+      CK(cudaStreamSynchronize(p->stream));
+      for (int i = 0; i < p->n; ++i) accepted[i] = is[i * NIS + IS_ACCEPT];
+    }
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_solve(nrto_problem_t p, const nrto_solver_opts* o, int n_outer, double* u_bar, double* K,
+                       double* merit) {
+  try {
+    if (!p) fail(NRTO_ERR_INVALID, "null problem");
+    check_opts(o);
+    if (n_outer < 0) fail(NRTO_ERR_INVALID, "n_outer < 0");
+    const bool f64 = p->prec == NRTO_PREC_FP64;
+    if (f64) k_reset_outer<double><<<p->n, 128, 0, p->stream>>>(p->dev<double>(), o->r0);
+    else k_reset_outer<float><<<p->n, 128, 0, p->stream>>>(p->dev<float>(), o->r0);
+    p->check_launch("k_reset_outer");
+    k_scatter_uhat<<<p->n, 128, 0, p->stream>>>(p->d_slot_arena[0], p->d_inst, p->d_ustage, p->d_uoff, p->n);
+    p->check_launch("k_scatter_uhat");
+    if (f64) { launch_linearize<double>(p, -1); launch_merit_current<double>(p, o->w_p); }
+    else { launch_linearize<float>(p, -1); launch_merit_current<float>(p, o->w_p); }
+    p->linearized = true;
+    for (int it = 0; it < n_outer; ++it) {
+      if (f64) launch_outer_step<double>(p, *o); else launch_outer_step<float>(p, *o);
+    }
+    if (u_bar) copy_arena_field(p, 1, off_uhat, u_bar, cnt_u);
+    if (K) copy_arena_field(p, 0, off_kacc, K, cnt_k);
+    if (merit) {
+      std::vector<double> sc(p->n * NSC);
+      CK(cudaMemcpyAsync(sc.data(), p->d_sc, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
+      CK(cudaStreamSynchronize(p->stream));
+      for (int i = 0; i < p->n; ++i) merit[i] = sc[i * NSC + SC_PHI];
+    }
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_set_warm_start(nrto_problem_t p, const double* K, const double* ptilde, const double* lambda_p) {
+  try {
+    if (!p || !K || !ptilde || !lambda_p) fail(NRTO_ERR_INVALID, "null argument");
+    long long o = 0;
+    for (int i = 0; i < p->n; ++i) {
+      const Inst& I = p->h_inst[i];
+      const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+      const long long cnt = (long long)I.T * I.nu * I.nx;
+      if (!finite_arr(K + o, cnt)) fail(NRTO_ERR_NUMERIC, "warm-start K not finite");
+      CK(cudaMemcpyAsync(p->d_arena + I.arena0 + L.K1, K + o, sizeof(double) * cnt, cudaMemcpyHostToDevice, p->stream));
+      o += cnt;
+    }
+    if (!finite_arr(ptilde, p->n_rows) || !finite_arr(lambda_p, p->n_rows)) fail(NRTO_ERR_NUMERIC, "warm start not finite");
+    CK(cudaMemcpyAsync(p->d_pt, ptilde, sizeof(double) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->d_lamp, lambda_p, sizeof(double) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    p->warm_pending = true;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_export(nrto_problem_t p, int field, int i, double* dst, long long count) {
+  return exchange(p, field, i, dst, count, true);
+}
+
+nrto_status nrto_import(nrto_problem_t p, int field, int i, const double* src, long long count) {
+  return exchange(p, field, i, const_cast<double*>(src), count, false);
+}
+
+nrto_status nrto_profile(nrto_problem_t p, int enable, double* solver_ms, long long* solver_launches) {
+  try {
+    if (!p) fail(NRTO_ERR_INVALID, "null problem");
+    double ms = 0.0;
+    if (!p->prof_events.empty()) {
+      CK(cudaStreamSynchronize(p->stream));
+      for (auto& ev : p->prof_events) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ev.first, ev.second));
+        ms += t;
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+      }
+    }
+    if (solver_ms) *solver_ms = ms;
+    if (solver_launches) *solver_launches = p->prof_launches;
+    p->prof_events.clear();
+    p->prof_launches = 0;
+    p->profiling = enable != 0;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+long long nrto_kernel_launches(nrto_problem_t p) { return p ? p->launches : -1; }
+
+}  // extern "C"
+
+template <typename Real>
+void launch_dr(nrto_problem* P, const nrto_solver_opts& o, SolveParams sp) {
+  (void)P; (void)o; (void)sp;
+  fail(NRTO_ERR_INVALID, "NRTO-DR solver not available in this build");
+}

@@ -1,0 +1,418 @@
+// Linearization prologue kernels (once per outer step) and per-solve factor kernels.
+//
+// Problem 2 data (Supplementary Sec. I) without dense matrices: for a state constraint j at
+// time t with a_j = ∇g_j(x̂_t), the adjoint vectors v_t = a_j, v_i = A_iᵀ v_{i+1} give
+//   b_{j,i} = (F_uᵀ a_j)_i = B_iᵀ v_{i+1}      and      b̂_{j,i} = √τ Ψ_i v_i      (i <= t),
+// because F_u's block (t,i) is A_{t-1}⋯A_{i+1}B_i and F_ζ's block (t,m) is A_{t-1}⋯A_m.
+// Control bounds have b_{j,k} = ±e_i and b̂_j = 0.
+#pragma once
+#include "dynamics.cuh"
+
+namespace nrto {
+
+// Slot selector of the linearization kernels: >= 0 a fixed slot, -1 the instance's current slot,
+// -2 its candidate slot (the other one).
+__device__ __forceinline__ int resolve_slot(const int* is, int i, int sel) {
+  const int cur = is[i * NIS + IS_SLOT];
+  return sel >= 0 ? sel : (sel == -1 ? cur : 1 - cur);
+}
+
+__device__ __forceinline__ long long kbuf_off(const Arena& L, int kbuf) {
+  return kbuf == 0 ? L.K0 : (kbuf == 1 ? L.K1 : (kbuf == 2 ? L.Kt : L.Kacc));
+}
+
+// Ψ_m = L_mᵀ (L_m L_mᵀ = Σ_m), Σ_m = U_m diag(λ_m) U_mᵀ, Φ_m = Ψ_m U_m.  Block per instance.
+template <typename Real>
+__global__ void k_setup(Dev<Real> D) {
+  const int i = blockIdx.x;
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  double* ar = D.arena + I.arena0;
+  const int nx = I.nx;
+  for (int m = threadIdx.x; m <= I.T; m += blockDim.x) {
+    double S[196], V[196], lam[14], C[196];
+    for (int k = 0; k < nx * nx; ++k) { S[k] = ar[L.Sigma + (long long)m * nx * nx + k]; C[k] = S[k]; }
+    chol_inplace(C, nx);
+    double* Psi = ar + L.Psi + (long long)m * nx * nx;
+    for (int r = 0; r < nx; ++r)
+      for (int c = 0; c < nx; ++c) Psi[r * nx + c] = C[c * nx + r];   // Ψ = Lᵀ (upper triangular)
+    jacobi_eig(S, nx, lam, V);
+    double* U = ar + L.SigU + (long long)m * nx * nx;
+    for (int k = 0; k < nx * nx; ++k) U[k] = V[k];
+    for (int k = 0; k < nx; ++k) ar[L.SigL + (long long)m * nx + k] = lam[k];
+    double* Phi = ar + L.Phi + (long long)m * nx * nx;
+    for (int r = 0; r < nx; ++r)
+      for (int c = 0; c < nx; ++c) {
+        double acc = 0.0;
+        for (int k = 0; k < nx; ++k) acc += Psi[r * nx + k] * V[k * nx + c];
+        Phi[r * nx + c] = acc;
+      }
+  }
+}
+
+// Nominal rollout x̂ (thread 0, sequential) then A_k, B_k in parallel.  Block per instance.
+template <typename Real>
+__global__ void k_rollout_jac(Dev<Real> D, int slot_sel) {
+  const int i = blockIdx.x;
+  const int slot = resolve_slot(D.is, i, slot_sel);
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  const double* ar = D.arena + I.arena0;
+  double* sa = D.slot[slot].arena + I.slot0;
+  const int nx = I.nx, nu = I.nu;
+  if (threadIdx.x == 0) {
+    double* x = sa + SL.x_hat;
+    for (int c = 0; c < nx; ++c) x[c] = ar[L.x0 + c];
+    for (int k = 0; k < I.T; ++k)
+      dyn_step(I.kind, ar + L.dyn, I.dt, x + (long long)k * nx, sa + SL.u_hat + (long long)k * nu,
+               x + (long long)(k + 1) * nx, nullptr, nullptr);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < I.T; k += blockDim.x) {
+    double xn[14];
+    dyn_step(I.kind, ar + L.dyn, I.dt, sa + SL.x_hat + (long long)k * nx, sa + SL.u_hat + (long long)k * nu, xn,
+             sa + SL.A + (long long)k * nx * nx, sa + SL.B + (long long)k * nx * nu);
+  }
+}
+
+// g_j(x̂) and ∇g_j for every state row; g for control rows.  Block per instance.
+template <typename Real>
+__global__ void k_rows(Dev<Real> D, int slot_sel) {
+  const int i = blockIdx.x;
+  const int slot = resolve_slot(D.is, i, slot_sel);
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  const double* ar = D.arena + I.arena0;
+  const double* sa = D.slot[slot].arena + I.slot0;
+  LinSlot<Real> S = D.slot[slot];
+  const int nx = I.nx, nu = I.nu;
+  for (int r = threadIdx.x; r < I.n_sr; r += blockDim.x) {
+    const long long R = I.row0 + r;
+    const int4 ri = D.rinfo[R];
+    double grad[14];
+    S.g0[R] = row_g_grad(I, ar, L, ri, sa + SL.x_hat + (long long)ri.x * nx, grad);
+    for (int c = 0; c < nx; ++c) S.arow[I.arow0 + (long long)r * nx + c] = grad[c];
+  }
+  for (int r = threadIdx.x; r < I.n_cr; r += blockDim.x) {
+    const long long R = I.row0 + I.n_sr + r;
+    const int4 ri = D.rinfo[R];
+    const double u = sa[SL.u_hat + (long long)ri.x * nu + ri.z];
+    S.g0[R] = (ri.y == ROW_UHI) ? (u - ar[L.uhi + ri.z]) : (ar[L.ulo + ri.z] - u);
+  }
+}
+
+// Adjoint sweep per state row, G lanes per row (G = 4 for nx <= 4, else 16).  Block per instance.
+template <typename Real>
+__global__ void k_adjoint(Dev<Real> D, int slot_sel) {
+  const int i = blockIdx.x;
+  const int slot = resolve_slot(D.is, i, slot_sel);
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  const double* ar = D.arena + I.arena0;
+  const double* sa = D.slot[slot].arena + I.slot0;
+  LinSlot<Real> S = D.slot[slot];
+  const int nx = I.nx, nu = I.nu;
+  const int G = (nx <= 4) ? 4 : 16;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % G;
+  const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - sub));
+  const double sq = I.sqrt_tau;
+  const double* A = sa + SL.A;
+  const double* B = sa + SL.B;
+  const double* Psi = ar + L.Psi;
+  for (int r = grp; r < I.n_sr; r += ngrp) {
+    const long long R = I.row0 + r;
+    const int t = D.rinfo[R].x;
+    const long long e0 = D.rent[R], b0 = D.rbent[R];
+    double v = (sub < nx) ? S.arow[I.arow0 + (long long)r * nx + sub] : 0.0;
+    // block t: b̂_t = √τ Ψ_t v_t, b_t = 0
+    {
+      double acc = 0.0;
+      for (int q = 0; q < nx; ++q) {
+        double vq = __shfl_sync(mask, v, q, G);
+        if (sub < nx) acc += Psi[(long long)t * nx * nx + sub * nx + q] * vq;
+      }
+      if (sub < nx) S.bhat[e0 + (long long)t * nx + sub] = (Real)(sq * acc);
+      if (sub < nu) S.bvec[b0 + (long long)t * nu + sub] = (Real)0.0;
+    }
+    for (int k = t - 1; k >= 0; --k) {
+      const double* Ak = A + (long long)k * nx * nx;
+      const double* Bk = B + (long long)k * nx * nu;
+      const double* Pk = Psi + (long long)k * nx * nx;
+      double bu = 0.0, vn = 0.0;
+      for (int q = 0; q < nx; ++q) {
+        double vq = __shfl_sync(mask, v, q, G);
+        if (sub < nu) bu += Bk[q * nu + sub] * vq;
+        if (sub < nx) vn += Ak[q * nx + sub] * vq;
+      }
+      v = vn;
+      double acc = 0.0;
+      for (int q = 0; q < nx; ++q) {
+        double vq = __shfl_sync(mask, v, q, G);
+        if (sub < nx) acc += Pk[sub * nx + q] * vq;
+      }
+      if (sub < nx) S.bhat[e0 + (long long)k * nx + sub] = (Real)(sq * acc);
+      if (sub < nu) S.bvec[b0 + (long long)k * nu + sub] = (Real)bu;
+    }
+  }
+}
+
+// G_m = Σ_j b_{j,m} b_{j,m}ᵀ over state rows (from the stored, possibly rounded b) plus e_ie_iᵀ per
+// control bound at step m.  Block per instance, thread per (m, u1, u2).
+template <typename Real>
+__global__ void k_gram(Dev<Real> D, int slot_sel) {
+  const int i = blockIdx.x;
+  const int slot = resolve_slot(D.is, i, slot_sel);
+  const Inst I = D.inst[i];
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  double* sa = D.slot[slot].arena + I.slot0;
+  const Real* bv = D.slot[slot].bvec;
+  const int nu = I.nu;
+  const int total = I.T * nu * nu;
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    const int m = q / (nu * nu), u1 = (q / nu) % nu, u2 = q % nu;
+    double acc = 0.0;
+    // state rows with t > m start at local row m·rows_per_t (rows are ordered by t = 1..T)
+    for (int r = m * I.rows_per_t; r < I.n_sr; ++r) {
+      const long long b0 = D.rbent[I.row0 + r] + (long long)m * nu;
+      acc += (double)bv[b0 + u1] * (double)bv[b0 + u2];
+    }
+    if (u1 == u2 && I.n_groups > 0) {
+      const int gpk = I.n_groups / I.T;   // control groups are ordered by step, gpk per step
+      for (int g = m * gpk; g < (m + 1) * gpk; ++g) {
+        const int2 gr = D.groups[I.grp0 + g];
+        if (D.rinfo[gr.x].z == u1) acc += (double)gr.y;
+      }
+    }
+    sa[SL.Gm + q] = acc;
+  }
+}
+
+// Gain-solve factors for H_m = I⊗(2W + shift·I) + coef·τ Σ_m⊗G_m (W = R_KᵀR_K):
+// with a = (2W+shift)^{-1/2}, a G_m a = V diag(γ) Vᵀ:  Pf_m = a V,  Dv_m[u][c] = 1/(1 + coef τ γ_u λ_c).
+// Then H_m vec(K) = vec(R) is solved by K = Pf X U_mᵀ with X = (Pfᵀ R U_m) ⊙ Dv.  Thread per (inst, m).
+template <typename Real>
+__global__ void k_gain_factors(Dev<Real> D, double coef, double shift) {
+  const int i = blockIdx.x;
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  double* ar = D.arena + I.arena0;
+  const int sl = D.is[i * NIS + IS_SLOT];
+  const double* sa = D.slot[sl].arena + I.slot0;
+  const int nx = I.nx, nu = I.nu;
+  for (int m = threadIdx.x; m < I.T; m += blockDim.x) {
+    double a[7], G[49], V[49], gam[7];
+    for (int u = 0; u < nu; ++u) a[u] = 1.0 / sqrt(2.0 * ar[L.RK + u] * ar[L.RK + u] + shift);
+    for (int u = 0; u < nu; ++u)
+      for (int v = 0; v < nu; ++v) G[u * nu + v] = a[u] * sa[SL.Gm + (long long)m * nu * nu + u * nu + v] * a[v];
+    jacobi_eig(G, nu, gam, V);
+    double* Pf = ar + L.Pf + (long long)m * nu * nu;
+    for (int u = 0; u < nu; ++u)
+      for (int v = 0; v < nu; ++v) Pf[u * nu + v] = a[u] * V[u * nu + v];
+    for (int u = 0; u < nu; ++u) ar[L.Gam + (long long)m * nu + u] = gam[u];
+    double* Dv = ar + L.Dv + (long long)m * nu * nx;
+    for (int u = 0; u < nu; ++u)
+      for (int c = 0; c < nx; ++c)
+        Dv[u * nx + c] = 1.0 / (1.0 + coef * I.tau * gam[u] * ar[L.SigL + (long long)m * nx + c]);
+  }
+}
+
+// warp-cooperative small matrix product C = op(A)·op(B) (row-major), lanes over outputs.
+__device__ inline void wmm(double* C, const double* A, bool tA, int lda, const double* B, bool tB, int ldb,
+                           int m, int n, int k, double alpha, bool accumulate) {
+  for (int q = threadIdx.x & 31; q < m * n; q += 32) {
+    int r = q / n, c = q % n;
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) {
+      double av = tA ? A[j * lda + r] : A[r * lda + j];
+      double bv = tB ? B[c * ldb + j] : B[j * ldb + c];
+      acc += av * bv;
+    }
+    C[r * n + c] = accumulate ? C[r * n + c] + alpha * acc : alpha * acc;
+  }
+  __syncwarp();
+}
+
+// Riccati factorization of the FullADMM Block-2 LQ problem (lifted reading): stage Hessians
+//   Q_t = 2Q_x + ρ I + (ρ/2) Σ_{state rows j at t} a_j a_jᵀ (t = 1..T),
+//   R_k = 2R_u + (ρ/2) Σ_{control rows j at k} e_i e_iᵀ,
+// dynamics δx_{k+1} = A_k δx_k + B_k δu_k, δx_0 = 0.  Stores per step
+//   L_k = -Huu⁻¹Hux, Acl_k = A_k + B_k L_k, N_k = Huu⁻¹, M_k = Huu⁻¹ B_kᵀ.
+// One warp per instance (block per instance, blockDim = 32).
+template <typename Real>
+__global__ void k_riccati_factor(Dev<Real> D, double rho) {
+  const int i = blockIdx.x;
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  double* ar = D.arena + I.arena0;
+  const int sl = D.is[i * NIS + IS_SLOT];
+  const double* sa = D.slot[sl].arena + I.slot0;
+  const double* arow = D.slot[sl].arow;
+  const int nx = I.nx, nu = I.nu;
+  const int lane = threadIdx.x & 31;
+  __shared__ double P[196], PA[196], PB[98], Huu[49], Hux[98], Nm[49], Lm[98], Q[196], tmp[196];
+  auto build_Q = [&](int t) {
+    for (int q = lane; q < nx * nx; q += 32) {
+      int r = q / nx, c = q % nx;
+      double v = (r == c) ? (2.0 * ar[L.Qx + r] + rho) : 0.0;
+      for (int s = 0; s < I.rows_per_t; ++s) {
+        long long rr = (long long)(t - 1) * I.rows_per_t + s;
+        v += 0.5 * rho * arow[I.arow0 + rr * nx + r] * arow[I.arow0 + rr * nx + c];
+      }
+      Q[q] = v;
+    }
+    __syncwarp();
+  };
+  build_Q(I.T);
+  for (int q = lane; q < nx * nx; q += 32) P[q] = Q[q];
+  __syncwarp();
+  for (int k = I.T - 1; k >= 0; --k) {
+    const double* Ak = sa + SL.A + (long long)k * nx * nx;
+    const double* Bk = sa + SL.B + (long long)k * nx * nu;
+    wmm(PA, P, false, nx, Ak, false, nx, nx, nx, nx, 1.0, false);
+    wmm(PB, P, false, nx, Bk, false, nu, nx, nu, nx, 1.0, false);
+    wmm(Huu, Bk, true, nu, PB, false, nu, nu, nu, nx, 1.0, false);
+    wmm(Hux, Bk, true, nu, PA, false, nx, nu, nx, nx, 1.0, false);
+    if (lane == 0) {
+      for (int u = 0; u < nu; ++u) Huu[u * nu + u] += 2.0 * ar[L.Ru + u];
+      if (I.n_groups > 0) {
+        const int gpk = I.n_groups / I.T;
+        for (int g = k * gpk; g < (k + 1) * gpk; ++g) {
+          const int2 gr = D.groups[I.grp0 + g];
+          const int iu = D.rinfo[gr.x].z;
+          Huu[iu * nu + iu] += 0.5 * rho * gr.y;
+        }
+      }
+      // N = Huu⁻¹ through Cholesky
+      double C[49];
+      for (int q = 0; q < nu * nu; ++q) C[q] = Huu[q];
+      chol_inplace(C, nu);
+      for (int col = 0; col < nu; ++col) {
+        double y[7];
+        for (int r = 0; r < nu; ++r) {
+          double v = (r == col) ? 1.0 : 0.0;
+          for (int s = 0; s < r; ++s) v -= C[r * nu + s] * y[s];
+          y[r] = v / C[r * nu + r];
+        }
+        for (int r = nu - 1; r >= 0; --r) {
+          double v = y[r];
+          for (int s = r + 1; s < nu; ++s) v -= C[s * nu + r] * y[s];
+          y[r] = v / C[r * nu + r];
+        }
+        for (int r = 0; r < nu; ++r) Nm[r * nu + col] = y[r];
+      }
+    }
+    __syncwarp();
+    wmm(Lm, Nm, false, nu, Hux, false, nx, nu, nx, nu, -1.0, false);
+    double* gL = ar + L.RicL + (long long)k * nu * nx;
+    double* gAcl = ar + L.RicAcl + (long long)k * nx * nx;
+    double* gN = ar + L.RicN + (long long)k * nu * nu;
+    double* gM = ar + L.RicM + (long long)k * nu * nx;
+    for (int q = lane; q < nu * nx; q += 32) gL[q] = Lm[q];
+    for (int q = lane; q < nu * nu; q += 32) gN[q] = Nm[q];
+    wmm(gM, Nm, false, nu, Bk, true, nu, nu, nx, nu, 1.0, false);
+    for (int q = lane; q < nx * nx; q += 32) gAcl[q] = Ak[q];
+    __syncwarp();
+    wmm(gAcl, Bk, false, nu, Lm, false, nx, nx, nx, nu, 1.0, true);
+    if (k >= 1) {
+      build_Q(k);
+      wmm(tmp, Ak, true, nx, PA, false, nx, nx, nx, nx, 1.0, false);        // AᵀPA
+      wmm(tmp, Hux, true, nx, Lm, false, nx, nx, nx, nu, 1.0, true);        // + HuxᵀL
+      for (int q = lane; q < nx * nx; q += 32) {
+        int r = q / nx, c = q % nx;
+        P[q] = Q[q] + 0.5 * (tmp[r * nx + c] + tmp[c * nx + r]);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Gtᵀ_m = √τ K_m Ψ_mᵀ (nu×nx) for every step from a gain buffer; Gt_T = 0.  Block per instance.
+template <typename Real>
+__global__ void k_gain_to_gt(Dev<Real> D, int kbuf, int gtbuf) {
+  const int i = blockIdx.x;
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  double* ar = D.arena + I.arena0;
+  const int nx = I.nx, nu = I.nu;
+  const double* K = ar + kbuf_off(L, kbuf);
+  double* Gt = ar + (gtbuf == 0 ? L.Gt0 : L.Gt1);
+  const int total = (I.T + 1) * nu * nx;
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    int m = q / (nu * nx), u = (q / nx) % nu, c = q % nx;
+    double acc = 0.0;
+    if (m < I.T)
+      for (int r = 0; r < nx; ++r)
+        acc += K[(long long)m * nu * nx + u * nx + r] * ar[L.Psi + (long long)m * nx * nx + c * nx + r];
+    Gt[q] = I.sqrt_tau * acc;
+  }
+}
+
+// Merit of Problem 1 at the nominal of the selected slot with the gains in `kbuf` (Gtᵀ in `gtbuf`):
+// φ = Σ_k (ū_k-u_ref)ᵀR_u(·) + Σ_{t≥1}(x̄_t-x_goal)ᵀQ_x(·) + Σ_k‖R_K K_k‖_F²
+//     + w_p Σ_j max(0, g_j(x̄) + ‖Â_j k_v + b̂_j‖).
+// Block per instance; writes sc[out_idx] and the cost to sc[SC_COST].
+template <typename Real>
+__global__ void k_merit(Dev<Real> D, int slot_sel, int kbuf, int gtbuf, double w_p, int out_idx) {
+  const int i = blockIdx.x;
+  const int slot = resolve_slot(D.is, i, slot_sel);
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  const double* ar = D.arena + I.arena0;
+  const double* sa = D.slot[slot].arena + I.slot0;
+  const LinSlot<Real> S = D.slot[slot];
+  const int nx = I.nx, nu = I.nu;
+  const double* Gt = ar + (gtbuf == 0 ? L.Gt0 : L.Gt1);
+  const double* K = ar + kbuf_off(L, kbuf);
+  __shared__ double red[4 * 32];
+  double cst = 0.0, vio = 0.0, z0 = 0.0, z1 = 0.0;
+  for (int q = threadIdx.x; q < I.T * nu; q += blockDim.x) {
+    double d = sa[SL.u_hat + q] - ar[L.uref + q % nu];
+    cst += ar[L.Ru + q % nu] * d * d;
+  }
+  for (int q = threadIdx.x; q < I.T * nx; q += blockDim.x) {
+    double d = sa[SL.x_hat + nx + q] - ar[L.xg + q % nx];
+    cst += ar[L.Qx + q % nx] * d * d;
+  }
+  for (int q = threadIdx.x; q < I.T * nu * nx; q += blockDim.x) {
+    double kv = K[q] * ar[L.RK + (q / nx) % nu];
+    cst += kv * kv;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = wid; r < I.n_sr + I.n_cr; r += nw) {
+    const long long R = I.row0 + r;
+    const int4 ri = D.rinfo[R];
+    double n2 = 0.0;
+    if (r < I.n_sr) {
+      const long long e0 = D.rent[R], b0 = D.rbent[R];
+      const int len = (ri.x + 1) * nx;
+      for (int e = lane; e < len; e += 32) {
+        int m = e / nx, c = e % nx;
+        double y = (double)S.bhat[e0 + e];
+        for (int u = 0; u < nu; ++u) y += Gt[(long long)m * nu * nx + u * nx + c] * (double)S.bvec[b0 + (long long)m * nu + u];
+        n2 += y * y;
+      }
+    } else {
+      for (int c = lane; c < nx; c += 32) {
+        double y = Gt[(long long)ri.x * nu * nx + ri.z * nx + c];
+        n2 += y * y;
+      }
+    }
+    n2 = warp_sum(n2);
+    if (lane == 0) vio += fmax(0.0, S.g0[R] + sqrt(n2));
+  }
+  block_sum4(cst, vio, z0, z1, red);
+  if (threadIdx.x == 0) {
+    D.sc[i * NSC + out_idx] = cst + w_p * vio;
+    D.sc[i * NSC + SC_COST] = cst;
+  }
+}
+
+}  // namespace nrto

@@ -1,0 +1,221 @@
+// Device-side data layout and helpers of libnrto (NRTO inner loop on sm_103a).
+//
+// Storage model (one problem = a batch of independent instances):
+//  * per-instance "arena" of doubles (parameters, per-step matrices, gains, solver vectors);
+//  * two linearization "slots" (current nominal and candidate nominal of the outer loop), each
+//    holding per-instance slot arenas (û, x̂, A_k, B_k, G_m) and the ragged row arrays;
+//  * ragged row arrays in the compute precision `Real`: for a state constraint at time t the row
+//    holds ζ-blocks 0..t ((t+1)·nx entries; a state constraint at t only sees the disturbances up
+//    to t); a control bound holds one block (nx entries).
+//      lam  : λ_ν (FullADMM) or η̃ (DR)          entries
+//      bhat : b̂_j                                 entries (state rows)
+//      bvec : b_{j,m}, nu values per block          (t+1)·nu per state row (block t is zero)
+//  * per-row scalars in double (p, p̃, λ_p, lifted slack w, λ_w, projection scale s, ...).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#ifndef NRTO_HD
+#define NRTO_HD __host__ __device__ __forceinline__
+#endif
+
+namespace nrto {
+
+enum : int { KIND_UNICYCLE = 0, KIND_QUADCOPTER = 1, KIND_ARM = 2 };
+// row codes (int4.y of the row table)
+enum : int { ROW_SPHERE = 0, ROW_XHI = 1, ROW_XLO = 2, ROW_UHI = 3, ROW_ULO = 4 };
+// instance status
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NUMERIC = 3 };
+
+constexpr int MAX_DYN = 24;
+
+// Per-instance metadata (host builds it at create time).
+struct Inst {
+  int kind, nx, nu, T;
+  int n_sr, n_cr, rows_per_t, n_groups;   // state rows, control rows, state rows per step, (k,i) groups
+  int n_obs, obs_dim, n_link, n_dyn;
+  int cb0, n_chunks;                      // chunk boundary table offset, number of chunks
+  int pad0;
+  long long row0;                         // first global row (state rows, then control rows)
+  long long ent0;                         // first entry of the instance's rows
+  long long n_ent;                        // entries of the instance (state + control rows)
+  long long n_ent_state;                  // entries of the state rows
+  long long bent0;                        // first bvec value
+  long long grp0;                         // first control group
+  long long arena0;                       // offset into the double arena
+  long long slot0;                        // offset into each slot arena
+  long long arow0;                        // offset into the a_j table (nx per state row)
+  double dt, tau, sqrt_tau;
+};
+
+// Offsets (in doubles) inside one instance's arena.
+struct Arena {
+  long long x0, xg, uref, Qx, Ru, RK, ulo, uhi, xlo, xhi, dyn, obs, link, Sigma;
+  long long Psi, SigU, SigL, Phi;
+  long long K0, K1, Kt, Kacc, Gt0, Gt1, Zp;
+  long long du, dx, du_prev, dx_prev, e, lam_e, qv, rv;
+  long long Pf, Gam, Dv, RicL, RicAcl, RicN, RicM;
+  long long total;
+};
+
+NRTO_HD Arena arena_layout(int nx, int nu, int T, int n_obs, int n_link) {
+  Arena a;
+  long long o = 0;
+  auto take = [&](long long n) { long long r = o; o += (n + 1) & ~1LL; return r; };
+  a.x0 = take(nx); a.xg = take(nx); a.uref = take(nu); a.Qx = take(nx); a.Ru = take(nu); a.RK = take(nu);
+  a.ulo = take(nu); a.uhi = take(nu); a.xlo = take(nx); a.xhi = take(nx); a.dyn = take(MAX_DYN);
+  a.obs = take(4LL * (n_obs > 0 ? n_obs : 1)); a.link = take(5LL * (n_link > 0 ? n_link : 1));
+  long long s1 = (long long)(T + 1);
+  a.Sigma = take(s1 * nx * nx); a.Psi = take(s1 * nx * nx); a.SigU = take(s1 * nx * nx);
+  a.SigL = take(s1 * nx); a.Phi = take(s1 * nx * nx);
+  long long g = (long long)T * nu * nx;
+  a.K0 = take(g); a.K1 = take(g); a.Kt = take(g); a.Kacc = take(g);
+  a.Gt0 = take(s1 * nu * nx); a.Gt1 = take(s1 * nu * nx); a.Zp = take(g);
+  a.du = take((long long)T * nu); a.dx = take(s1 * nx); a.du_prev = take((long long)T * nu);
+  a.dx_prev = take(s1 * nx); a.e = take(s1 * nx); a.lam_e = take(s1 * nx); a.qv = take(s1 * nx);
+  a.rv = take((long long)T * nu);
+  a.Pf = take((long long)T * nu * nu); a.Gam = take((long long)T * nu); a.Dv = take(g);
+  a.RicL = take(g); a.RicAcl = take((long long)T * nx * nx); a.RicN = take((long long)T * nu * nu);
+  a.RicM = take(g);
+  a.total = o;
+  return a;
+}
+
+// Offsets (in doubles) inside one instance's slot arena (one per linearization slot).
+struct SlotL {
+  long long u_hat, x_hat, A, B, Gm, total;
+};
+
+NRTO_HD SlotL slot_layout(int nx, int nu, int T) {
+  SlotL s;
+  long long o = 0;
+  auto take = [&](long long n) { long long r = o; o += (n + 1) & ~1LL; return r; };
+  s.u_hat = take((long long)T * nu);
+  s.x_hat = take((long long)(T + 1) * nx);
+  s.A = take((long long)T * nx * nx);
+  s.B = take((long long)T * nx * nu);
+  s.Gm = take((long long)T * nu * nu);
+  s.total = o;
+  return s;
+}
+
+// Per-instance scalar record (double) and integer record.
+enum : int { SC_RTRUST = 0, SC_RP, SC_RD, SC_RPP, SC_RDP, SC_SCAL_RP, SC_SCAL_RD, SC_SCAL_RPP, SC_SCAL_RDP,
+             SC_PHI, SC_PHI_CAND, SC_COST, SC_ENORM, SC_RDR, NSC = 16 };
+enum : int { IS_STATUS = 0, IS_ITERS, IS_SLOT, IS_ACCEPT, IS_DRITERS, IS_CUMITERS, IS_NACC, NIS = 8 };
+
+template <typename Real>
+struct LinSlot {
+  double* arena;     // slot arenas (per instance at Inst::slot0)
+  double* g0;        // per row g_j(x̂) (control rows: ±û - bound)
+  double* arow;      // ∇g_j (nx per state row)
+  Real* bhat;        // per entry
+  Real* bvec;        // per state-row block, nu values
+};
+
+template <typename Real>
+struct Dev {
+  int n_inst;
+  const Inst* inst;
+  double* arena;
+  const int4* rinfo;            // per row: {t or k, code, a, b}
+  const long long* rent;        // per row: first entry
+  const long long* rbent;       // per state row: first bvec value (global row index)
+  const int* cbound;            // chunk boundaries (local state-row indices), n_chunks+1 per instance
+  const int2* groups;           // control groups: {first global row, count}, per instance at grp0
+  LinSlot<Real> slot[2];
+  Real* lam;                    // λ_ν or η̃ rows
+  double *p, *pt, *ptn, *lamp, *w, *lamw, *s, *ell, *dd, *rnorm;   // per row
+  double* sc;                   // NSC per instance
+  int* is;                      // NIS per instance
+  int* queue;                   // work counters
+  const int* order;             // instance order per launch
+};
+
+// ------------------------------------------------------------------------------------------
+// warp helpers
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of up to 4 doubles; `red` is shared scratch of >= 4*(blockDim/32) doubles.
+// All threads get the result.  Deterministic (fixed tree).
+__device__ inline void block_sum4(double& a, double& b, double& c, double& d, double* red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum(a); b = warp_sum(b); c = warp_sum(c); d = warp_sum(d);
+  __syncthreads();
+  if (lane == 0) { red[4 * wid] = a; red[4 * wid + 1] = b; red[4 * wid + 2] = c; red[4 * wid + 3] = d; }
+  __syncthreads();
+  a = b = c = d = 0.0;
+  for (int i = 0; i < nw; ++i) { a += red[4 * i]; b += red[4 * i + 1]; c += red[4 * i + 2]; d += red[4 * i + 3]; }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// small dense linear algebra (row-major, sequential; used by single threads on tiny matrices)
+// ------------------------------------------------------------------------------------------
+// In-place Cholesky A = L Lᵀ (lower); returns false if not positive definite.
+NRTO_HD bool chol_inplace(double* A, int n) {
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
+    if (!(d > 0.0)) return false;
+    d = sqrt(d);
+    A[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double v = A[i * n + j];
+      for (int k = 0; k < j; ++k) v -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = v / d;
+    }
+    for (int i = 0; i < j; ++i) A[i * n + j] = 0.0;
+  }
+  return true;
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n×n matrix (n <= 16).
+// On return A is overwritten, lam holds eigenvalues, V (row-major) holds eigenvectors in columns.
+NRTO_HD void jacobi_eig(double* A, int n, double* lam, double* V) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double v = A[i * n + j] * A[i * n + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[p * n + q];
+        if (apq == 0.0) continue;
+        double app = A[p * n + p], aqq = A[q * n + q];
+        double theta = (aqq - app) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {   // A ← Jᵀ A J  (rotate columns p,q then rows p,q)
+          double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
+}
+
+}  // namespace nrto

@@ -1,0 +1,276 @@
+"""ctypes binding of libnrto (include/nrto.h).  Argument marshalling only: every step of the
+solver runs in the library's CUDA kernels.  `load()` raises if the shared library is missing;
+there is no CPU fallback."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnrto.so")
+
+PREC_FP64, PREC_MIXED = 0, 1
+SOLVER_DR, SOLVER_FULLADMM = 0, 1
+
+(F_XHAT, F_UHAT, F_A, F_B, F_G0, F_BHAT, F_BVEC, F_LAMNU, F_K, F_DU, F_P, F_PT, F_LAMP, F_GM, F_KACC,
+ F_DX, F_SCAL, F_STATS) = range(18)
+
+STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "NOT_CONVERGED", 4: "NUMERIC", 5: "TIMEOUT", 6: "STATE"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("dyn", C.c_int), ("nx", C.c_int), ("nu", C.c_int), ("T", C.c_int), ("dt", C.c_double),
+                ("dyn_params", _dp), ("n_dyn_params", C.c_int),
+                ("x0", _dp), ("x_goal", _dp), ("u_init", _dp), ("u_ref", _dp), ("Sigma", _dp),
+                ("tau", C.c_double), ("Qx", _dp), ("Ru", _dp), ("RK", _dp),
+                ("n_obs", C.c_int), ("obs_dim", C.c_int), ("obs_center", _dp), ("obs_radius", _dp),
+                ("n_link", C.c_int), ("link_spheres", _dp),
+                ("u_lo", _dp), ("u_hi", _dp), ("x_lo", _dp), ("x_hi", _dp)]
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("solver", C.c_int), ("rho", C.c_double), ("alpha", C.c_double), ("r_chi", C.c_double),
+                ("sigma", C.c_double), ("eps_p", C.c_double), ("eps_d", C.c_double), ("eps_dr", C.c_double),
+                ("max_inner", C.c_int), ("max_dr", C.c_int), ("check", C.c_int),
+                ("r0", C.c_double), ("r_min", C.c_double), ("w_p", C.c_double)]
+
+
+class InstanceInfo(C.Structure):
+    _fields_ = [("nx", C.c_int), ("nu", C.c_int), ("T", C.c_int), ("n_rows", C.c_int),
+                ("n_state_rows", C.c_int), ("n_control_rows", C.c_int),
+                ("n_entries", C.c_longlong), ("n_entries_state", C.c_longlong)]
+
+
+class SocpOut(C.Structure):
+    _fields_ = [("du", _dp), ("K", _dp), ("p", _dp), ("ptilde", _dp), ("iters", _ip),
+                ("r_p", _dp), ("r_d", _dp), ("status", _ip)]
+
+
+_LIB = None
+
+
+def load():
+    """Load libnrto.so (built by `paper_2603_02642_b300.build.build()`)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libnrto.so not found at {LIB_PATH}; run paper_2603_02642_b300/build.py")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    lib.nrto_problem_create.argtypes = [C.POINTER(ProblemDesc), C.c_int, C.c_int, C.c_void_p, C.POINTER(P)]
+    lib.nrto_problem_destroy.argtypes = [P]
+    lib.nrto_problem_info.argtypes = [P, C.c_int, C.POINTER(InstanceInfo)]
+    lib.nrto_problem_update.argtypes = [P, C.POINTER(ProblemDesc), C.c_int]
+    lib.nrto_linearize.argtypes = [P, _dp]
+    lib.nrto_set_trust_radius.argtypes = [P, _dp]
+    lib.nrto_solve_socp.argtypes = [P, C.POINTER(SolverOpts), C.POINTER(SocpOut)]
+    lib.nrto_outer_step.argtypes = [P, C.POINTER(SolverOpts), _ip]
+    lib.nrto_solve.argtypes = [P, C.POINTER(SolverOpts), C.c_int, _dp, _dp, _dp]
+    lib.nrto_set_warm_start.argtypes = [P, _dp, _dp, _dp]
+    lib.nrto_export.argtypes = [P, C.c_int, C.c_int, _dp, C.c_longlong]
+    lib.nrto_import.argtypes = [P, C.c_int, C.c_int, _dp, C.c_longlong]
+    lib.nrto_profile.argtypes = [P, C.c_int, _dp, C.POINTER(C.c_longlong)]
+    lib.nrto_kernel_launches.argtypes = [P]
+    lib.nrto_kernel_launches.restype = C.c_longlong
+    lib.nrto_last_error.restype = C.c_char_p
+    for name in ["nrto_problem_create", "nrto_problem_destroy", "nrto_problem_info", "nrto_problem_update",
+                 "nrto_linearize", "nrto_set_trust_radius", "nrto_solve_socp", "nrto_outer_step", "nrto_solve",
+                 "nrto_set_warm_start", "nrto_export", "nrto_import", "nrto_profile"]:
+        getattr(lib, name).restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+class NrtoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code, allow=()):
+    if code != 0 and code not in allow:
+        raise NrtoError(code, load().nrto_last_error().decode())
+    return code
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+@dataclass
+class Options:
+    solver: int = SOLVER_FULLADMM
+    rho: float = 10.0
+    alpha: float = 0.9
+    r_chi: float = 1.0
+    sigma: float = 1.0
+    eps_p: float = 1e-4
+    eps_d: float = 1e-4
+    eps_dr: float = 1e-4
+    max_inner: int = 500
+    max_dr: int = 500
+    check: int = 1
+    r0: float = 2.0
+    r_min: float = 1e-3
+    w_p: float = 10.0
+
+    def c(self) -> SolverOpts:
+        return SolverOpts(self.solver, self.rho, self.alpha, self.r_chi, self.sigma, self.eps_p, self.eps_d,
+                          self.eps_dr, self.max_inner, self.max_dr, self.check, self.r0, self.r_min, self.w_p)
+
+
+def _desc(inst, keep):
+    def arr(a):
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+        keep.append(a)
+        return a
+    is_arm = inst.kind == 2
+    return ProblemDesc(
+        dyn=inst.kind, nx=inst.nx, nu=inst.nu, T=inst.T, dt=inst.dt,
+        dyn_params=_ptr(arr(inst.dyn_params if inst.dyn_params.size else np.zeros(1))),
+        n_dyn_params=int(inst.dyn_params.size),
+        x0=_ptr(arr(inst.x0)), x_goal=_ptr(arr(inst.x_goal)), u_init=_ptr(arr(inst.u_init)),
+        u_ref=_ptr(arr(inst.u_ref)), Sigma=_ptr(arr(inst.Sigma)), tau=inst.tau,
+        Qx=_ptr(arr(inst.Qx)), Ru=_ptr(arr(inst.Ru)), RK=_ptr(arr(inst.RK)),
+        n_obs=inst.n_obs, obs_dim=inst.obs_dim,
+        obs_center=_ptr(arr(inst.obs_center if inst.n_obs else np.zeros(1))),
+        obs_radius=_ptr(arr(inst.obs_radius if inst.n_obs else np.zeros(1))),
+        n_link=int(inst.link_spheres.shape[0]) if is_arm else 0,
+        link_spheres=_ptr(arr(inst.link_spheres if is_arm and inst.link_spheres.size else np.zeros(5))),
+        u_lo=_ptr(arr(inst.u_lo)), u_hi=_ptr(arr(inst.u_hi)), x_lo=_ptr(arr(inst.x_lo)), x_hi=_ptr(arr(inst.x_hi)))
+
+
+class Problem:
+    """A batch of robust trajectory problems resident on the GPU."""
+
+    _COUNTS = {
+        F_XHAT: lambda x: (x.T + 1) * x.nx, F_DX: lambda x: (x.T + 1) * x.nx, F_UHAT: lambda x: x.T * x.nu,
+        F_DU: lambda x: x.T * x.nu, F_A: lambda x: x.T * x.nx * x.nx, F_B: lambda x: x.T * x.nx * x.nu,
+        F_G0: lambda x: x.n_rows, F_P: lambda x: x.n_rows, F_PT: lambda x: x.n_rows, F_LAMP: lambda x: x.n_rows,
+        F_BHAT: lambda x: x.n_entries_state, F_BVEC: lambda x: x.n_entries_state // x.nx * x.nu,
+        F_LAMNU: lambda x: x.n_entries, F_K: lambda x: x.T * x.nu * x.nx, F_KACC: lambda x: x.T * x.nu * x.nx,
+        F_GM: lambda x: x.T * x.nu * x.nu, F_SCAL: lambda x: 8, F_STATS: lambda x: 4,
+    }
+
+    def __init__(self, instances, precision=PREC_FP64, stream=None):
+        lib = load()
+        self.instances = list(instances)
+        self.n = len(self.instances)
+        keep = []
+        descs = (ProblemDesc * self.n)(*[_desc(x, keep) for x in self.instances])
+        h = C.c_void_p()
+        _check(lib.nrto_problem_create(descs, self.n, precision, C.c_void_p(stream), C.byref(h)))
+        self._h = h
+        self.precision = precision
+        self.info = []
+        for i in range(self.n):
+            inf = InstanceInfo()
+            _check(lib.nrto_problem_info(h, i, C.byref(inf)))
+            self.info.append(inf)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().nrto_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n_rows(self, i=None):
+        return self.info[i].n_rows if i is not None else sum(x.n_rows for x in self.info)
+
+    def _cat(self, per):
+        return int(sum(per(x) for x in self.info))
+
+    def _split(self, flat, shape):
+        out, o = [], 0
+        for x in self.info:
+            s = shape(x)
+            n = int(np.prod(s))
+            out.append(flat[o:o + n].reshape(s))
+            o += n
+        return out
+
+    def update(self, instances):
+        keep = []
+        descs = (ProblemDesc * self.n)(*[_desc(x, keep) for x in instances])
+        _check(load().nrto_problem_update(self._h, descs, self.n))
+
+    def linearize(self, u_hat=None):
+        u = None if u_hat is None else np.ascontiguousarray(np.concatenate([np.asarray(x).reshape(-1) for x in u_hat]))
+        _check(load().nrto_linearize(self._h, _ptr(u)))
+
+    def set_trust_radius(self, r):
+        r = np.ascontiguousarray(np.broadcast_to(np.asarray(r, dtype=np.float64), (self.n,)).copy())
+        _check(load().nrto_set_trust_radius(self._h, _ptr(r)))
+
+    def solve_socp(self, opts: Options, fetch=True):
+        o = opts.c()
+        if not fetch:
+            return _check(load().nrto_solve_socp(self._h, C.byref(o), None), allow=(3,))
+        du = np.zeros(self._cat(lambda x: x.T * x.nu))
+        K = np.zeros(self._cat(lambda x: x.T * x.nu * x.nx))
+        p = np.zeros(self.n_rows())
+        pt = np.zeros(self.n_rows())
+        it = np.zeros(self.n, dtype=np.int32)
+        rp = np.zeros(self.n)
+        rd = np.zeros(self.n)
+        st = np.zeros(self.n, dtype=np.int32)
+        out = SocpOut(_ptr(du), _ptr(K), _ptr(p), _ptr(pt), it.ctypes.data_as(_ip), _ptr(rp), _ptr(rd),
+                      st.ctypes.data_as(_ip))
+        code = _check(load().nrto_solve_socp(self._h, C.byref(o), C.byref(out)), allow=(3,))
+        return dict(du=self._split(du, lambda x: (x.T, x.nu)), K=self._split(K, lambda x: (x.T, x.nu, x.nx)),
+                    p=self._split(p, lambda x: (x.n_rows,)), pt=self._split(pt, lambda x: (x.n_rows,)),
+                    iters=it, r_p=rp, r_d=rd, status=st, code=code)
+
+    def outer_step(self, opts: Options):
+        acc = np.zeros(self.n, dtype=np.int32)
+        _check(load().nrto_outer_step(self._h, C.byref(opts.c()), acc.ctypes.data_as(_ip)))
+        return acc
+
+    def solve(self, opts: Options, n_outer=10, fetch=True):
+        o = opts.c()
+        if not fetch:
+            return _check(load().nrto_solve(self._h, C.byref(o), n_outer, None, None, None))
+        u = np.zeros(self._cat(lambda x: x.T * x.nu))
+        K = np.zeros(self._cat(lambda x: x.T * x.nu * x.nx))
+        m = np.zeros(self.n)
+        _check(load().nrto_solve(self._h, C.byref(o), n_outer, _ptr(u), _ptr(K), _ptr(m)))
+        return dict(u_bar=self._split(u, lambda x: (x.T, x.nu)), K=self._split(K, lambda x: (x.T, x.nu, x.nx)),
+                    merit=m)
+
+    def set_warm_start(self, K, pt, lam_p):
+        K = np.ascontiguousarray(np.concatenate([np.asarray(k).reshape(-1) for k in K]))
+        pt = np.ascontiguousarray(np.concatenate([np.asarray(k).reshape(-1) for k in pt]))
+        lp = np.ascontiguousarray(np.concatenate([np.asarray(k).reshape(-1) for k in lam_p]))
+        _check(load().nrto_set_warm_start(self._h, _ptr(K), _ptr(pt), _ptr(lp)))
+
+    def export(self, field, i):
+        n = int(self._COUNTS[field](self.info[i]))
+        out = np.zeros(n)
+        _check(load().nrto_export(self._h, field, i, _ptr(out), n))
+        return out
+
+    def import_(self, field, i, values):
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(-1))
+        _check(load().nrto_import(self._h, field, i, _ptr(v), v.size))
+
+    def profile(self, enable=True):
+        """(solver-kernel ms, launches) since the previous call; then enable/disable recording."""
+        ms = C.c_double()
+        n = C.c_longlong()
+        _check(load().nrto_profile(self._h, int(enable), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def kernel_launches(self):
+        return int(load().nrto_kernel_launches(self._h))

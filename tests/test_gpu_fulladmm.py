@@ -1,0 +1,118 @@
+"""GPU parity of the linearization prologue and the FullADMM inner loop against the oracle,
+through the C ABI (libnrto.so).  FP64 mode: element-wise within 1e-8 relative at fixed
+iteration counts; mixed mode: stated per-result bounds."""
+import numpy as np
+import pytest
+
+from oracle import fulladmm as F, problem as P
+from paper_2603_02642_b300 import nrto, workloads as W
+
+from .gpu_common import RTOL64, assert_close, bvec_ragged, ragged_from_dense, relerr
+
+pytestmark = pytest.mark.gpu
+
+# Sizes: several solver chunks per instance (chunks hold ~8k row entries) and a ragged tail.
+CASES = {
+    "uni_T50_o4": lambda: W.unicycle(3, T=50, n_obs=4),
+    "quad_T40_o5": lambda: W.quadcopter(4, T=40, n_obs=5),
+    "arm_T12": lambda: W.arm(5, T=12),
+}
+
+
+def _lin_oracle(inst):
+    return P.linearize(inst, inst.u_init)
+
+
+@pytest.fixture(scope="module")
+def cases():
+    return {k: f() for k, f in CASES.items()}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_linearization_parity_fp64(cases, name):
+    inst = cases[name]
+    lin = _lin_oracle(inst)
+    prob = nrto.Problem([inst], nrto.PREC_FP64)
+    prob.linearize()
+    assert_close(prob.export(nrto.F_XHAT, 0), lin.x_hat, 1e-12, "x_hat")
+    assert_close(prob.export(nrto.F_A, 0), lin.A, 1e-12, "A")
+    assert_close(prob.export(nrto.F_B, 0), lin.B, 1e-12, "B")
+    assert_close(prob.export(nrto.F_G0, 0), lin.g0, 1e-12, "g0")
+    assert_close(prob.export(nrto.F_BHAT, 0), ragged_from_dense(lin, lin.bhat)[:prob.info[0].n_entries_state], 1e-10, "bhat")
+    assert_close(prob.export(nrto.F_BVEC, 0), bvec_ragged(lin), 1e-10, "bvec")
+    G = np.einsum("jmu,jmv->muv", lin.bvec, lin.bvec)
+    assert_close(prob.export(nrto.F_GM, 0), G, 1e-10, "G_m")
+    prob.close()
+
+
+def _run_both(inst, n_iter, prec, rho=10.0, r=0.5):
+    lin = _lin_oracle(inst)
+    o = F.FullADMMOptions(rho=rho, r_trust=r, check=False)
+    s = F.iterate(inst, lin, o, n_iter=n_iter)
+    prob = nrto.Problem([inst], prec)
+    prob.linearize()
+    prob.set_trust_radius(r)
+    out = prob.solve_socp(nrto.Options(rho=rho, max_inner=n_iter, check=0))
+    return lin, s, prob, out
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("n_iter", [1, 2, 25])
+def test_fulladmm_iterates_parity_fp64(cases, name, n_iter):
+    inst = cases[name]
+    lin, s, prob, out = _run_both(inst, n_iter, nrto.PREC_FP64)
+    assert out["iters"][0] == n_iter
+    assert_close(out["K"][0], s.K, RTOL64, "K")
+    assert_close(out["du"][0], s.du, RTOL64, "du")
+    assert_close(out["p"][0], s.p, RTOL64, "p")
+    assert_close(out["pt"][0], s.pt, RTOL64, "p~")
+    assert_close(prob.export(nrto.F_LAMP, 0), s.lam_p, RTOL64, "lambda_p")
+    assert_close(prob.export(nrto.F_LAMNU, 0), ragged_from_dense(lin, s.lam_nu), RTOL64, "lambda_nu")
+    assert_close(prob.export(nrto.F_DX, 0), s.dx, RTOL64, "dx")
+    sc = prob.export(nrto.F_SCAL, 0)
+    assert abs(sc[0] - s.r_p) <= RTOL64 * s.r_p and abs(sc[1] - s.r_d) <= RTOL64 * s.r_d
+    assert abs(sc[2] - s.r_p_paper) <= RTOL64 * max(s.r_p_paper, 1e-300)
+    prob.close()
+
+
+def test_fulladmm_termination_matches_oracle():
+    inst = W.unicycle(0)
+    lin = _lin_oracle(inst)
+    s = F.iterate(inst, lin, F.FullADMMOptions(rho=10.0, r_trust=2.0, eps_p=1e-4, eps_d=1e-4, max_iter=2000))
+    prob = nrto.Problem([inst], nrto.PREC_FP64)
+    prob.linearize()
+    prob.set_trust_radius(2.0)
+    out = prob.solve_socp(nrto.Options(rho=10.0, max_inner=2000, eps_p=1e-4, eps_d=1e-4, check=1))
+    assert out["status"][0] == 1 and s.converged
+    assert out["iters"][0] == s.iters
+    assert_close(out["K"][0], s.K, 1e-7, "K at termination")
+    assert_close(out["du"][0], s.du, 1e-7, "du at termination")
+    prob.close()
+
+
+def test_batch_equals_single_instances():
+    """Instances are independent: a mixed batch gives the same iterates as solving each alone."""
+    insts = [W.unicycle(7, T=30, n_obs=3), W.quadcopter(8, T=25, n_obs=2), W.unicycle(9, T=22, n_obs=5)]
+    opts = nrto.Options(rho=10.0, max_inner=15, check=0)
+    batch = nrto.Problem(insts, nrto.PREC_FP64)
+    batch.linearize()
+    ob = batch.solve_socp(opts)
+    for i, inst in enumerate(insts):
+        single = nrto.Problem([inst], nrto.PREC_FP64)
+        single.linearize()
+        os_ = single.solve_socp(opts)
+        assert np.array_equal(ob["K"][i], os_["K"][0]) and np.array_equal(ob["du"][i], os_["du"][0])
+        single.close()
+    batch.close()
+
+
+@pytest.mark.parametrize("name", ["uni_T50_o4", "quad_T40_o5"])
+def test_mixed_precision_error_bounds(cases, name):
+    """Mixed mode (FP32 rows, cones and gain products; FP64 factorizations) after 25 iterations:
+    per-result error against the FP64 oracle stays within the FP32 rounding budget."""
+    inst = cases[name]
+    lin, s, prob, out = _run_both(inst, 25, nrto.PREC_MIXED)
+    assert relerr(out["K"][0], s.K) < 5e-4
+    assert relerr(out["du"][0], s.du) < 5e-5
+    assert relerr(out["pt"][0], s.pt) < 5e-5
+    prob.close()
