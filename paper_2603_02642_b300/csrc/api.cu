@@ -46,10 +46,10 @@ int kind_tmax(int k) { return k == KIND_UNICYCLE ? 256 : (k == KIND_QUADCOPTER ?
 constexpr int SMEM_BUDGET = 227 * 1024 - 1024;
 
 template <typename Real>
-size_t smem_for(int kind, int tmax, int chunk, int max_rows) {
-  if (kind == KIND_UNICYCLE) return FASmem<3, 2, Real>::bytes(tmax, chunk, max_rows);
-  if (kind == KIND_QUADCOPTER) return FASmem<12, 4, Real>::bytes(tmax, chunk, max_rows);
-  return FASmem<14, 7, Real>::bytes(tmax, chunk, max_rows);
+size_t smem_for(int kind, int chunk, int max_rows) {
+  if (kind == KIND_UNICYCLE) return FASmem<3, 2, Real>::bytes(chunk, max_rows);
+  if (kind == KIND_QUADCOPTER) return FASmem<12, 4, Real>::bytes(chunk, max_rows);
+  return FASmem<14, 7, Real>::bytes(chunk, max_rows);
 }
 
 struct KindLaunch {
@@ -154,7 +154,9 @@ struct nrto_problem {
   int4* d_rinfo = nullptr;
   long long* d_rent = nullptr;
   long long* d_rbent = nullptr;
-  int* d_cbound = nullptr;
+  ChunkInfo* d_chunks = nullptr;
+  RowMeta* d_rmeta = nullptr;
+  std::vector<long long> h_rent, h_rbent;
   int2* d_groups = nullptr;
   double* d_slot_arena[2] = {nullptr, nullptr};
   double* d_g0[2] = {nullptr, nullptr};
@@ -202,7 +204,8 @@ struct nrto_problem {
     D.rinfo = d_rinfo;
     D.rent = d_rent;
     D.rbent = d_rbent;
-    D.cbound = d_cbound;
+    D.chunks = d_chunks;
+    D.rmeta = d_rmeta;
     D.groups = d_groups;
     for (int s = 0; s < 2; ++s) {
       D.slot[s].arena = d_slot_arena[s];
@@ -350,7 +353,7 @@ void launch_fa_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
   int dev = 0, nsm = 0, per_sm = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FACfg<NX, NU>::NT, kl.smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FACfg<NX, NU, Real>::NT, kl.smem));
   if (per_sm < 1) fail(NRTO_ERR_CUDA, "solver kernel does not fit on an SM");
   const int grid = std::min(kl.count, nsm * per_sm);
   sp.chunk = kl.chunk; sp.max_rows = kl.max_rows; sp.tmax = kl.tmax; sp.n_order = kl.count;
@@ -361,7 +364,7 @@ void launch_fa_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, P->stream));
   }
-  kern<<<grid, FACfg<NX, NU>::NT, kl.smem, P->stream>>>(P->dev<Real>(), sp);
+  kern<<<grid, FACfg<NX, NU, Real>::NT, kl.smem, P->stream>>>(P->dev<Real>(), sp);
   P->check_launch("k_fulladmm");
   if (P->profiling) {
     CK(cudaEventRecord(e1, P->stream));
@@ -424,12 +427,12 @@ template <typename Real>
 void choose_chunk(KindLaunch& kl) {
   const int nx = kind_nx(kl.kind);
   const int minc = ((kl.tmax + 1) * nx + 3) & ~3;
-  int chunk = 8192;
-  while (chunk > minc && smem_for<Real>(kl.kind, kl.tmax, chunk, chunk / (2 * nx) + 2) > (size_t)SMEM_BUDGET) chunk -= 256;
+  int chunk = 6144;
+  while (chunk > minc && smem_for<Real>(kl.kind, chunk, chunk / (2 * nx) + 2) > (size_t)SMEM_BUDGET) chunk -= 256;
   if (chunk < minc) chunk = minc;
   kl.chunk = chunk;
   kl.max_rows = chunk / (2 * nx) + 2;
-  kl.smem = smem_for<Real>(kl.kind, kl.tmax, chunk, kl.max_rows);
+  kl.smem = smem_for<Real>(kl.kind, chunk, kl.max_rows);
   if (kl.smem > (size_t)SMEM_BUDGET) fail(NRTO_ERR_INVALID, "horizon too long for the shared-memory budget of this precision");
 }
 
@@ -592,18 +595,52 @@ nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long 
     if (dptr) {
       CK(cudaMemcpy(to_host ? (void*)buf : (void*)dptr, to_host ? (void*)dptr : (void*)buf, sizeof(double) * count,
                     to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice));
-    } else if (p->prec == NRTO_PREC_FP64) {
-      CK(cudaMemcpy(to_host ? (void*)buf : rptr, to_host ? rptr : (void*)buf, sizeof(double) * count,
+      return NRTO_OK;
+    }
+    // Ragged fields: the device layout has padding at chunk starts; map compact <-> padded
+    // element by element through the row tables.
+    const bool is_b = field == NRTO_F_BVEC;
+    const int nrow = field == NRTO_F_LAMNU ? I.n_sr + I.n_cr : I.n_sr;
+    const long long base = is_b ? I.bent0 : I.ent0;
+    long long span = 0;
+    std::vector<std::pair<long long, long long>> seg;   // (padded offset rel. base, length)
+    for (int r = 0; r < nrow; ++r) {
+      const long long R = I.row0 + r;
+      const int4 ri = p->h_rinfo[R];
+      const long long len = r < I.n_sr ? (long long)(ri.x + 1) * (is_b ? I.nu : I.nx) : I.nx;
+      const long long off = (is_b ? p->h_rbent[R] : p->h_rent[R]) - base;
+      seg.push_back({off, len});
+      span = std::max(span, off + len);
+    }
+    std::vector<double> full(span);
+    if (!to_host) {
+      // read-modify-write so that padding keeps its contents
+      if (p->prec == NRTO_PREC_FP64) {
+        CK(cudaMemcpy(full.data(), rptr, sizeof(double) * span, cudaMemcpyDeviceToHost));
+      } else {
+        std::vector<float> tmp(span);
+        CK(cudaMemcpy(tmp.data(), rptr, sizeof(float) * span, cudaMemcpyDeviceToHost));
+        for (long long k = 0; k < span; ++k) full[k] = tmp[k];
+      }
+      long long o = 0;
+      for (auto& sg : seg) { for (long long k = 0; k < sg.second; ++k) full[sg.first + k] = buf[o + k]; o += sg.second; }
+    }
+    if (p->prec == NRTO_PREC_FP64) {
+      CK(cudaMemcpy(to_host ? (void*)full.data() : rptr, to_host ? rptr : (void*)full.data(), sizeof(double) * span,
                     to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice));
     } else {
-      std::vector<float> tmp(count);
+      std::vector<float> tmp(span);
       if (to_host) {
-        CK(cudaMemcpy(tmp.data(), rptr, sizeof(float) * count, cudaMemcpyDeviceToHost));
-        for (long long k = 0; k < count; ++k) buf[k] = tmp[k];
+        CK(cudaMemcpy(tmp.data(), rptr, sizeof(float) * span, cudaMemcpyDeviceToHost));
+        for (long long k = 0; k < span; ++k) full[k] = tmp[k];
       } else {
-        for (long long k = 0; k < count; ++k) tmp[k] = (float)buf[k];
-        CK(cudaMemcpy(rptr, tmp.data(), sizeof(float) * count, cudaMemcpyHostToDevice));
+        for (long long k = 0; k < span; ++k) tmp[k] = (float)full[k];
+        CK(cudaMemcpy(rptr, tmp.data(), sizeof(float) * span, cudaMemcpyHostToDevice));
       }
+    }
+    if (to_host) {
+      long long o = 0;
+      for (auto& sg : seg) { for (long long k = 0; k < sg.second; ++k) buf[o + k] = full[sg.first + k]; o += sg.second; }
     }
     return NRTO_OK;
   } catch (const std::exception& e) {
@@ -641,8 +678,10 @@ nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int preci
         if (precision == NRTO_PREC_FP64) choose_chunk<double>(P->kl[k]);
         else choose_chunk<float>(P->kl[k]);
       }
-    std::vector<long long> rent, rbent;
-    std::vector<int> cbound;
+    std::vector<long long>& rent = P->h_rent;
+    std::vector<long long>& rbent = P->h_rbent;
+    std::vector<ChunkInfo> chunks;
+    std::vector<RowMeta> rmeta;
     std::vector<int2> groups;
     std::vector<int4> srows, crows;
     long long row = 0, ent = 0, bent = 0, arena = 0, slot = 0, arow = 0, grp = 0, stage = 0, uo = 0;
@@ -659,14 +698,53 @@ nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int preci
       I.row0 = row; I.ent0 = ent; I.bent0 = bent; I.arena0 = arena; I.slot0 = slot; I.arow0 = arow;
       I.grp0 = grp; I.cb0 = cb;
       I.dt = d.dt; I.tau = d.tau; I.sqrt_tau = std::sqrt(d.tau);
-      for (const int4& r : srows) {
-        P->h_rinfo.push_back(r);
+      // State rows in chunks of whole rows for the persistent solver; every chunk starts on a
+      // 4-element (16-byte) boundary of the entry and b arrays so that it can be bulk-copied.
+      const int chunk = P->kl[d.dyn].chunk;
+      int nch = 0;
+      long long accn = 0;
+      long long n_ent_state = 0;
+      for (int r = 0; r < (int)srows.size(); ++r) {
+        const int4& rr = srows[r];
+        const long long len = (long long)(rr.x + 1) * d.nx;
+        if (r == 0 || accn + len > chunk) {
+          if (r > 0) {
+            ChunkInfo& c = chunks.back();
+            c.r1 = r;
+            c.ne = (int)(((ent - c.e0) + 3) & ~3LL);
+            c.nb = (int)(((bent - c.b0) + 3) & ~3LL);
+          }
+          ent = (ent + 3) & ~3LL;
+          bent = (bent + 3) & ~3LL;
+          ChunkInfo c{};
+          c.e0 = ent; c.b0 = bent; c.r0 = r;
+          chunks.push_back(c);
+          ++nch;
+          accn = 0;
+        }
+        accn += len;
+        const ChunkInfo& c = chunks.back();
+        RowMeta m{};
+        m.off = (int)(ent - c.e0); m.boff = (int)(bent - c.b0); m.t = rr.x;
+        rmeta.push_back(m);
+        P->h_rinfo.push_back(rr);
         rent.push_back(ent);
         rbent.push_back(bent);
-        ent += (long long)(r.x + 1) * d.nx;
-        bent += (long long)(r.x + 1) * d.nu;
+        ent += len;
+        bent += (long long)(rr.x + 1) * d.nu;
+        n_ent_state += len;
       }
-      I.n_ent_state = ent - I.ent0;
+      if (nch > 0) {
+        ChunkInfo& c = chunks.back();
+        c.r1 = (int)srows.size();
+        c.ne = (int)(((ent - c.e0) + 3) & ~3LL);
+        c.nb = (int)(((bent - c.b0) + 3) & ~3LL);
+        ent = (ent + 3) & ~3LL;
+        bent = (bent + 3) & ~3LL;
+      }
+      I.n_chunks = nch;
+      cb += nch;
+      I.n_ent_state = n_ent_state;
       int ng = 0;
       for (size_t q = 0; q < crows.size(); ++q) {
         const long long R = row + I.n_sr + (long long)q;
@@ -677,6 +755,7 @@ nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int preci
           groups.back().y += 1;
         }
         P->h_rinfo.push_back(crows[q]);
+        rmeta.push_back(RowMeta{0, 0, -1, 0});
         rent.push_back(ent);
         rbent.push_back(-1);
         ent += d.nx;
@@ -684,19 +763,6 @@ nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int preci
       I.n_groups = ng;
       if (ng > 0 && ng % d.T != 0) fail(NRTO_ERR_INVALID, "internal: control groups not uniform over steps");
       I.n_ent = ent - I.ent0;
-      // chunks of whole state rows for the persistent solver
-      const int chunk = P->kl[d.dyn].chunk;
-      int nch = 0;
-      cbound.push_back(0);
-      long long accn = 0;
-      for (int r = 0; r < I.n_sr; ++r) {
-        const long long len = (long long)(srows[r].x + 1) * d.nx;
-        if (accn + len > chunk && accn > 0) { cbound.push_back(r); ++nch; accn = 0; }
-        accn += len;
-      }
-      if (I.n_sr > 0) { cbound.push_back(I.n_sr); ++nch; }
-      I.n_chunks = nch;
-      cb += nch + 1;
       const Arena L = arena_layout(d.nx, d.nu, d.T, d.n_obs, d.n_link);
       const SlotL SL = slot_layout(d.nx, d.nu, d.T);
       P->stage_off.push_back(stage);
@@ -727,19 +793,21 @@ nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int preci
     P->d_rinfo = P->dalloc<int4>(row);
     P->d_rent = P->dalloc<long long>(row);
     P->d_rbent = P->dalloc<long long>(row);
-    P->d_cbound = P->dalloc<int>(cb);
+    P->d_chunks = P->dalloc<ChunkInfo>(cb);
+    P->d_rmeta = P->dalloc<RowMeta>(row);
     P->d_groups = P->dalloc<int2>(grp);
     for (int s = 0; s < 2; ++s) {
       P->d_slot_arena[s] = P->dalloc<double>(slot);
       P->d_g0[s] = P->dalloc<double>(row);
       P->d_arow[s] = P->dalloc<double>(arow);
-      P->d_bhat[s] = P->dalloc<char>(rs * ent);
-      P->d_bvec[s] = P->dalloc<char>(rs * bent);
+      P->d_bhat[s] = P->dalloc<char>(rs * (ent + 16));   // +16: bulk copies round sizes up
+      P->d_bvec[s] = P->dalloc<char>(rs * (bent + 16));
     }
-    P->d_lam = P->dalloc<char>(rs * ent);
-    P->d_p = P->dalloc<double>(row); P->d_pt = P->dalloc<double>(row); P->d_ptn = P->dalloc<double>(row);
-    P->d_lamp = P->dalloc<double>(row); P->d_w = P->dalloc<double>(row); P->d_lamw = P->dalloc<double>(row);
-    P->d_s = P->dalloc<double>(row); P->d_ell = P->dalloc<double>(row); P->d_dd = P->dalloc<double>(row);
+    P->d_lam = P->dalloc<char>(rs * (ent + 16));
+    // per-row arrays that are bulk-copied are read from an even row index with an even count
+    P->d_p = P->dalloc<double>(row + 4); P->d_pt = P->dalloc<double>(row); P->d_ptn = P->dalloc<double>(row);
+    P->d_lamp = P->dalloc<double>(row + 4); P->d_w = P->dalloc<double>(row); P->d_lamw = P->dalloc<double>(row);
+    P->d_s = P->dalloc<double>(row + 4); P->d_ell = P->dalloc<double>(row); P->d_dd = P->dalloc<double>(row);
     P->d_rnorm = P->dalloc<double>(row);
     P->d_sc = P->dalloc<double>((size_t)n * NSC);
     P->d_is = P->dalloc<int>((size_t)n * NIS);
@@ -757,7 +825,8 @@ nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int preci
     up(P->d_rinfo, P->h_rinfo.data(), sizeof(int4) * row);
     up(P->d_rent, rent.data(), sizeof(long long) * row);
     up(P->d_rbent, rbent.data(), sizeof(long long) * row);
-    up(P->d_cbound, cbound.data(), sizeof(int) * cb);
+    up(P->d_chunks, chunks.data(), sizeof(ChunkInfo) * cb);
+    up(P->d_rmeta, rmeta.data(), sizeof(RowMeta) * row);
     up(P->d_groups, groups.data(), sizeof(int2) * grp);
     up(P->d_order, P->h_order.data(), sizeof(int) * n);
     up(P->d_stage_off, P->stage_off.data(), sizeof(long long) * n);

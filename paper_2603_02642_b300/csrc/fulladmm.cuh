@@ -7,12 +7,22 @@
 //       Z'_m = Σ_j b_{j,m} w_{j,m}ᵀ, then K_m is solved with the per-step eigen factors;
 //   (b) Block 2 (δû, p): Riccati backward/forward sweep with the factorization fixed per outer step;
 //   (d) duals λ_p, λ_ν, λ_w, λ_e and the primal/dual residual reductions.
+//
 // Row state kept between iterations is λ_ν only (plus one scale s_j per row): ν^l = s^l(y^{l-1}+λ^{l-1})
-// is recomputed from the gains, so the λ_ν update of iteration l is done during the row pass of
-// iteration l+1 (which also yields the row parts of iteration l's residuals).  Termination at
-// iteration l therefore happens after that pass; iteration l+1's block-1 results are discarded.
+// is recomputed from the gains (y = Â_j k + b̂_j), so the λ_ν update of iteration l is done during the
+// row pass of iteration l+1, which also yields the row parts of iteration l's residuals.  Termination
+// at iteration l therefore happens after that pass; iteration l+1's block-1 results are discarded.
+//
+// Row pass data flow: the rows are cut into chunks of whole rows; each chunk's λ, b̂, b ranges and its
+// row metadata arrive in shared memory by bulk copies (double buffered, mbarrier completion).  Thread
+// `tid` owns the (block m, component c) columns P = tid + k·NT of the ζ-layout for every row, and keeps
+// the gain tables Gtᵀ_m[:, c] (= √τ K_m Ψ_mᵀ) of the current and previous iterate and its Z'_m[:, c]
+// accumulators in registers across all rows, so the row data is read from shared memory once per
+// sub-pass and the gain tables are never re-read.  Row norms are reduced by warp shuffles and a
+// fixed-order sum over warps (deterministic).
 #pragma once
 #include "linearize.cuh"
+#include "tma.cuh"
 
 namespace nrto {
 
@@ -24,13 +34,14 @@ struct SolveParams {
   int order0, queue_idx;
 };
 
-template <int NX, int NU>
+template <int NX, int NU, typename Real>
 struct FACfg {
-  static constexpr int NT = 512;
+  static constexpr int NT = sizeof(Real) == 4 ? 1024 : 512;
   static constexpr int NW = NT / 32;
-  static constexpr int GS = NU * NX + 1;  // padded Gtᵀ step stride
   static constexpr int TMAXC = (NX == 3) ? 256 : (NX == 12 ? 160 : 128);
-  static constexpr int PAIRS = ((TMAXC + 1) * NX + NT - 1) / NT;
+  static constexpr int LMAX = (TMAXC + 1) * NX;                      // longest row
+  static constexpr int PAIRS = (LMAX + NT - 1) / NT;                  // (m, c) columns per thread
+  static constexpr int NWR = (NW < (LMAX + 31) / 32) ? NW : (LMAX + 31) / 32;   // warps touching a row
 };
 
 // Supplementary Sec. II-C closed form: (t̂, η̂) ↦ (p̃, s·η̂)
@@ -40,91 +51,138 @@ __device__ __forceinline__ void soc_case(double tt, double a, double& s_new, dou
   else { pt_new = 0.5 * (tt + a); s_new = pt_new / a; }
 }
 
-// Shared-memory carve for one CTA (sizes must match fa_smem_bytes on the host).
+// Shared memory of one CTA: two chunk buffers plus per-chunk scratch.  Host and device use the
+// same size function.
 template <int NX, int NU, typename Real>
 struct FASmem {
-  Real* gtA; Real* gtB; Real* eta; Real* uu; Real* bb; Real* rowS; int* rowOff; int* rowBOff; int* rowT;
-  double* red; double* vec;
-  NRTO_HD static size_t bytes(int tmax, int chunk, int max_rows) {
-    size_t g = (size_t)(tmax + 1) * FACfg<NX, NU>::GS;
-    size_t nb = (size_t)chunk / NX * NU + NU;
-    size_t b = 2 * g * sizeof(Real) + 2 * (size_t)chunk * sizeof(Real) + nb * sizeof(Real) + max_rows * sizeof(Real);
-    b = (b + 15) & ~(size_t)15;
-    b += 3 * (size_t)max_rows * sizeof(int);
-    b = (b + 15) & ~(size_t)15;
-    b += (4 * FACfg<NX, NU>::NW + 4 * 16) * sizeof(double);
+  struct Buf {
+    Real* lam; Real* bhat; Real* bb; RowMeta* meta; double* sold; double* pp; double* lp;
+  };
+  Buf buf[2];
+  Real* rowpart;   // [max_rows][NWR] warp partial norms
+  Real* snew;      // [max_rows]
+  double* red;     // block reductions
+  double* vec;     // Riccati sweep vector
+
+  NRTO_HD static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+  NRTO_HD static size_t buf_bytes(int chunk, int max_rows) {
+    size_t b = 0;
+    b += align16((size_t)(chunk + 4) * sizeof(Real));            // lam
+    b += align16((size_t)(chunk + 4) * sizeof(Real));            // bhat
+    b += align16((size_t)(chunk / NX * NU + 8) * sizeof(Real));  // b
+    b += align16((size_t)max_rows * sizeof(RowMeta));            // meta
+    b += 3 * align16((size_t)(max_rows + 4) * sizeof(double));   // s_old, p, λ_p
     return b;
   }
-  __device__ void carve(char* base, int tmax, int chunk, int max_rows) {
-    size_t g = (size_t)(tmax + 1) * FACfg<NX, NU>::GS;
-    size_t nb = (size_t)chunk / NX * NU + NU;
-    Real* r = reinterpret_cast<Real*>(base);
-    gtA = r; r += g; gtB = r; r += g; eta = r; r += chunk; uu = r; r += chunk; bb = r; r += nb; rowS = r; r += max_rows;
-    char* c = reinterpret_cast<char*>(r);
-    c = base + ((c - base + 15) & ~(size_t)15);
-    int* ip = reinterpret_cast<int*>(c);
-    rowOff = ip; ip += max_rows; rowBOff = ip; ip += max_rows; rowT = ip; ip += max_rows;
-    c = reinterpret_cast<char*>(ip);
-    c = base + ((c - base + 15) & ~(size_t)15);
+  NRTO_HD static size_t bytes(int chunk, int max_rows) {
+    size_t b = 2 * buf_bytes(chunk, max_rows);
+    b += align16((size_t)max_rows * FACfg<NX, NU, Real>::NWR * sizeof(Real));
+    b += align16((size_t)max_rows * sizeof(Real));
+    b += (4 * FACfg<NX, NU, Real>::NW + 4 * 16) * sizeof(double);
+    return b;
+  }
+  __device__ void carve(char* base, int chunk, int max_rows) {
+    char* c = base;
+    auto take = [&](size_t bytes) { char* r = c; c += align16(bytes); return r; };
+    for (int k = 0; k < 2; ++k) {
+      buf[k].lam = reinterpret_cast<Real*>(take((size_t)(chunk + 4) * sizeof(Real)));
+      buf[k].bhat = reinterpret_cast<Real*>(take((size_t)(chunk + 4) * sizeof(Real)));
+      buf[k].bb = reinterpret_cast<Real*>(take((size_t)(chunk / NX * NU + 8) * sizeof(Real)));
+      buf[k].meta = reinterpret_cast<RowMeta*>(take((size_t)max_rows * sizeof(RowMeta)));
+      buf[k].sold = reinterpret_cast<double*>(take((size_t)(max_rows + 4) * sizeof(double)));
+      buf[k].pp = reinterpret_cast<double*>(take((size_t)(max_rows + 4) * sizeof(double)));
+      buf[k].lp = reinterpret_cast<double*>(take((size_t)(max_rows + 4) * sizeof(double)));
+    }
+    rowpart = reinterpret_cast<Real*>(take((size_t)max_rows * FACfg<NX, NU, Real>::NWR * sizeof(Real)));
+    snew = reinterpret_cast<Real*>(take((size_t)max_rows * sizeof(Real)));
     red = reinterpret_cast<double*>(c);
-    vec = red + 4 * FACfg<NX, NU>::NW;
+    vec = red + 4 * FACfg<NX, NU, Real>::NW;
   }
 };
 
-// Per-step gain solve (FullADMM: coefA = ρ√τ on Z', no K̃ term; DR adds r_χ K̃):
-//   X = (Pfᵀ (coefA Z' Φ + coefK K̃ U)) ⊙ Dv,  K = Pf X Uᵀ,  Gtᵀ = √τ Pf X Φᵀ.
+// Issue the bulk copies of one chunk into a buffer (one thread).  Per-row doubles (s, p, λ_p) are
+// fetched from an even row index so that both ends stay 16-byte aligned; the kernel shifts by R0 & 1.
 template <int NX, int NU, typename Real>
-__device__ void gain_solve_step(const double* ar, const Arena& L, int m, double sqrt_tau, double coefA, double coefK,
-                                const double* Kt, double* Kout, Real* gt_smem, double* gt_glob) {
-  constexpr int GS = FACfg<NX, NU>::GS;
-  Real Z[NU][NX], Y[NU][NX];
-  const double* Zp = ar + L.Zp + (long long)m * NU * NX;
-  const double* Pf = ar + L.Pf + (long long)m * NU * NU;
-  const double* Phi = ar + L.Phi + (long long)m * NX * NX;
-  const double* U = ar + L.SigU + (long long)m * NX * NX;
-  const double* Dv = ar + L.Dv + (long long)m * NU * NX;
+__device__ void issue_chunk(const Dev<Real>& D, const LinSlot<Real>& S, const Inst& I, const ChunkInfo& ck,
+                            typename FASmem<NX, NU, Real>::Buf& bf, uint64_t* bar) {
+  const long long R0 = I.row0 + ck.r0, R1 = I.row0 + ck.r1;
+  const long long Ra = R0 & ~1LL;
+  const long long nd = ((R1 - Ra) + 1) & ~1LL;
+  const uint32_t bl = (uint32_t)(ck.ne * sizeof(Real)), bbb = (uint32_t)(ck.nb * sizeof(Real));
+  const uint32_t bm = (uint32_t)((ck.r1 - ck.r0) * sizeof(RowMeta)), bd = (uint32_t)(nd * sizeof(double));
+  mbar_arrive_expect_tx(bar, 2 * bl + bbb + bm + 3 * bd);
+  bulk_g2s(bf.lam, D.lam + ck.e0, bl, bar);
+  bulk_g2s(bf.bhat, S.bhat + ck.e0, bl, bar);
+  bulk_g2s(bf.bb, S.bvec + ck.b0, bbb, bar);
+  bulk_g2s(bf.meta, D.rmeta + R0, bm, bar);
+  bulk_g2s(bf.sold, D.s + Ra, bd, bar);
+  bulk_g2s(bf.pp, D.p + Ra, bd, bar);
+  bulk_g2s(bf.lp, D.lamp + Ra, bd, bar);
+}
+
+// Per-step gain solve, parallel over (m, u, c) in four phases through arena scratch:
+//   Y = coefA Z' Φ + coefK K̃ U;  X = (Pfᵀ Y) ⊙ Dv;  PX = Pf X;  K = PX Uᵀ;  Gtᵀ = √τ PX Φᵀ.
+// (FullADMM: coefA = ρ√τ, coefK = 0; DR: coefA = σ√τ, coefK = r_χ.)  All threads of the block.
+template <int NX, int NU, typename Real>
+__device__ void gain_solve(double* ar, const Arena& L, int T, double sqrt_tau, double coefA, double coefK,
+                           double* Kout, double* gt_out) {
+  const int n = T * NU * NX;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
+    const double* Zp = ar + L.Zp + (long long)m * NU * NX + u * NX;
+    const double* Phi = ar + L.Phi + (long long)m * NX * NX;
+    Real acc = 0;
 #pragma unroll
-  for (int u = 0; u < NU; ++u)
+    for (int r = 0; r < NX; ++r) acc += (Real)Zp[r] * (Real)Phi[r * NX + c];
+    acc *= (Real)coefA;
+    if (coefK != 0.0) {
+      const double* Kt = ar + L.Kt + (long long)m * NU * NX + u * NX;
+      const double* U = ar + L.SigU + (long long)m * NX * NX;
+      Real a2 = 0;
 #pragma unroll
-    for (int c = 0; c < NX; ++c) Z[u][c] = (Real)Zp[u * NX + c];
-  for (int u = 0; u < NU; ++u)
-    for (int c = 0; c < NX; ++c) {
-      Real acc = 0;
-      for (int r = 0; r < NX; ++r) acc += Z[u][r] * (Real)Phi[r * NX + c];
-      acc *= (Real)coefA;
-      if (coefK != 0.0) {
-        Real a2 = 0;
-        for (int r = 0; r < NX; ++r) a2 += (Real)Kt[(long long)m * NU * NX + u * NX + r] * (Real)U[r * NX + c];
-        acc += (Real)coefK * a2;
-      }
-      Y[u][c] = acc;
+      for (int r = 0; r < NX; ++r) a2 += (Real)Kt[r] * (Real)U[r * NX + c];
+      acc += (Real)coefK * a2;
     }
-  // X = (Pfᵀ Y) ⊙ Dv  (into Z)
-  for (int u = 0; u < NU; ++u)
-    for (int c = 0; c < NX; ++c) {
-      Real acc = 0;
-      for (int v = 0; v < NU; ++v) acc += (Real)Pf[v * NU + u] * Y[v][c];
-      Z[u][c] = acc * (Real)Dv[u * NX + c];
+    ar[L.Ws1 + q] = (double)acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
+    const double* Pf = ar + L.Pf + (long long)m * NU * NU;
+    const double* Y = ar + L.Ws1 + (long long)m * NU * NX;
+    Real acc = 0;
+#pragma unroll
+    for (int v = 0; v < NU; ++v) acc += (Real)Pf[v * NU + u] * (Real)Y[v * NX + c];
+    ar[L.Ws2 + q] = (double)(acc * (Real)ar[L.Dv + q]);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
+    const double* Pf = ar + L.Pf + (long long)m * NU * NU;
+    const double* X = ar + L.Ws2 + (long long)m * NU * NX;
+    Real acc = 0;
+#pragma unroll
+    for (int v = 0; v < NU; ++v) acc += (Real)Pf[u * NU + v] * (Real)X[v * NX + c];
+    ar[L.Ws1 + q] = (double)acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
+    const double* PX = ar + L.Ws1 + (long long)m * NU * NX + u * NX;
+    const double* U = ar + L.SigU + (long long)m * NX * NX + c * NX;
+    const double* Phi = ar + L.Phi + (long long)m * NX * NX + c * NX;
+    Real k = 0, g = 0;
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      const Real px = (Real)PX[r];
+      k += px * (Real)U[r];
+      g += px * (Real)Phi[r];
     }
-  // PX = Pf X  (into Y)
-  for (int u = 0; u < NU; ++u)
-    for (int c = 0; c < NX; ++c) {
-      Real acc = 0;
-      for (int v = 0; v < NU; ++v) acc += (Real)Pf[u * NU + v] * Z[v][c];
-      Y[u][c] = acc;
-    }
-  for (int u = 0; u < NU; ++u)
-    for (int c = 0; c < NX; ++c) {
-      Real k = 0, g = 0;
-      for (int r = 0; r < NX; ++r) {
-        k += Y[u][r] * (Real)U[c * NX + r];
-        g += Y[u][r] * (Real)Phi[c * NX + r];
-      }
-      Kout[(long long)m * NU * NX + u * NX + c] = (double)k;
-      g *= (Real)sqrt_tau;
-      gt_smem[m * GS + u * NX + c] = g;
-      gt_glob[(long long)m * NU * NX + u * NX + c] = (double)g;
-    }
+    Kout[q] = (double)k;
+    gt_out[q] = (double)(g * (Real)sqrt_tau);
+  }
+  for (int q = threadIdx.x; q < NU * NX; q += blockDim.x) gt_out[(long long)T * NU * NX + q] = 0.0;
+  __syncthreads();
 }
 
 // Block-2 (δû) LQ sweep with fixed factors (warp 0 only).  Linear terms q_t (t = 0..T, index t
@@ -183,10 +241,22 @@ __device__ void riccati_sweep(double* ar, const Arena& L, const double* sa, cons
   }
 }
 
+// Load the gain-table registers of this thread's columns from an arena Gtᵀ table ((T+1)×NU×NX).
+template <int NX, int NU, typename Real, int PAIRS>
+__device__ __forceinline__ void load_gt_regs(const double* gt, int T, const int (&mk)[PAIRS], const int (&ck)[PAIRS],
+                                             Real (&g)[PAIRS][NU]) {
+#pragma unroll
+  for (int k = 0; k < PAIRS; ++k)
+#pragma unroll
+    for (int u = 0; u < NU; ++u)
+      g[k][u] = (mk[k] < T) ? (Real)gt[(long long)mk[k] * NU * NX + u * NX + ck[k]] : (Real)0;
+}
+
 template <int NX, int NU, typename Real>
-__device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int inst, FASmem<NX, NU, Real>& sm) {
-  using C = FACfg<NX, NU>;
-  constexpr int NT = C::NT, NW = C::NW, GS = C::GS, PAIRS = C::PAIRS;
+__device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int inst, FASmem<NX, NU, Real>& sm,
+                                  uint64_t* bars, uint32_t* phase, int* s_flag) {
+  using C = FACfg<NX, NU, Real>;
+  constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR = C::NWR;
   const Inst I = D.inst[inst];
   const Arena L = arena_layout(NX, NU, I.T, I.n_obs, I.n_link);
   const SlotL SL = slot_layout(NX, NU, I.T);
@@ -201,6 +271,12 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   Real* lam = D.lam;
   double* sc = D.sc + (long long)inst * NSC;
   int* isr = D.is + inst * NIS;
+  const ChunkInfo* chunks = D.chunks + I.cb0;
+
+  // this thread's (m, c) columns
+  int mk[PAIRS], ck[PAIRS];
+#pragma unroll
+  for (int k = 0; k < PAIRS; ++k) { const int P = tid + k * NT; mk[k] = P / NX; ck[k] = P - mk[k] * NX; }
 
   // ---- initialization (Algorithm 1): λ_p, λ_ν, k, p <- 0 (or a warm start of k, p̃, λ_p) ----
   for (long long e = tid; e < I.n_ent; e += NT) lam[I.ent0 + e] = (Real)0;
@@ -210,130 +286,153 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     else { D.p[R] = D.pt[R]; }
     D.w[R] = 0.0; D.lamw[R] = 0.0; D.s[R] = 1.0; D.ell[R] = 0.0;
   }
-  for (int q = tid; q < T * NU; q += NT) { ar[L.du + q] = 0.0; }
+  for (int q = tid; q < T * NU; q += NT) ar[L.du + q] = 0.0;
   for (int q = tid; q < (T + 1) * NX; q += NT) { ar[L.dx + q] = 0.0; ar[L.e + q] = 0.0; ar[L.lam_e + q] = 0.0; }
   if (!sp.warm)
     for (int q = tid; q < T * NU * NX; q += NT) ar[L.K1 + q] = 0.0;
   __syncthreads();
-  // Gtᵀ of the initial gains
+  // Gtᵀ of the initial gains into Gt1 ("current"); Gt0 is the "previous" table
   for (int q = tid; q < (T + 1) * NU * NX; q += NT) {
-    int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
+    const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
     double acc = 0.0;
     if (m < T)
       for (int r = 0; r < NX; ++r) acc += ar[L.K1 + (long long)m * NU * NX + u * NX + r] * ar[L.Psi + (long long)m * NX * NX + c * NX + r];
     ar[L.Gt1 + q] = I.sqrt_tau * acc;
-    sm.gtB[m * GS + u * NX + c] = (Real)(I.sqrt_tau * acc);
+    ar[L.Gt0 + q] = 0.0;
   }
   if (tid == 0) { sc[SC_SCAL_RP] = 0; sc[SC_SCAL_RD] = 0; sc[SC_SCAL_RPP] = 0; sc[SC_SCAL_RDP] = 0; }
   __syncthreads();
-  Real* gtOld = sm.gtA;   // Gtᵀ of k^{b-2}
-  Real* gtCur = sm.gtB;   // Gtᵀ of k^{b-1}
+  int gsel = 1;           // arena table holding Gtᵀ of the current gains (other one: previous)
   const int Lmax = sp.max_iter;
   int status = ST_MAXITER, iters = 0;
   double r_p = 0, r_d = 0;
+  const int gpk = (I.n_groups > 0) ? I.n_groups / T : 0;
 
   for (int b = 1; b <= Lmax + 1 && Lmax > 0; ++b) {
     const bool first = (b == 1);
     const bool block1 = (b <= Lmax);
-    double prp = 0.0, prd = 0.0;
-    Real acc[PAIRS][NU];
+    const double* gtc_arena = ar + (gsel ? L.Gt1 : L.Gt0);
+    const double* gto_arena = ar + (gsel ? L.Gt0 : L.Gt1);
+    Real gc[PAIRS][NU], go[PAIRS][NU], z[PAIRS][NU];
+    load_gt_regs<NX, NU, Real, PAIRS>(gtc_arena, T, mk, ck, gc);
+    load_gt_regs<NX, NU, Real, PAIRS>(gto_arena, T, mk, ck, go);
 #pragma unroll
     for (int k = 0; k < PAIRS; ++k)
 #pragma unroll
-      for (int u = 0; u < NU; ++u) acc[k][u] = (Real)0;
+      for (int u = 0; u < NU; ++u) z[k][u] = (Real)0;
+    Real arp = 0, ard = 0;
 
-    // ---------------- row pass over state rows, chunk by chunk ----------------
+    // ---------------- row pass over state rows, chunk by chunk (bulk copies, double buffered) --------
+    __syncthreads();
+    if (tid == 0) {
+      fence_proxy_async();
+      for (int c0 = 0; c0 < 2 && c0 < I.n_chunks; ++c0) issue_chunk<NX, NU, Real>(D, S, I, chunks[c0], sm.buf[c0], &bars[c0]);
+    }
     for (int ch = 0; ch < I.n_chunks; ++ch) {
-      const int r0 = D.cbound[I.cb0 + ch], r1 = D.cbound[I.cb0 + ch + 1];
-      const long long ec0 = D.rent[I.row0 + r0];
-      const long long bc0 = D.rbent[I.row0 + r0];
-      // sub-pass 1: warp per row
-      for (int r = r0 + warp; r < r1; r += NW) {
-        const long long R = I.row0 + r;
-        const int t = D.rinfo[R].x;
-        const long long e0 = D.rent[R], b0 = D.rbent[R];
-        const int len = (t + 1) * NX;
-        const int loc = (int)(e0 - ec0), bloc = (int)(b0 - bc0);
-        const Real sold = (Real)D.s[R];
-        Real arp = 0, ard = 0, an = 0;
-        for (int e = lane; e < len; e += 32) {
-          const int m = e / NX, c = e - m * NX;
-          Real bvv[NU];
+      const int bi = ch & 1;
+      typename FASmem<NX, NU, Real>::Buf& bf = sm.buf[bi];
+      const ChunkInfo cki = chunks[ch];
+      const int nr = cki.r1 - cki.r0;
+      const int soff = (int)((I.row0 + cki.r0) & 1LL);
+      if (tid == 0) *s_flag = mbar_wait_bounded(&bars[bi], phase[bi]) ? 1 : 0;
+      __syncthreads();
+      phase[bi] ^= 1u;
+      if (*s_flag == 0) { status = ST_TIMEOUT; goto done; }
+      // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms
+      for (int q = 0; q < nr; ++q) {
+        const RowMeta rm = bf.meta[q];
+        const Real so = (Real)bf.sold[soff + q];
+        Real pn = 0;
+        bool act = false;
 #pragma unroll
-          for (int u = 0; u < NU; ++u) bvv[u] = S.bvec[b0 + (long long)m * NU + u];
-          const Real yb = S.bhat[e0 + e];
-          Real y = yb;
-          const Real* gc = gtCur + m * GS + c;
+        for (int k = 0; k < PAIRS; ++k) {
+          if (mk[k] <= rm.t) {
+            act = true;
+            const int e = rm.off + mk[k] * NX + ck[k];
+            const Real* bq = bf.bb + rm.boff + mk[k] * NU;
+            Real bv[NU];
 #pragma unroll
-          for (int u = 0; u < NU; ++u) y += gc[u * NX] * bvv[u];
-          Real l = lam[e0 + e];
-          if (!first) {
-            Real yo = yb;
-            const Real* go = gtOld + m * GS + c;
+            for (int u = 0; u < NU; ++u) bv[u] = bq[u];
+            const Real yb = bf.bhat[e];
+            Real l = bf.lam[e];
+            Real y = yb;
 #pragma unroll
-            for (int u = 0; u < NU; ++u) yo += go[u * NX] * bvv[u];
-            const Real nu = sold * (yo + l);
-            const Real ln = l + y - nu;
-            arp += (y - nu) * (y - nu);
-            ard += (y - yo) * (y - yo);
-            l = ln;
-            lam[e0 + e] = l;
-          }
-          if (block1) {
+            for (int u = 0; u < NU; ++u) y += gc[k][u] * bv[u];
+            if (!first) {
+              Real yo = yb;
+#pragma unroll
+              for (int u = 0; u < NU; ++u) yo += go[k][u] * bv[u];
+              const Real nu = so * (yo + l);
+              const Real ln = l + y - nu;
+              arp += (y - nu) * (y - nu);
+              ard += (y - yo) * (y - yo);
+              l = ln;
+              bf.lam[e] = l;
+              lam[cki.e0 + e] = l;
+            }
             const Real et = y + l;
-            an += et * et;
-            sm.eta[loc + e] = et;
-            sm.uu[loc + e] = -yb - l;
-            if (c < NU) sm.bb[bloc + m * NU + c] = S.bvec[b0 + (long long)m * NU + c];
+            pn += et * et;
           }
         }
-        arp = warp_sum(arp); ard = warp_sum(ard); an = warp_sum(an);
-        if (lane == 0) {
-          prp += (double)arp; prd += (double)ard;
-          if (block1) {
-            double snew, ptn;
-            soc_case(D.p[R] + D.lamp[R], sqrt((double)an), snew, ptn);
-            D.s[R] = snew; D.ptn[R] = ptn;
-            sm.rowS[r - r0] = (Real)snew; sm.rowOff[r - r0] = loc; sm.rowBOff[r - r0] = bloc; sm.rowT[r - r0] = t;
-          }
+        if (block1 && warp < NWR) {
+          if (__any_sync(0xffffffffu, act)) pn = warp_sum(pn);
+          if (lane == 0) sm.rowpart[q * NWR + warp] = pn;
         }
       }
       __syncthreads();
-      // sub-pass 2: Z'_m += Σ_j b_{j,m} w_{j,m}ᵀ, thread per (m, c) pairs, rows of the chunk
       if (block1) {
-        const int nr = r1 - r0;
+        // SOC projection per row (Supplementary Sec. II-C) with t̂ = p + λ_p
+        for (int q = tid; q < nr; q += NT) {
+          Real a2 = 0;
+          for (int w = 0; w < NWR; ++w) a2 += sm.rowpart[q * NWR + w];
+          double snew, ptn;
+          soc_case(bf.pp[soff + q] + bf.lp[soff + q], sqrt((double)a2), snew, ptn);
+          sm.snew[q] = (Real)snew;
+          const long long R = I.row0 + cki.r0 + q;
+          D.s[R] = snew;
+          D.ptn[R] = ptn;
+        }
+        __syncthreads();
+        // sub-pass 2: Z'_m[:, c] += b_{j,m} w_{j,m}[c], w = ν - b̂ - λ = s(y + λ) - b̂ - λ
+        for (int q = 0; q < nr; ++q) {
+          const RowMeta rm = bf.meta[q];
+          const Real sn = sm.snew[q];
 #pragma unroll
-        for (int k = 0; k < PAIRS; ++k) {
-          const int P = tid + k * NT;
-          const int m = P / NX, c = P - m * NX;
-          if (m < T) {
-            int lo = 0, hi = nr;
-            while (lo < hi) { int mid = (lo + hi) >> 1; if (sm.rowT[mid] > m) hi = mid; else lo = mid + 1; }
-            for (int q = lo; q < nr; ++q) {
-              const int off = sm.rowOff[q] + m * NX + c;
-              const Real wv = sm.rowS[q] * sm.eta[off] + sm.uu[off];
-              const Real* bq = sm.bb + sm.rowBOff[q] + m * NU;
+          for (int k = 0; k < PAIRS; ++k) {
+            if (mk[k] < rm.t) {
+              const int e = rm.off + mk[k] * NX + ck[k];
+              const Real* bq = bf.bb + rm.boff + mk[k] * NU;
+              Real bv[NU];
 #pragma unroll
-              for (int u = 0; u < NU; ++u) acc[k][u] += bq[u] * wv;
+              for (int u = 0; u < NU; ++u) bv[u] = bq[u];
+              const Real yb = bf.bhat[e];
+              const Real l = bf.lam[e];
+              Real y = yb;
+#pragma unroll
+              for (int u = 0; u < NU; ++u) y += gc[k][u] * bv[u];
+              const Real wv = sn * (y + l) - yb - l;
+#pragma unroll
+              for (int u = 0; u < NU; ++u) z[k][u] += bv[u] * wv;
             }
           }
         }
       }
       __syncthreads();
+      if (tid == 0 && ch + 2 < I.n_chunks) {
+        fence_proxy_async();
+        issue_chunk<NX, NU, Real>(D, S, I, chunks[ch + 2], bf, &bars[bi]);
+      }
     }
     if (block1) {
 #pragma unroll
-      for (int k = 0; k < PAIRS; ++k) {
-        const int P = tid + k * NT;
-        const int m = P / NX, c = P - m * NX;
-        if (m < T)
+      for (int k = 0; k < PAIRS; ++k)
+        if (mk[k] < T)
 #pragma unroll
-          for (int u = 0; u < NU; ++u) ar[L.Zp + (long long)m * NU * NX + u * NX + c] = (double)acc[k][u];
-      }
+          for (int u = 0; u < NU; ++u) ar[L.Zp + (long long)mk[k] * NU * NX + u * NX + ck[k]] = (double)z[k][u];
     }
     __syncthreads();
     // ---------------- control rows (one block each; b = ±e_i, b̂ = 0) ----------------
-    const int gpk = (I.n_groups > 0) ? I.n_groups / T : 0;
+    double prp = (double)arp, prd = (double)ard;
     for (int g = tid; g < I.n_groups; g += NT) {
       const int2 gr = D.groups[I.grp0 + g];
       for (int q = 0; q < gr.y; ++q) {
@@ -348,10 +447,10 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
         double lrp = 0, lrd = 0;
 #pragma unroll
         for (int c = 0; c < NX; ++c) {
-          const Real y = sg * gtCur[k * GS + iu * NX + c];
+          const Real y = sg * (Real)gtc_arena[(long long)k * NU * NX + iu * NX + c];
           Real l = lam[e0 + c];
           if (!first) {
-            const Real yo = sg * gtOld[k * GS + iu * NX + c];
+            const Real yo = sg * (Real)gto_arena[(long long)k * NU * NX + iu * NX + c];
             const Real nu = sold * (yo + l);
             const Real ln = l + y - nu;
             lrp += (double)((y - nu) * (y - nu));
@@ -405,10 +504,6 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     const double escale = (sqrt(en) <= sc[SC_RTRUST]) ? 1.0 : sc[SC_RTRUST] / sqrt(en);
     for (int q = tid; q < T * NX; q += NT) ar[L.e + NX + q] = escale * (ar[L.dx + NX + q] + ar[L.lam_e + NX + q]);
     __syncthreads();
-
-    // ---------------- (c) gain update: K^b from Z' (thread per step) ----------------
-    for (int m = tid; m < T; m += NT)
-      gain_solve_step<NX, NU, Real>(ar, L, m, I.sqrt_tau, rho * I.sqrt_tau, 0.0, nullptr, ar + L.K1, gtOld, ar + L.Gt1);
     // Riccati linear terms: q_t = 2Q_x(x̂_t - x_g) - ρ(e_t - λ_e,t) + (ρ/2) Σ_{rows at t} d_j a_j
     for (int q = tid; q < T * NX; q += NT) {
       const int t = q / NX + 1, c = q % NX;
@@ -424,20 +519,20 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     for (int q = tid; q < T * NU; q += NT) {
       const int k = q / NU, iu = q % NU;
       double v = 2.0 * ar[L.Ru + iu] * (sa[SL.u_hat + q] - ar[L.uref + iu]);
-      if (gpk > 0) {
-        for (int g = k * gpk; g < (k + 1) * gpk; ++g) {
-          const int2 gr = D.groups[I.grp0 + g];
-          for (int qq = 0; qq < gr.y; ++qq) {
-            const int4 ri = D.rinfo[gr.x + qq];
-            if (ri.z == iu) v += 0.5 * rho * ((ri.y == ROW_UHI) ? 1.0 : -1.0) * D.dd[gr.x + qq];
-          }
+      for (int g = k * gpk; g < (k + 1) * gpk; ++g) {
+        const int2 gr = D.groups[I.grp0 + g];
+        for (int qq = 0; qq < gr.y; ++qq) {
+          const int4 ri = D.rinfo[gr.x + qq];
+          if (ri.z == iu) v += 0.5 * rho * ((ri.y == ROW_UHI) ? 1.0 : -1.0) * D.dd[gr.x + qq];
         }
       }
       ar[L.rv + q] = v;
     }
     for (int q = tid; q < (T + 1) * NX; q += NT) ar[L.dx_prev + q] = ar[L.dx + q];
     __syncthreads();
-    { Real* t2 = gtOld; gtOld = gtCur; gtCur = t2; }
+    // ---------------- (c) gain update: K^b from Z'; Gtᵀ^b replaces the previous table ----------------
+    gain_solve<NX, NU, Real>(ar, L, T, I.sqrt_tau, rho * I.sqrt_tau, 0.0, ar + L.K1, ar + (gsel ? L.Gt0 : L.Gt1));
+    gsel ^= 1;
     // ---------------- (b) Block 2: Riccati sweep (warp 0) ----------------
     if (warp == 0) riccati_sweep<NX, NU, Real>(ar, L, sa, SL, T, sm.vec);
     __syncthreads();
@@ -478,6 +573,11 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     if (tid == 0) { sc[SC_SCAL_RP] = a_rp; sc[SC_SCAL_RD] = a_rd; sc[SC_SCAL_RPP] = a_rpp; sc[SC_SCAL_RDP] = a_rdp; }
     __syncthreads();
   }
+done:
+  // On a copy timeout the other buffer may still have a copy in flight: wait for it (bounded).
+  if (status == ST_TIMEOUT && tid == 0) {
+    for (int k = 0; k < 2; ++k) (void)mbar_wait_bounded(&bars[k], phase[k]);
+  }
   if (tid == 0) {
     sc[SC_RP] = r_p; sc[SC_RD] = r_d;
     sc[SC_RPP] = sqrt(sc[SC_SCAL_RPP]); sc[SC_RDP] = rho * sqrt(sc[SC_SCAL_RDP]);
@@ -487,18 +587,28 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
 }
 
 template <int NX, int NU, typename Real>
-__global__ void __launch_bounds__(FACfg<NX, NU>::NT, 1) k_fulladmm(Dev<Real> D, SolveParams sp) {
+__global__ void __launch_bounds__(FACfg<NX, NU, Real>::NT, 1) k_fulladmm(Dev<Real> D, SolveParams sp) {
   extern __shared__ __align__(16) char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int s_next, s_flag;
   FASmem<NX, NU, Real> sm;
-  sm.carve(smem_raw, sp.tmax, sp.chunk, sp.max_rows);
-  __shared__ int s_next;
+  sm.carve(smem_raw, sp.chunk, sp.max_rows);
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t ph[2] = {0u, 0u};
   while (true) {
     if (threadIdx.x == 0) s_next = atomicAdd(D.queue + sp.queue_idx, 1);
     __syncthreads();
     const int q = s_next;
     __syncthreads();
     if (q >= sp.n_order) break;
-    fulladmm_instance<NX, NU, Real>(D, sp, D.order[sp.order0 + q], sm);
+    const int inst = D.order[sp.order0 + q];
+    fulladmm_instance<NX, NU, Real>(D, sp, inst, sm, bars, ph, &s_flag);
+    if (D.is[inst * NIS + IS_STATUS] == ST_TIMEOUT) break;
   }
 }
 

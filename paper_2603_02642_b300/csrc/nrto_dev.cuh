@@ -25,7 +25,7 @@ enum : int { KIND_UNICYCLE = 0, KIND_QUADCOPTER = 1, KIND_ARM = 2 };
 // row codes (int4.y of the row table)
 enum : int { ROW_SPHERE = 0, ROW_XHI = 1, ROW_XLO = 2, ROW_UHI = 3, ROW_ULO = 4 };
 // instance status
-enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NUMERIC = 3 };
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NUMERIC = 3, ST_TIMEOUT = 4 };
 
 constexpr int MAX_DYN = 24;
 
@@ -48,13 +48,27 @@ struct Inst {
   double dt, tau, sqrt_tau;
 };
 
+// One solver chunk: a run of whole state rows staged together in shared memory.  Entry and b
+// ranges start 16-byte aligned (the host pads the row layout at every chunk start).
+struct ChunkInfo {
+  long long e0, b0;     // first entry / first b value of the chunk (global indices)
+  int r0, r1;           // local state-row range [r0, r1) of the instance
+  int ne, nb;           // entries / b values to copy, rounded up to 4 (16-byte multiples)
+  int pad0, pad1;
+};
+
+// Per state row, offsets relative to its chunk (copied to shared memory with the chunk).
+struct RowMeta {
+  int off, boff, t, pad;
+};
+
 // Offsets (in doubles) inside one instance's arena.
 struct Arena {
   long long x0, xg, uref, Qx, Ru, RK, ulo, uhi, xlo, xhi, dyn, obs, link, Sigma;
   long long Psi, SigU, SigL, Phi;
   long long K0, K1, Kt, Kacc, Gt0, Gt1, Zp;
   long long du, dx, du_prev, dx_prev, e, lam_e, qv, rv;
-  long long Pf, Gam, Dv, RicL, RicAcl, RicN, RicM;
+  long long Pf, Gam, Dv, RicL, RicAcl, RicN, RicM, Ws1, Ws2;
   long long total;
 };
 
@@ -76,7 +90,7 @@ NRTO_HD Arena arena_layout(int nx, int nu, int T, int n_obs, int n_link) {
   a.rv = take((long long)T * nu);
   a.Pf = take((long long)T * nu * nu); a.Gam = take((long long)T * nu); a.Dv = take(g);
   a.RicL = take(g); a.RicAcl = take((long long)T * nx * nx); a.RicN = take((long long)T * nu * nu);
-  a.RicM = take(g);
+  a.RicM = take(g); a.Ws1 = take(g); a.Ws2 = take(g);
   a.total = o;
   return a;
 }
@@ -121,7 +135,8 @@ struct Dev {
   const int4* rinfo;            // per row: {t or k, code, a, b}
   const long long* rent;        // per row: first entry
   const long long* rbent;       // per state row: first bvec value (global row index)
-  const int* cbound;            // chunk boundaries (local state-row indices), n_chunks+1 per instance
+  const ChunkInfo* chunks;      // n_chunks per instance at Inst::cb0
+  const RowMeta* rmeta;         // per row (state rows only)
   const int2* groups;           // control groups: {first global row, count}, per instance at grp0
   LinSlot<Real> slot[2];
   Real* lam;                    // λ_ν or η̃ rows
