@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--n-outer", type=int, default=10)
     ap.add_argument("--max-inner", type=int, default=500)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--rho", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -191,7 +192,7 @@ def main():
     prec = nrto.PREC_MIXED if args.prec == "mixed" else nrto.PREC_FP64
     stream = torch.cuda.current_stream()
     prob = nrto.Problem(insts, prec, stream=stream.cuda_stream)
-    opts = nrto.Options(rho=10.0, max_inner=args.max_inner, eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0)
+    opts = nrto.Options(rho=args.rho, max_inner=args.max_inner, eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0)
 
     def barrier():
         if ws > 1:
@@ -217,6 +218,9 @@ def main():
     barrier()
     ms = ev0.elapsed_time(ev1)
     solver_ms, solver_launches = prob.profile(False)
+    phases = prob.phase_cycles()
+    tot = max(sum(phases.values()), 1)
+    phase_share = {k: round(v / tot, 4) for k, v in phases.items()}
     launches = prob.kernel_launches() - launches0
     if clk:
         clk.terminate()
@@ -274,7 +278,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == nrto.PREC_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": f"batch{args.n}_mixed_unicycle_quadcopter", "instances_per_gpu": args.n,
-                       "n_outer": args.n_outer, "max_inner": args.max_inner, "precision": args.prec,
+                       "n_outer": args.n_outer, "max_inner": args.max_inner, "precision": args.prec, "rho": args.rho,
                        "l2": "inputs larger than L2 (row arrays of several GB)",
                        "inner_iters_per_solve_mean": float(np.mean(iters)),
                        "final_inner_converged_frac": conv / prob.n,
@@ -285,6 +289,7 @@ def main():
                          "peak_source": peak_kind, "avg_launch_ms": avg_launch_s * 1000.0,
                          "launches": int(solver_launches),
                          "algorithmic_bytes_per_launch": bytes_step / max(launches_per_step, 1e-30)},
+            "phase_share": phase_share,
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -182,6 +182,14 @@ nrto_status nrto_import(nrto_problem_t p, int field, int instance, const double*
  * Synchronizes the stream when events are pending. */
 nrto_status nrto_profile(nrto_problem_t p, int enable, double* solver_ms, long long* solver_launches);
 
+/* Per-phase SM cycles of the inner-loop kernels, summed over CTAs (thread 0 of each CTA marks the
+ * phase boundaries), recorded while nrto_profile recording is enabled; returned and cleared.
+ * Phases: 0 initialization, 1 row pass (cone projections, λ_ν update, Z' accumulation), 2 control
+ * rows and residual reduction, 3 orthant/ball slacks, 4 Riccati linear terms, 5 gain solve,
+ * 6 Riccati sweep, 7 scalar duals.  n must be >= NRTO_NPHASE. */
+#define NRTO_NPHASE 8
+nrto_status nrto_phase_cycles(nrto_problem_t p, long long* cycles, int n);
+
 /* Number of kernel launches the library issued since create (all of its own kernels). */
 long long nrto_kernel_launches(nrto_problem_t p);
 

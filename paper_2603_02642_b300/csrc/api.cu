@@ -170,6 +170,7 @@ struct nrto_problem {
   int* d_is = nullptr;
   int* d_queue = nullptr;
   int* d_order = nullptr;
+  unsigned long long* d_phase = nullptr;
   double* d_stage = nullptr;
   long long* d_stage_off = nullptr;
   long long* d_stage_len = nullptr;
@@ -218,6 +219,7 @@ struct nrto_problem {
     D.p = d_p; D.pt = d_pt; D.ptn = d_ptn; D.lamp = d_lamp; D.w = d_w; D.lamw = d_lamw; D.s = d_s;
     D.ell = d_ell; D.dd = d_dd; D.rnorm = d_rnorm;
     D.sc = d_sc; D.is = d_is; D.queue = d_queue; D.order = d_order;
+    D.phase_cycles = profiling ? d_phase : nullptr;
     return D;
   }
   void check_launch(const char* what) {
@@ -532,7 +534,7 @@ long long field_count(const Inst& I, int f) {
     case NRTO_F_G0: case NRTO_F_P: case NRTO_F_PT: case NRTO_F_LAMP: return I.n_sr + I.n_cr;
     case NRTO_F_BHAT: return I.n_ent_state;
     case NRTO_F_BVEC: return (I.n_ent_state / I.nx) * I.nu;
-    case NRTO_F_LAMNU: return I.n_ent;
+    case NRTO_F_LAMNU: return I.n_ent_state + (long long)I.n_cr * I.nx;
     case NRTO_F_K: case NRTO_F_KACC: return (long long)I.T * I.nu * I.nx;
     case NRTO_F_GM: return (long long)I.T * I.nu * I.nu;
     case NRTO_F_SCAL: return 8;
@@ -812,6 +814,7 @@ nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int preci
     P->d_sc = P->dalloc<double>((size_t)n * NSC);
     P->d_is = P->dalloc<int>((size_t)n * NIS);
     P->d_queue = P->dalloc<int>(8);
+    P->d_phase = P->dalloc<unsigned long long>(NPHASE);
     P->d_order = P->dalloc<int>(n);
     P->d_stage = P->dalloc<double>(stage);
     P->d_stage_off = P->dalloc<long long>(n);
@@ -863,7 +866,8 @@ nrto_status nrto_problem_info(nrto_problem_t p, int i, nrto_instance_info* info)
     const Inst& I = p->h_inst[i];
     info->nx = I.nx; info->nu = I.nu; info->T = I.T;
     info->n_rows = I.n_sr + I.n_cr; info->n_state_rows = I.n_sr; info->n_control_rows = I.n_cr;
-    info->n_entries = I.n_ent; info->n_entries_state = I.n_ent_state;
+    info->n_entries = I.n_ent_state + (long long)I.n_cr * I.nx;   // compact (without layout padding)
+    info->n_entries_state = I.n_ent_state;
     return NRTO_OK;
   } catch (const std::exception& e) {
     return handle(e);
@@ -1048,6 +1052,20 @@ nrto_status nrto_profile(nrto_problem_t p, int enable, double* solver_ms, long l
     p->prof_events.clear();
     p->prof_launches = 0;
     p->profiling = enable != 0;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_phase_cycles(nrto_problem_t p, long long* cycles, int n) {
+  try {
+    if (!p || !cycles || n < NPHASE) fail(NRTO_ERR_INVALID, "need a buffer of NRTO_NPHASE counters");
+    unsigned long long h[NPHASE];
+    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaMemcpy(h, p->d_phase, sizeof(h), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(p->d_phase, 0, sizeof(h)));
+    for (int k = 0; k < NPHASE; ++k) cycles[k] = (long long)h[k];
     return NRTO_OK;
   } catch (const std::exception& e) {
     return handle(e);

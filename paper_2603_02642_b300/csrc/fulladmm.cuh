@@ -252,6 +252,26 @@ __device__ __forceinline__ void load_gt_regs(const double* gt, int T, const int 
       g[k][u] = (mk[k] < T) ? (Real)gt[(long long)mk[k] * NU * NX + u * NX + ck[k]] : (Real)0;
 }
 
+// Phase timer: thread 0 accumulates the SM cycles between consecutive marks (taken right after block
+// barriers) and adds them to the global counters at the end of the instance.
+struct PhaseTimer {
+  unsigned long long acc[NPHASE];
+  long long last;
+  bool on;
+  __device__ void start(bool enable) {
+    on = enable && threadIdx.x == 0;
+    for (int k = 0; k < NPHASE; ++k) acc[k] = 0;
+    last = clock64();
+  }
+  __device__ __forceinline__ void mark(int ph) {
+    if (on) { const long long t = clock64(); acc[ph] += (unsigned long long)(t - last); last = t; }
+  }
+  __device__ void flush(unsigned long long* out) {
+    if (on && out)
+      for (int k = 0; k < NPHASE; ++k) atomicAdd(out + k, acc[k]);
+  }
+};
+
 template <int NX, int NU, typename Real>
 __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int inst, FASmem<NX, NU, Real>& sm,
                                   uint64_t* bars, uint32_t* phase, int* s_flag) {
@@ -272,6 +292,8 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   double* sc = D.sc + (long long)inst * NSC;
   int* isr = D.is + inst * NIS;
   const ChunkInfo* chunks = D.chunks + I.cb0;
+  PhaseTimer tm;
+  tm.start(D.phase_cycles != nullptr);
 
   // this thread's (m, c) columns
   int mk[PAIRS], ck[PAIRS];
@@ -302,6 +324,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   }
   if (tid == 0) { sc[SC_SCAL_RP] = 0; sc[SC_SCAL_RD] = 0; sc[SC_SCAL_RPP] = 0; sc[SC_SCAL_RDP] = 0; }
   __syncthreads();
+  tm.mark(PH_INIT);
   int gsel = 1;           // arena table holding Gtᵀ of the current gains (other one: previous)
   const int Lmax = sp.max_iter;
   int status = ST_MAXITER, iters = 0;
@@ -431,6 +454,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
           for (int u = 0; u < NU; ++u) ar[L.Zp + (long long)mk[k] * NU * NX + u * NX + ck[k]] = (double)z[k][u];
     }
     __syncthreads();
+    tm.mark(PH_ROWS);
     // ---------------- control rows (one block each; b = ±e_i, b̂ = 0) ----------------
     double prp = (double)arp, prd = (double)ard;
     for (int g = tid; g < I.n_groups; g += NT) {
@@ -475,6 +499,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     }
     double z2 = 0.0, z3 = 0.0;
     block_sum4(prp, prd, z2, z3, sm.red);
+    tm.mark(PH_CTRL);
 
     // ---------------- convergence test of iteration b-1 ----------------
     if (!first) {
@@ -504,6 +529,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     const double escale = (sqrt(en) <= sc[SC_RTRUST]) ? 1.0 : sc[SC_RTRUST] / sqrt(en);
     for (int q = tid; q < T * NX; q += NT) ar[L.e + NX + q] = escale * (ar[L.dx + NX + q] + ar[L.lam_e + NX + q]);
     __syncthreads();
+    tm.mark(PH_SCAL1);
     // Riccati linear terms: q_t = 2Q_x(x̂_t - x_g) - ρ(e_t - λ_e,t) + (ρ/2) Σ_{rows at t} d_j a_j
     for (int q = tid; q < T * NX; q += NT) {
       const int t = q / NX + 1, c = q % NX;
@@ -530,12 +556,15 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     }
     for (int q = tid; q < (T + 1) * NX; q += NT) ar[L.dx_prev + q] = ar[L.dx + q];
     __syncthreads();
+    tm.mark(PH_QR);
     // ---------------- (c) gain update: K^b from Z'; Gtᵀ^b replaces the previous table ----------------
     gain_solve<NX, NU, Real>(ar, L, T, I.sqrt_tau, rho * I.sqrt_tau, 0.0, ar + L.K1, ar + (gsel ? L.Gt0 : L.Gt1));
     gsel ^= 1;
+    tm.mark(PH_GAIN);
     // ---------------- (b) Block 2: Riccati sweep (warp 0) ----------------
     if (warp == 0) riccati_sweep<NX, NU, Real>(ar, L, sa, SL, T, sm.vec);
     __syncthreads();
+    tm.mark(PH_RICCATI);
     // ---------------- (d) p, scalar duals, scalar residual parts of iteration b ----------------
     double a_rp = 0, a_rd = 0, a_rpp = 0, a_rdp = 0;
     for (int r = tid; r < n_rows; r += NT) {
@@ -572,6 +601,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     block_sum4(a_rp, a_rd, a_rpp, a_rdp, sm.red);
     if (tid == 0) { sc[SC_SCAL_RP] = a_rp; sc[SC_SCAL_RD] = a_rd; sc[SC_SCAL_RPP] = a_rpp; sc[SC_SCAL_RDP] = a_rdp; }
     __syncthreads();
+    tm.mark(PH_DUALS);
   }
 done:
   // On a copy timeout the other buffer may still have a copy in flight: wait for it (bounded).
@@ -583,6 +613,7 @@ done:
     sc[SC_RPP] = sqrt(sc[SC_SCAL_RPP]); sc[SC_RDP] = rho * sqrt(sc[SC_SCAL_RDP]);
     isr[IS_STATUS] = status; isr[IS_ITERS] = iters; isr[IS_CUMITERS] += iters;
   }
+  tm.flush(D.phase_cycles);
   __syncthreads();
 }
 

@@ -145,7 +145,11 @@ struct Dev {
   int* is;                      // NIS per instance
   int* queue;                   // work counters
   const int* order;             // instance order per launch
+  unsigned long long* phase_cycles;   // NPHASE counters, or null when phase timing is off
 };
+
+// Phases of one inner iteration timed by the persistent solvers (thread 0 of each CTA, SM cycles).
+enum : int { PH_INIT = 0, PH_ROWS, PH_CTRL, PH_SCAL1, PH_QR, PH_GAIN, PH_RICCATI, PH_DUALS, NPHASE };
 
 // ------------------------------------------------------------------------------------------
 // warp helpers

@@ -77,6 +77,8 @@ def load():
     lib.nrto_export.argtypes = [P, C.c_int, C.c_int, _dp, C.c_longlong]
     lib.nrto_import.argtypes = [P, C.c_int, C.c_int, _dp, C.c_longlong]
     lib.nrto_profile.argtypes = [P, C.c_int, _dp, C.POINTER(C.c_longlong)]
+    lib.nrto_phase_cycles.argtypes = [P, C.POINTER(C.c_longlong), C.c_int]
+    lib.nrto_phase_cycles.restype = C.c_int
     lib.nrto_kernel_launches.argtypes = [P]
     lib.nrto_kernel_launches.restype = C.c_longlong
     lib.nrto_last_error.restype = C.c_char_p
@@ -271,6 +273,14 @@ class Problem:
         n = C.c_longlong()
         _check(load().nrto_profile(self._h, int(enable), C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    PHASES = ["init", "rows", "control+reduce", "slacks", "riccati_terms", "gain_solve", "riccati_sweep", "duals"]
+
+    def phase_cycles(self):
+        """Per-phase SM cycles (summed over CTAs) recorded while profiling was enabled; clears them."""
+        buf = (C.c_longlong * 8)()
+        _check(load().nrto_phase_cycles(self._h, buf, 8))
+        return dict(zip(self.PHASES, [int(x) for x in buf]))
 
     def kernel_launches(self):
         return int(load().nrto_kernel_launches(self._h))
