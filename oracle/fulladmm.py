@@ -38,6 +38,19 @@ class FullADMMOptions:
     eps_d: float = 1e-4
     max_iter: int = 500
     check: bool = True          # stop at the first iteration meeting both tolerances
+    # Residual balancing (standard ADMM penalty adaptation; the paper keeps ρ fixed): at the start
+    # of iteration l with (l-1) % adapt_every == 0 and l > adapt_every, look at the residuals of
+    # iteration l-2; ρ ← min(τρ, ρ_max) if r_p > μ r_d, ρ ← max(ρ/τ, ρ_min) if r_d > μ r_p, and the
+    # scaled duals are multiplied by ρ_old/ρ_new.  adapt_every = 0 disables it.
+    adapt_every: int = 0
+    adapt_mu: float = 10.0
+    adapt_tau: float = 2.0
+    rho_min: float = 1e-3
+    rho_max: float = 1e3
+    # Stall stop: at iterations l that are multiples of stall_every (l >= 2·stall_every), stop when
+    # r_p^l > stall_ratio · r_p^{l-stall_every} (and the tolerances are not met).  0 disables it.
+    stall_every: int = 0
+    stall_ratio: float = 0.9
 
 
 @dataclass
@@ -60,6 +73,8 @@ class FullADMMState:
     r_p_paper: float = np.inf
     r_d_paper: float = np.inf
     converged: bool = False
+    stalled: bool = False
+    rho: float = np.nan
     history: list = field(default_factory=list)
 
 
@@ -123,7 +138,22 @@ def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None
     mats = block2_matrices(inst, lin, rho)
     L = opts.max_iter if n_iter is None else n_iter
     Y_prev = P.Ahat_apply(lin, s.K) + lin.bhat
+    rp_mark = np.inf
     for it in range(1, L + 1):
+        A = opts.adapt_every
+        if A > 0 and it > A and (it - 1) % A == 0 and len(s.history) >= it - 2:
+            rp2, rd2 = s.history[it - 3]
+            rho_new = rho
+            if rp2 > opts.adapt_mu * rd2:
+                rho_new = min(rho * opts.adapt_tau, opts.rho_max)
+            elif rd2 > opts.adapt_mu * rp2:
+                rho_new = max(rho / opts.adapt_tau, opts.rho_min)
+            if rho_new != rho:
+                f = rho / rho_new
+                s.lam_p, s.lam_nu, s.lam_w, s.lam_e = s.lam_p * f, s.lam_nu * f, s.lam_w * f, s.lam_e * f
+                rho = rho_new
+                H = P.gain_hessian_blocks(lin, inst, coef=rho)
+                mats = block2_matrices(inst, lin, rho)
         # Block 1 (13): per-row SOC projection of (Â_j k + b̂_j + λ_ν,j, p_j + λ_p,j);
         # lifted slacks: orthant for w, ball for e.
         Y = Y_prev
@@ -154,9 +184,15 @@ def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None
         s = FullADMMState(K=K_new, du=du, dx=dx, p=p, pt=pt_new, lam_p=lam_p, lam_nu=lam_nu,
                           w=w, lam_w=lam_w, e=e, lam_e=lam_e, nu=nu, iters=s.iters + 1,
                           r_p=float(r_p), r_d=float(r_d), r_p_paper=r_p_paper, r_d_paper=r_d_paper,
-                          history=s.history + [(float(r_p), float(r_d))])
+                          rho=rho, history=s.history + [(float(r_p), float(r_d))])
         Y_prev = Y_new
         if opts.check and r_p <= opts.eps_p and r_d <= opts.eps_d:
             s.converged = True
             break
+        S_ = opts.stall_every
+        if opts.check and S_ > 0 and it % S_ == 0:
+            if it >= 2 * S_ and r_p > opts.stall_ratio * rp_mark:
+                s.stalled = True
+                break
+            rp_mark = r_p
     return s

@@ -187,28 +187,65 @@ __device__ void gain_solve(double* ar, const Arena& L, int T, double sqrt_tau, d
 
 // Block-2 (δû) LQ sweep with fixed factors (warp 0 only).  Linear terms q_t (t = 0..T, index t
 // of qv; q_0 unused) and r_k in the arena.  Writes du, dx.  Arithmetic in Real.
+// Each lane keeps the factor rows it needs for one step in registers and loads the next step's rows
+// before the current step's dependent arithmetic, so the 2T dependent steps do not each wait for L2.
 template <int NX, int NU, typename Real>
 __device__ void riccati_sweep(double* ar, const Arena& L, const double* sa, const SlotL& SL, int T, double* pv) {
   const int lane = threadIdx.x & 31;
-  // backward: l_k = -(N_k r_k + M_k p_{k+1}),  p_k = q_k + Acl_kᵀ p_{k+1} + L_kᵀ r_k
-  if (lane < NX) pv[lane] = ar[L.qv + (long long)T * NX + lane];
-  __syncwarp();
-  for (int k = T - 1; k >= 0; --k) {
+  // lane j < NX: column j of Acl_k and of L_k, q_k[j];   lane j < NU: row j of N_k and of M_k, r_k
+  Real acl[NX], lk[NU], nrow[NU], mrow[NX], rr[NU];
+  Real qk = 0;
+  auto load_back = [&](int k) {
     const double* N = ar + L.RicN + (long long)k * NU * NU;
     const double* M = ar + L.RicM + (long long)k * NU * NX;
     const double* Lk = ar + L.RicL + (long long)k * NU * NX;
     const double* Acl = ar + L.RicAcl + (long long)k * NX * NX;
     const double* r = ar + L.rv + (long long)k * NU;
-    Real lv = 0, pn = 0;
+#pragma unroll
+    for (int v = 0; v < NU; ++v) rr[v] = (Real)r[v];
+    if (lane < NX) {
+#pragma unroll
+      for (int c = 0; c < NX; ++c) acl[c] = (Real)Acl[c * NX + lane];
+#pragma unroll
+      for (int v = 0; v < NU; ++v) lk[v] = (Real)Lk[v * NX + lane];
+      qk = (Real)ar[L.qv + (long long)k * NX + lane];
+    }
     if (lane < NU) {
-      for (int v = 0; v < NU; ++v) lv += (Real)N[lane * NU + v] * (Real)r[v];
-      for (int c = 0; c < NX; ++c) lv += (Real)M[lane * NX + c] * (Real)pv[c];
+#pragma unroll
+      for (int v = 0; v < NU; ++v) nrow[v] = (Real)N[lane * NU + v];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) mrow[c] = (Real)M[lane * NX + c];
+    }
+  };
+  // backward: l_k = -(N_k r_k + M_k p_{k+1}),  p_k = q_k + Acl_kᵀ p_{k+1} + L_kᵀ r_k
+  if (lane < NX) pv[lane] = ar[L.qv + (long long)T * NX + lane];
+  load_back(T - 1);
+  __syncwarp();
+  for (int k = T - 1; k >= 0; --k) {
+    Real acl_c[NX], lk_c[NU], n_c[NU], m_c[NX], r_c[NU];
+    const Real q_c = qk;
+#pragma unroll
+    for (int c = 0; c < NX; ++c) { acl_c[c] = acl[c]; m_c[c] = mrow[c]; }
+#pragma unroll
+    for (int v = 0; v < NU; ++v) { lk_c[v] = lk[v]; n_c[v] = nrow[v]; r_c[v] = rr[v]; }
+    if (k >= 1) load_back(k - 1);
+    Real p_in[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) p_in[c] = (Real)pv[c];
+    if (lane < NU) {
+      Real lv = 0;
+#pragma unroll
+      for (int v = 0; v < NU; ++v) lv += n_c[v] * r_c[v];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) lv += m_c[c] * p_in[c];
       ar[L.du + (long long)k * NU + lane] = -(double)lv;   // l_k stored in du until the forward pass
     }
+    Real pn = q_c;
     if (lane < NX && k >= 1) {
-      pn = (Real)ar[L.qv + (long long)k * NX + lane];
-      for (int c = 0; c < NX; ++c) pn += (Real)Acl[c * NX + lane] * (Real)pv[c];
-      for (int v = 0; v < NU; ++v) pn += (Real)Lk[v * NX + lane] * (Real)r[v];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) pn += acl_c[c] * p_in[c];
+#pragma unroll
+      for (int v = 0; v < NU; ++v) pn += lk_c[v] * r_c[v];
     }
     __syncwarp();
     if (lane < NX && k >= 1) pv[lane] = (double)pn;
@@ -217,28 +254,60 @@ __device__ void riccati_sweep(double* ar, const Arena& L, const double* sa, cons
   // forward: δx_0 = 0, δu_k = L_k δx_k + l_k, δx_{k+1} = A_k δx_k + B_k δu_k
   double* dx = ar + L.dx;
   double* du = ar + L.du;
-  if (lane < NX) dx[lane] = 0.0;
-  __syncwarp();
-  for (int k = 0; k < T; ++k) {
+  // lane j < NU: row j of L_k, l_k[j];   lane j < NX: row j of A_k and of B_k
+  Real lrow[NX], arow[NX], brow[NU];
+  Real lkv = 0;
+  auto load_fwd = [&](int k) {
     const double* Lk = ar + L.RicL + (long long)k * NU * NX;
     const double* A = sa + SL.A + (long long)k * NX * NX;
     const double* B = sa + SL.B + (long long)k * NX * NU;
-    Real u = 0;
     if (lane < NU) {
-      u = (Real)du[(long long)k * NU + lane];
-      for (int c = 0; c < NX; ++c) u += (Real)Lk[lane * NX + c] * (Real)dx[(long long)k * NX + c];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) lrow[c] = (Real)Lk[lane * NX + c];
+      lkv = (Real)du[(long long)k * NU + lane];
     }
-    __syncwarp();
-    if (lane < NU) du[(long long)k * NU + lane] = (double)u;
-    __syncwarp();
     if (lane < NX) {
-      Real x = 0;
-      for (int c = 0; c < NX; ++c) x += (Real)A[lane * NX + c] * (Real)dx[(long long)k * NX + c];
-      for (int v = 0; v < NU; ++v) x += (Real)B[lane * NU + v] * (Real)du[(long long)k * NU + v];
-      dx[(long long)(k + 1) * NX + lane] = (double)x;
+#pragma unroll
+      for (int c = 0; c < NX; ++c) arow[c] = (Real)A[lane * NX + c];
+#pragma unroll
+      for (int v = 0; v < NU; ++v) brow[v] = (Real)B[lane * NU + v];
     }
-    __syncwarp();
+  };
+  Real xk[NX];
+#pragma unroll
+  for (int c = 0; c < NX; ++c) xk[c] = 0;
+  if (lane < NX) dx[lane] = 0.0;
+  load_fwd(0);
+  for (int k = 0; k < T; ++k) {
+    Real l_c[NX], a_c[NX], b_c[NU];
+    const Real lk0 = lkv;
+#pragma unroll
+    for (int c = 0; c < NX; ++c) { l_c[c] = lrow[c]; a_c[c] = arow[c]; }
+#pragma unroll
+    for (int v = 0; v < NU; ++v) b_c[v] = brow[v];
+    if (k + 1 < T) load_fwd(k + 1);
+    // every lane holds the full δx_k (xk); δu_k is formed by lanes < NU and broadcast by shuffles
+    Real u = lk0;
+    if (lane < NU) {
+#pragma unroll
+      for (int c = 0; c < NX; ++c) u += l_c[c] * xk[c];
+      du[(long long)k * NU + lane] = (double)u;
+    }
+    Real uk[NU];
+#pragma unroll
+    for (int v = 0; v < NU; ++v) uk[v] = __shfl_sync(0xffffffffu, u, v);
+    Real xn = 0;
+    if (lane < NX) {
+#pragma unroll
+      for (int c = 0; c < NX; ++c) xn += a_c[c] * xk[c];
+#pragma unroll
+      for (int v = 0; v < NU; ++v) xn += b_c[v] * uk[v];
+      dx[(long long)(k + 1) * NX + lane] = (double)xn;
+    }
+#pragma unroll
+    for (int c = 0; c < NX; ++c) xk[c] = __shfl_sync(0xffffffffu, xn, c);
   }
+  __syncwarp();
 }
 
 // Load the gain-table registers of this thread's columns from an arena Gtᵀ table ((T+1)×NU×NX).

@@ -161,3 +161,26 @@ def test_iterates_are_deterministic_and_warm_start_shapes():
     ws = F.warm_state(lin, a.K, a.pt, a.lam_p)
     c = F.iterate(inst, lin, o, ws, n_iter=1)
     assert c.iters == 1 and np.isfinite(c.r_p)
+
+
+def test_adaptive_rho_reaches_the_same_fixed_point():
+    """Residual balancing changes the path, not the solution: the adaptive loop converges to the
+    interior-point solution of Problem 2 as the fixed-ρ loop does."""
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    du_ip, K_ip = problem2_ip(inst, lin, r=0.5)
+    s = F.iterate(inst, lin, F.FullADMMOptions(rho=100.0, r_trust=0.5, eps_p=1e-9, eps_d=1e-9, max_iter=30000,
+                                               adapt_every=25))
+    assert s.converged and s.rho < 100.0
+    assert np.allclose(s.du, du_ip, atol=2e-6) and np.allclose(s.K, K_ip, atol=2e-6)
+
+
+def test_stall_stop_on_infeasible_linearization():
+    """A trust radius too small to clear an obstacle that the nominal crosses makes Problem 2
+    infeasible: the primal residual plateaus and the stall rule stops the loop."""
+    inst = tiny_unicycle()
+    inst.obs_center = np.array([[0.5, 0.0]])           # on the nominal path
+    inst.obs_radius = np.array([0.3])
+    lin = P.linearize(inst, inst.u_init)
+    s = F.iterate(inst, lin, F.FullADMMOptions(rho=1.0, r_trust=0.01, max_iter=5000, stall_every=100))
+    assert s.stalled and not s.converged and s.iters < 5000 and s.r_p > 1e-3
