@@ -85,6 +85,15 @@ typedef struct {
   int max_dr;          /* DR iterations cap per ADMM iteration                                   */
   int check;           /* 1: stop at tolerance; 0: run exactly max_inner iterations             */
   double r0, r_min, w_p;  /* outer loop: initial/max trust radius, minimum radius, merit weight   */
+  /* FullADMM residual balancing (standard ADMM penalty adaptation; the paper keeps ρ fixed): every
+   * adapt_every iterations ρ ← min(τρ, ρ_max) if r_p > μ r_d, ρ ← max(ρ/τ, ρ_min) if r_d > μ r_p,
+   * using the residuals of the iteration before last; scaled duals are rescaled.  0 disables it. */
+  int adapt_every;
+  double adapt_mu, adapt_tau, rho_min, rho_max;
+  /* Stall stop: every stall_every iterations, stop when r_p fell by less than the factor
+   * stall_ratio since the previous checkpoint (status 5).  0 disables it. */
+  int stall_every;
+  double stall_ratio;
 } nrto_solver_opts;
 
 /* Per-instance sizes, for sizing output buffers. */
@@ -104,7 +113,8 @@ typedef struct {
   int* iters;          /* n            iterations run                                            */
   double* r_p;         /* n            full primal residual                                      */
   double* r_d;         /* n            full dual residual                                        */
-  int* status;         /* n            1 converged, 2 iteration cap, 3 non-finite                 */
+  int* status;         /* n            1 converged, 2 iteration cap, 3 non-finite, 4 copy timeout,
+                                        5 stalled (primal residual stopped decreasing)            */
 } nrto_socp_out;
 
 typedef struct nrto_problem* nrto_problem_t;
@@ -170,8 +180,8 @@ enum {
   NRTO_F_KACC = 14,  /* T*nu*nx    gains of the accepted nominal (outer loop)                 */
   NRTO_F_DX = 15,    /* (T+1)*nx   δx of the last inner solve                                */
   NRTO_F_SCAL = 16,  /* 8: r_p, r_d, r_p(paper), r_d(paper), merit, candidate merit, cost, trust r */
-  NRTO_F_STATS = 17  /* 4, read-only: inner iterations since the last nrto_solve reset, iterations of
-                        the last inner solve, its status, accepted outer steps                     */
+  NRTO_F_STATS = 17  /* 5, read-only: inner iterations since the last nrto_solve reset, iterations of
+                        the last inner solve, its status, accepted outer steps, its final ρ         */
 };
 nrto_status nrto_export(nrto_problem_t p, int field, int instance, double* dst, long long count);
 nrto_status nrto_import(nrto_problem_t p, int field, int instance, const double* src, long long count);

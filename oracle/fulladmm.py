@@ -141,7 +141,7 @@ def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None
     rp_mark = np.inf
     for it in range(1, L + 1):
         A = opts.adapt_every
-        if A > 0 and it > A and (it - 1) % A == 0 and len(s.history) >= it - 2:
+        if A > 0 and it >= 3 and it > A and (it - 1) % A == 0:
             rp2, rd2 = s.history[it - 3]
             rho_new = rho
             if rp2 > opts.adapt_mu * rd2:

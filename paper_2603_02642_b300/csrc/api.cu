@@ -43,7 +43,8 @@ int kind_nu(int k) { return k == KIND_UNICYCLE ? 2 : (k == KIND_QUADCOPTER ? 4 :
 int kind_tmax(int k) { return k == KIND_UNICYCLE ? 256 : (k == KIND_QUADCOPTER ? 160 : 128); }
 
 // opt-in shared memory per block on sm_103a is 227 KB; keep 1 KB for static shared variables
-constexpr int SMEM_BUDGET = 227 * 1024 - 1024;
+// (static shared memory of the solver: mbarriers, flags and the Riccati scratch, about 9.5 KB)
+constexpr int SMEM_BUDGET = 227 * 1024 - 12 * 1024;
 
 template <typename Real>
 size_t smem_for(int kind, int chunk, int max_rows) {
@@ -382,6 +383,9 @@ void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
   sp.rho = o.rho; sp.eps_p = o.eps_p; sp.eps_d = o.eps_d;
   sp.alpha = o.alpha; sp.r_chi = o.r_chi; sp.sigma = o.sigma; sp.eps_dr = o.eps_dr;
   sp.max_iter = o.max_inner; sp.check = o.check; sp.warm = P->warm_pending ? 1 : 0; sp.max_dr = o.max_dr;
+  sp.adapt_every = o.adapt_every; sp.stall_every = o.stall_every;
+  sp.adapt_mu = o.adapt_mu; sp.adapt_tau = o.adapt_tau; sp.rho_min = o.rho_min; sp.rho_max = o.rho_max;
+  sp.stall_ratio = o.stall_ratio;
   P->warm_pending = false;
   if (o.solver == NRTO_SOLVER_FULLADMM) {
     k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.rho, 0.0);
@@ -495,6 +499,10 @@ void check_opts(const nrto_solver_opts* o) {
   if (o->solver != NRTO_SOLVER_DR && o->solver != NRTO_SOLVER_FULLADMM) fail(NRTO_ERR_INVALID, "unknown solver");
   if (!(o->rho > 0)) fail(NRTO_ERR_INVALID, "rho must be positive");
   if (o->max_inner < 0 || o->max_inner > 1000000) fail(NRTO_ERR_INVALID, "max_inner out of range");
+  if (o->adapt_every < 0 || o->stall_every < 0) fail(NRTO_ERR_INVALID, "adapt_every and stall_every must be >= 0");
+  if (o->adapt_every > 0 && !(o->adapt_mu > 1 && o->adapt_tau > 1 && o->rho_min > 0 && o->rho_max >= o->rho_min))
+    fail(NRTO_ERR_INVALID, "residual balancing needs mu > 1, tau > 1, 0 < rho_min <= rho_max");
+  if (o->stall_every > 0 && !(o->stall_ratio > 0 && o->stall_ratio < 1)) fail(NRTO_ERR_INVALID, "stall_ratio must be in (0,1)");
   if (o->solver == NRTO_SOLVER_DR) {
     if (!(o->alpha > 0 && o->alpha < 2)) fail(NRTO_ERR_INVALID, "alpha must be in (0,2)");
     if (!(o->r_chi > 0) || !(o->sigma > 0)) fail(NRTO_ERR_INVALID, "r_chi and sigma must be positive");
@@ -538,7 +546,7 @@ long long field_count(const Inst& I, int f) {
     case NRTO_F_K: case NRTO_F_KACC: return (long long)I.T * I.nu * I.nx;
     case NRTO_F_GM: return (long long)I.T * I.nu * I.nu;
     case NRTO_F_SCAL: return 8;
-    case NRTO_F_STATS: return 4;
+    case NRTO_F_STATS: return 5;
   }
   return -1;
 }
@@ -578,7 +586,10 @@ nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long 
       case NRTO_F_LAMNU: rptr = static_cast<char*>(p->d_lam) + rs * I.ent0; break;
       case NRTO_F_STATS: {
         if (!to_host) fail(NRTO_ERR_INVALID, "stats are read-only");
+        double scv[NSC];
+        CK(cudaMemcpy(scv, p->d_sc + (long long)i * NSC, sizeof(scv), cudaMemcpyDeviceToHost));
         buf[0] = is[IS_CUMITERS]; buf[1] = is[IS_ITERS]; buf[2] = is[IS_STATUS]; buf[3] = is[IS_NACC];
+        buf[4] = scv[SC_RHO];
         return NRTO_OK;
       }
       case NRTO_F_SCAL: {

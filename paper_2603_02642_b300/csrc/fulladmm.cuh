@@ -32,6 +32,8 @@ struct SolveParams {
   int max_iter, check, warm, max_dr;
   int chunk, max_rows, tmax, n_order;   // chunk entries, rows per chunk, max T of the launch, instances
   int order0, queue_idx;
+  int adapt_every, stall_every;         // residual balancing / stall stop periods (0 = off)
+  double adapt_mu, adapt_tau, rho_min, rho_max, stall_ratio;
 };
 
 template <int NX, int NU, typename Real>
@@ -343,7 +345,7 @@ struct PhaseTimer {
 
 template <int NX, int NU, typename Real>
 __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int inst, FASmem<NX, NU, Real>& sm,
-                                  uint64_t* bars, uint32_t* phase, int* s_flag) {
+                                  uint64_t* bars, uint32_t* phase, int* s_flag, double* ric_scr) {
   using C = FACfg<NX, NU, Real>;
   constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR = C::NWR;
   const Inst I = D.inst[inst];
@@ -355,7 +357,9 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   const double* sa = S.arena + I.slot0;
   const int T = I.T;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double rho = sp.rho;
+  double rho = sp.rho;        // penalty of the current iteration (residual balancing may change it)
+  double rho_done = rho;      // penalty of the last iteration whose residuals were checked
+  double rp_mark = 0.0;       // r_p at the previous stall checkpoint
   const int n_rows = I.n_sr + I.n_cr;
   Real* lam = D.lam;
   double* sc = D.sc + (long long)inst * NSC;
@@ -413,6 +417,29 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
 #pragma unroll
       for (int u = 0; u < NU; ++u) z[k][u] = (Real)0;
     Real arp = 0, ard = 0;
+    const double rho_prev = rho;   // penalty of iteration b-1
+    Real lscale = (Real)1;         // rescale of the scaled dual λ_ν^{b-1} when ρ changes for iteration b
+
+    // ---------------- residual balancing at the start of iteration b (uses iteration b-2) ----------------
+    if (block1 && sp.adapt_every > 0 && b >= 3 && b > sp.adapt_every && (b - 1) % sp.adapt_every == 0) {
+      double rn = rho;
+      if (r_p > sp.adapt_mu * r_d) rn = fmin(rho * sp.adapt_tau, sp.rho_max);
+      else if (r_d > sp.adapt_mu * r_p) rn = fmax(rho / sp.adapt_tau, sp.rho_min);
+      if (rn != rho) {
+        const double f = rho / rn;
+        for (int r = tid; r < n_rows; r += NT) {
+          const long long R = I.row0 + r;
+          D.lamp[R] *= f;
+          D.lamw[R] *= f;
+        }
+        for (int q = tid; q < (T + 1) * NX; q += NT) ar[L.lam_e + q] *= f;
+        lscale = (Real)f;
+        rho = rn;
+        gain_divisors<Real>(D, inst, rho);
+        __syncthreads();
+        if (warp == 0) riccati_factor_warp<Real>(D, inst, rho, ric_scr);
+      }
+    }
 
     // ---------------- row pass over state rows, chunk by chunk (bulk copies, double buffered) --------
     __syncthreads();
@@ -458,7 +485,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
               const Real ln = l + y - nu;
               arp += (y - nu) * (y - nu);
               ard += (y - yo) * (y - yo);
-              l = ln;
+              l = ln * lscale;
               bf.lam[e] = l;
               lam[cki.e0 + e] = l;
             }
@@ -548,7 +575,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
             const Real ln = l + y - nu;
             lrp += (double)((y - nu) * (y - nu));
             lrd += (double)((y - yo) * (y - yo));
-            l = ln;
+            l = ln * lscale;
             lam[e0 + c] = l;
           }
           lv[c] = l;
@@ -573,11 +600,16 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     // ---------------- convergence test of iteration b-1 ----------------
     if (!first) {
       r_p = sqrt(sc[SC_SCAL_RP] + prp);
-      r_d = rho * sqrt(sc[SC_SCAL_RD] + prd);
+      r_d = rho_prev * sqrt(sc[SC_SCAL_RD] + prd);
+      rho_done = rho_prev;
       iters = b - 1;
       const bool bad = !(r_p == r_p) || !(r_d == r_d) || isinf(r_p) || isinf(r_d);
       if (bad) { status = ST_NUMERIC; break; }
       if (sp.check && r_p <= sp.eps_p && r_d <= sp.eps_d) { status = ST_CONVERGED; break; }
+      if (sp.check && sp.stall_every > 0 && iters % sp.stall_every == 0) {
+        if (iters >= 2 * sp.stall_every && r_p > sp.stall_ratio * rp_mark) { status = ST_STALLED; break; }
+        rp_mark = r_p;
+      }
       if (b - 1 == Lmax) { status = ST_MAXITER; break; }
     }
 
@@ -679,7 +711,8 @@ done:
   }
   if (tid == 0) {
     sc[SC_RP] = r_p; sc[SC_RD] = r_d;
-    sc[SC_RPP] = sqrt(sc[SC_SCAL_RPP]); sc[SC_RDP] = rho * sqrt(sc[SC_SCAL_RDP]);
+    sc[SC_RPP] = sqrt(sc[SC_SCAL_RPP]); sc[SC_RDP] = rho_done * sqrt(sc[SC_SCAL_RDP]);
+    sc[SC_RHO] = rho_done;
     isr[IS_STATUS] = status; isr[IS_ITERS] = iters; isr[IS_CUMITERS] += iters;
   }
   tm.flush(D.phase_cycles);
@@ -691,6 +724,7 @@ __global__ void __launch_bounds__(FACfg<NX, NU, Real>::NT, 1) k_fulladmm(Dev<Rea
   extern __shared__ __align__(16) char smem_raw[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_next, s_flag;
+  __shared__ double ric_scr[RIC_SCRATCH];
   FASmem<NX, NU, Real> sm;
   sm.carve(smem_raw, sp.chunk, sp.max_rows);
   if (threadIdx.x == 0) {
@@ -707,7 +741,7 @@ __global__ void __launch_bounds__(FACfg<NX, NU, Real>::NT, 1) k_fulladmm(Dev<Rea
     __syncthreads();
     if (q >= sp.n_order) break;
     const int inst = D.order[sp.order0 + q];
-    fulladmm_instance<NX, NU, Real>(D, sp, inst, sm, bars, ph, &s_flag);
+    fulladmm_instance<NX, NU, Real>(D, sp, inst, sm, bars, ph, &s_flag, ric_scr);
     if (D.is[inst * NIS + IS_STATUS] == ST_TIMEOUT) break;
   }
 }

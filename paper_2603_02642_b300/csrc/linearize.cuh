@@ -243,10 +243,10 @@ __device__ inline void wmm(double* C, const double* A, bool tA, int lda, const d
 //   R_k = 2R_u + (ρ/2) Σ_{control rows j at k} e_i e_iᵀ,
 // dynamics δx_{k+1} = A_k δx_k + B_k δu_k, δx_0 = 0.  Stores per step
 //   L_k = -Huu⁻¹Hux, Acl_k = A_k + B_k L_k, N_k = Huu⁻¹, M_k = Huu⁻¹ B_kᵀ.
-// One warp per instance (block per instance, blockDim = 32).
+// Run by one warp; `scr` is shared scratch of RIC_SCRATCH doubles.
+constexpr int RIC_SCRATCH = 1176;
 template <typename Real>
-__global__ void k_riccati_factor(Dev<Real> D, double rho) {
-  const int i = blockIdx.x;
+__device__ void riccati_factor_warp(const Dev<Real>& D, int i, double rho, double* scr) {
   const Inst I = D.inst[i];
   const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
   const SlotL SL = slot_layout(I.nx, I.nu, I.T);
@@ -256,7 +256,15 @@ __global__ void k_riccati_factor(Dev<Real> D, double rho) {
   const double* arow = D.slot[sl].arow;
   const int nx = I.nx, nu = I.nu;
   const int lane = threadIdx.x & 31;
-  __shared__ double P[196], PA[196], PB[98], Huu[49], Hux[98], Nm[49], Lm[98], Q[196], tmp[196];
+  double* P = scr;
+  double* PA = P + 196;
+  double* PB = PA + 196;
+  double* Huu = PB + 98;
+  double* Hux = Huu + 49;
+  double* Nm = Hux + 98;
+  double* Lm = Nm + 49;
+  double* Q = Lm + 98;
+  double* tmp = Q + 196;
   auto build_Q = [&](int t) {
     for (int q = lane; q < nx * nx; q += 32) {
       int r = q / nx, c = q % nx;
@@ -330,6 +338,26 @@ __global__ void k_riccati_factor(Dev<Real> D, double rho) {
       }
       __syncwarp();
     }
+  }
+}
+
+// One warp per instance (block per instance, blockDim = 32).
+template <typename Real>
+__global__ void k_riccati_factor(Dev<Real> D, double rho) {
+  __shared__ double scr[RIC_SCRATCH];
+  riccati_factor_warp<Real>(D, blockIdx.x, rho, scr);
+}
+
+// Dv_m[u][c] = 1/(1 + coef τ γ_u λ_c) for a new penalty (the eigen factors do not depend on it).
+template <typename Real>
+__device__ void gain_divisors(const Dev<Real>& D, int i, double coef) {
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  double* ar = D.arena + I.arena0;
+  const int n = I.T * I.nu * I.nx;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int m = q / (I.nu * I.nx), u = (q / I.nx) % I.nu, c = q % I.nx;
+    ar[L.Dv + q] = 1.0 / (1.0 + coef * I.tau * ar[L.Gam + (long long)m * I.nu + u] * ar[L.SigL + (long long)m * I.nx + c]);
   }
 }
 

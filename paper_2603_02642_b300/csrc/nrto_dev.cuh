@@ -25,7 +25,7 @@ enum : int { KIND_UNICYCLE = 0, KIND_QUADCOPTER = 1, KIND_ARM = 2 };
 // row codes (int4.y of the row table)
 enum : int { ROW_SPHERE = 0, ROW_XHI = 1, ROW_XLO = 2, ROW_UHI = 3, ROW_ULO = 4 };
 // instance status
-enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NUMERIC = 3, ST_TIMEOUT = 4 };
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NUMERIC = 3, ST_TIMEOUT = 4, ST_STALLED = 5 };
 
 constexpr int MAX_DYN = 24;
 
@@ -115,7 +115,7 @@ NRTO_HD SlotL slot_layout(int nx, int nu, int T) {
 
 // Per-instance scalar record (double) and integer record.
 enum : int { SC_RTRUST = 0, SC_RP, SC_RD, SC_RPP, SC_RDP, SC_SCAL_RP, SC_SCAL_RD, SC_SCAL_RPP, SC_SCAL_RDP,
-             SC_PHI, SC_PHI_CAND, SC_COST, SC_ENORM, SC_RDR, NSC = 16 };
+             SC_PHI, SC_PHI_CAND, SC_COST, SC_RHO, SC_RDR, NSC = 16 };
 enum : int { IS_STATUS = 0, IS_ITERS, IS_SLOT, IS_ACCEPT, IS_DRITERS, IS_CUMITERS, IS_NACC, NIS = 8 };
 
 template <typename Real>

@@ -116,3 +116,39 @@ def test_mixed_precision_error_bounds(cases, name):
     assert relerr(out["du"][0], s.du) < 5e-5
     assert relerr(out["pt"][0], s.pt) < 5e-5
     prob.close()
+
+
+@pytest.mark.parametrize("name", ["uni_T50_o4", "quad_T40_o5"])
+def test_residual_balancing_iterates_parity_fp64(cases, name):
+    """Iterates with ρ adapted every 5 iterations (starting far from balance) match the oracle's."""
+    inst = cases[name]
+    lin = _lin_oracle(inst)
+    o = F.FullADMMOptions(rho=200.0, r_trust=0.5, check=False, adapt_every=5)
+    s = F.iterate(inst, lin, o, n_iter=40)
+    assert s.rho != 200.0
+    prob = nrto.Problem([inst], nrto.PREC_FP64)
+    prob.linearize()
+    prob.set_trust_radius(0.5)
+    out = prob.solve_socp(nrto.Options(rho=200.0, max_inner=40, check=0, adapt_every=5))
+    st = prob.export(nrto.F_STATS, 0)
+    assert st[4] == s.rho
+    assert_close(out["K"][0], s.K, RTOL64, "K")
+    assert_close(out["du"][0], s.du, RTOL64, "du")
+    assert_close(out["pt"][0], s.pt, RTOL64, "p~")
+    assert_close(prob.export(nrto.F_LAMNU, 0), ragged_from_dense(lin, s.lam_nu), RTOL64, "lambda_nu")
+    assert_close(prob.export(nrto.F_LAMP, 0), s.lam_p, RTOL64, "lambda_p")
+    prob.close()
+
+
+def test_stall_stop_matches_oracle():
+    from .test_oracle_fulladmm import tiny_unicycle
+    inst = tiny_unicycle()
+    inst.obs_center = np.array([[0.5, 0.0]])
+    inst.obs_radius = np.array([0.3])
+    lin = _lin_oracle(inst)
+    s = F.iterate(inst, lin, F.FullADMMOptions(rho=1.0, r_trust=0.01, max_iter=5000, stall_every=100))
+    prob = nrto.Problem([inst], nrto.PREC_FP64)
+    prob.linearize()
+    prob.set_trust_radius(0.01)
+    out = prob.solve_socp(nrto.Options(rho=1.0, max_inner=5000, check=1, stall_every=100))
+    assert s.stalled and out["status"][0] == 5 and out["iters"][0] == s.iters
