@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--max-inner", type=int, default=500)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--rho", type=float, default=10.0)
+    ap.add_argument("--adapt", type=int, default=25, help="residual-balancing period (0 = fixed rho)")
+    ap.add_argument("--stall", type=int, default=100, help="stall-stop period (0 = off)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -192,7 +194,8 @@ def main():
     prec = nrto.PREC_MIXED if args.prec == "mixed" else nrto.PREC_FP64
     stream = torch.cuda.current_stream()
     prob = nrto.Problem(insts, prec, stream=stream.cuda_stream)
-    opts = nrto.Options(rho=args.rho, max_inner=args.max_inner, eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0)
+    opts = nrto.Options(rho=args.rho, max_inner=args.max_inner, eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0,
+                        adapt_every=args.adapt, stall_every=args.stall)
 
     def barrier():
         if ws > 1:
@@ -245,6 +248,7 @@ def main():
     achieved = bytes_step / launches_per_step / avg_launch_s / 1e9
     peak, peak_kind = measured_peak_gbs()
     conv = int(np.sum(stats[:, 2] == 1))
+    stalled = int(np.sum(stats[:, 2] == 5))
 
     # end to end through the C ABI with host buffers: upload the step's problem data, solve, read back
     e2e = None
@@ -278,10 +282,12 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == nrto.PREC_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": f"batch{args.n}_mixed_unicycle_quadcopter", "instances_per_gpu": args.n,
-                       "n_outer": args.n_outer, "max_inner": args.max_inner, "precision": args.prec, "rho": args.rho,
+                       "n_outer": args.n_outer, "max_inner": args.max_inner, "precision": args.prec, "rho0": args.rho,
+                       "adapt_every": args.adapt, "stall_every": args.stall,
                        "l2": "inputs larger than L2 (row arrays of several GB)",
                        "inner_iters_per_solve_mean": float(np.mean(iters)),
                        "final_inner_converged_frac": conv / prob.n,
+                       "final_inner_stalled_frac": stalled / prob.n,
                        "iterations_per_s": ws * float(np.sum(iters)) * args.steps / (ms_max / 1000.0)},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -440,6 +440,13 @@ void choose_chunk(KindLaunch& kl) {
   kl.max_rows = chunk / (2 * nx) + 2;
   kl.smem = smem_for<Real>(kl.kind, chunk, kl.max_rows);
   if (kl.smem > (size_t)SMEM_BUDGET) fail(NRTO_ERR_INVALID, "horizon too long for the shared-memory budget of this precision");
+  // the row-group partials of Z' are summed in the (then idle) chunk buffers
+  const int nu = kind_nu(kl.kind), ng = (kl.kind == KIND_UNICYCLE) ? 4 : 1;
+  size_t bb = 0;
+  if (kl.kind == KIND_UNICYCLE) bb = FASmem<3, 2, Real>::buf_bytes(chunk, kl.max_rows);
+  else if (kl.kind == KIND_QUADCOPTER) bb = FASmem<12, 4, Real>::buf_bytes(chunk, kl.max_rows);
+  else bb = FASmem<14, 7, Real>::buf_bytes(chunk, kl.max_rows);
+  if ((size_t)ng * kl.tmax * nu * nx * sizeof(Real) > 2 * bb) fail(NRTO_ERR_INVALID, "internal: chunk buffers too small for the row-group reduction");
 }
 
 // per-instance arena/slot field copy (device → host) of cnt(I) doubles at off(I)

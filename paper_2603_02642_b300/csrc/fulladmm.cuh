@@ -41,9 +41,14 @@ struct FACfg {
   static constexpr int NT = sizeof(Real) == 4 ? 1024 : 512;
   static constexpr int NW = NT / 32;
   static constexpr int TMAXC = (NX == 3) ? 256 : (NX == 12 ? 160 : 128);
-  static constexpr int LMAX = (TMAXC + 1) * NX;                      // longest row
-  static constexpr int PAIRS = (LMAX + NT - 1) / NT;                  // (m, c) columns per thread
-  static constexpr int NWR = (NW < (LMAX + 31) / 32) ? NW : (LMAX + 31) / 32;   // warps touching a row
+  static constexpr int W = (NX == 3) ? 3 : 2;            // consecutive components of a block per thread
+  static constexpr int NCG = NX / W;                     // column groups per ζ-block
+  static constexpr int NG = (NX == 3) ? 4 : 1;           // row groups (CTA slices working on different rows)
+  static constexpr int TPG = NT / NG;                    // threads per row group
+  static constexpr int NCOL = (TMAXC + 1) * NCG;         // column groups of the longest row
+  static constexpr int PAIRS = (NCOL + TPG - 1) / TPG;   // column groups per thread
+  static constexpr int NWG = TPG / 32;                   // warps per row group
+  static constexpr int NWR = (NWG < (NCOL + 31) / 32) ? NWG : (NCOL + 31) / 32;   // warps of a group touching a row
 };
 
 // Supplementary Sec. II-C closed form: (t̂, η̂) ↦ (p̃, s·η̂)
@@ -126,7 +131,7 @@ __device__ void issue_chunk(const Dev<Real>& D, const LinSlot<Real>& S, const In
 //   Y = coefA Z' Φ + coefK K̃ U;  X = (Pfᵀ Y) ⊙ Dv;  PX = Pf X;  K = PX Uᵀ;  Gtᵀ = √τ PX Φᵀ.
 // (FullADMM: coefA = ρ√τ, coefK = 0; DR: coefA = σ√τ, coefK = r_χ.)  All threads of the block.
 template <int NX, int NU, typename Real>
-__device__ void gain_solve(double* ar, const Arena& L, int T, double sqrt_tau, double coefA, double coefK,
+__device__ __noinline__ void gain_solve(double* ar, const Arena& L, int T, double sqrt_tau, double coefA, double coefK,
                            double* Kout, double* gt_out) {
   const int n = T * NU * NX;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
@@ -192,7 +197,7 @@ __device__ void gain_solve(double* ar, const Arena& L, int T, double sqrt_tau, d
 // Each lane keeps the factor rows it needs for one step in registers and loads the next step's rows
 // before the current step's dependent arithmetic, so the 2T dependent steps do not each wait for L2.
 template <int NX, int NU, typename Real>
-__device__ void riccati_sweep(double* ar, const Arena& L, const double* sa, const SlotL& SL, int T, double* pv) {
+__device__ __noinline__ void riccati_sweep(double* ar, const Arena& L, const double* sa, const SlotL& SL, int T, double* pv) {
   const int lane = threadIdx.x & 31;
   // lane j < NX: column j of Acl_k and of L_k, q_k[j];   lane j < NU: row j of N_k and of M_k, r_k
   Real acl[NX], lk[NU], nrow[NU], mrow[NX], rr[NU];
@@ -312,15 +317,151 @@ __device__ void riccati_sweep(double* ar, const Arena& L, const double* sa, cons
   __syncwarp();
 }
 
-// Load the gain-table registers of this thread's columns from an arena Gtᵀ table ((T+1)×NU×NX).
-template <int NX, int NU, typename Real, int PAIRS>
+// Block-2 sweep from shared memory: all threads first copy the per-step factors of one pass into
+// `st` (the idle chunk buffers, `cap` Real values), then warp 0 runs the dependent recursion on
+// shared-memory operands.  Same arithmetic as riccati_sweep.  Returns false (nothing done) when the
+// factors do not fit; the caller then uses riccati_sweep.
+template <int NX, int NU, typename Real>
+__device__ __noinline__ bool riccati_sweep_staged(double* ar, const Arena& L, const double* sa, const SlotL& SL, int T,
+                                     Real* st, size_t cap, double* pv) {
+  constexpr int BW = NU * NU + 2 * NU * NX + NX * NX + NX + NU;   // N, M, L, Acl, q, r per step
+  constexpr int FW = NU * NX + NX * NX + NX * NU;                 // L, A, B per step
+  if ((size_t)T * (BW > FW ? BW : FW) > cap) return false;
+  const int tid = threadIdx.x, lane = tid & 31;
+  // ---- backward pass factors ----
+  for (int q = tid; q < T * BW; q += blockDim.x) {
+    const int k = q / BW, o = q - k * BW;
+    double v;
+    if (o < NU * NU) v = ar[L.RicN + (long long)k * NU * NU + o];
+    else if (o < NU * NU + NU * NX) v = ar[L.RicM + (long long)k * NU * NX + (o - NU * NU)];
+    else if (o < NU * NU + 2 * NU * NX) v = ar[L.RicL + (long long)k * NU * NX + (o - NU * NU - NU * NX)];
+    else if (o < NU * NU + 2 * NU * NX + NX * NX) v = ar[L.RicAcl + (long long)k * NX * NX + (o - NU * NU - 2 * NU * NX)];
+    else if (o < NU * NU + 2 * NU * NX + NX * NX + NX) v = ar[L.qv + (long long)k * NX + (o - NU * NU - 2 * NU * NX - NX * NX)];
+    else v = ar[L.rv + (long long)k * NU + (o - NU * NU - 2 * NU * NX - NX * NX - NX)];
+    st[q] = (Real)v;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    if (lane < NX) pv[lane] = ar[L.qv + (long long)T * NX + lane];
+    __syncwarp();
+    for (int k = T - 1; k >= 0; --k) {
+      const Real* f = st + (long long)k * BW;
+      const Real* N = f;
+      const Real* M = N + NU * NU;
+      const Real* Lk = M + NU * NX;
+      const Real* Acl = Lk + NU * NX;
+      const Real* q = Acl + NX * NX;
+      const Real* r = q + NX;
+      Real p_in[NX];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) p_in[c] = (Real)pv[c];
+      if (lane < NU) {
+        Real lv = 0;
+#pragma unroll
+        for (int v = 0; v < NU; ++v) lv += N[lane * NU + v] * r[v];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) lv += M[lane * NX + c] * p_in[c];
+        ar[L.du + (long long)k * NU + lane] = -(double)lv;
+      }
+      Real pn = 0;
+      if (lane < NX && k >= 1) {
+        pn = q[lane];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) pn += Acl[c * NX + lane] * p_in[c];
+#pragma unroll
+        for (int v = 0; v < NU; ++v) pn += Lk[v * NX + lane] * r[v];
+      }
+      __syncwarp();
+      if (lane < NX && k >= 1) pv[lane] = (double)pn;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // ---- forward pass factors ----
+  for (int q = tid; q < T * FW; q += blockDim.x) {
+    const int k = q / FW, o = q - k * FW;
+    double v;
+    if (o < NU * NX) v = ar[L.RicL + (long long)k * NU * NX + o];
+    else if (o < NU * NX + NX * NX) v = sa[SL.A + (long long)k * NX * NX + (o - NU * NX)];
+    else v = sa[SL.B + (long long)k * NX * NU + (o - NU * NX - NX * NX)];
+    st[q] = (Real)v;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double* dx = ar + L.dx;
+    double* du = ar + L.du;
+    Real xk[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) xk[c] = 0;
+    if (lane < NX) dx[lane] = 0.0;
+    for (int k = 0; k < T; ++k) {
+      const Real* Lk = st + (long long)k * FW;
+      const Real* A = Lk + NU * NX;
+      const Real* B = A + NX * NX;
+      Real u = 0;
+      if (lane < NU) {
+        u = (Real)du[(long long)k * NU + lane];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) u += Lk[lane * NX + c] * xk[c];
+        du[(long long)k * NU + lane] = (double)u;
+      }
+      Real uk[NU];
+#pragma unroll
+      for (int v = 0; v < NU; ++v) uk[v] = __shfl_sync(0xffffffffu, u, v);
+      Real xn = 0;
+      if (lane < NX) {
+#pragma unroll
+        for (int c = 0; c < NX; ++c) xn += A[lane * NX + c] * xk[c];
+#pragma unroll
+        for (int v = 0; v < NU; ++v) xn += B[lane * NU + v] * uk[v];
+        dx[(long long)(k + 1) * NX + lane] = (double)xn;
+      }
+#pragma unroll
+      for (int c = 0; c < NX; ++c) xk[c] = __shfl_sync(0xffffffffu, xn, c);
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Load the gain-table registers of this thread's column groups from an arena Gtᵀ table ((T+1)×NU×NX).
+template <int NX, int NU, typename Real, int PAIRS, int W>
 __device__ __forceinline__ void load_gt_regs(const double* gt, int T, const int (&mk)[PAIRS], const int (&ck)[PAIRS],
-                                             Real (&g)[PAIRS][NU]) {
+                                             Real (&g)[PAIRS][NU][W]) {
 #pragma unroll
   for (int k = 0; k < PAIRS; ++k)
 #pragma unroll
     for (int u = 0; u < NU; ++u)
-      g[k][u] = (mk[k] < T) ? (Real)gt[(long long)mk[k] * NU * NX + u * NX + ck[k]] : (Real)0;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+        g[k][u][w] = (mk[k] < T) ? (Real)gt[(long long)mk[k] * NU * NX + u * NX + ck[k] + w] : (Real)0;
+}
+
+// Vector loads/stores of W consecutive shared-memory values (8- or 16-byte aligned by the layout:
+// row offsets within a chunk are multiples of NX, block offsets of NU, and W divides NX).
+template <int N, typename Real>
+__device__ __forceinline__ void ld_vec(const Real* p, Real (&v)[N]) {
+  if constexpr (N == 2 && sizeof(Real) == 4) {
+    const float2 t = *reinterpret_cast<const float2*>(p); v[0] = t.x; v[1] = t.y;
+  } else if constexpr (N == 4 && sizeof(Real) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (N == 2 && sizeof(Real) == 8) {
+    const double2 t = *reinterpret_cast<const double2*>(p); v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = p[i];
+  }
+}
+template <int N, typename Real>
+__device__ __forceinline__ void st_vec(Real* p, const Real (&v)[N]) {
+  if constexpr (N == 2 && sizeof(Real) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (N == 2 && sizeof(Real) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = v[i];
+  }
 }
 
 // Phase timer: thread 0 accumulates the SM cycles between consecutive marks (taken right after block
@@ -347,7 +488,7 @@ template <int NX, int NU, typename Real>
 __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int inst, FASmem<NX, NU, Real>& sm,
                                   uint64_t* bars, uint32_t* phase, int* s_flag, double* ric_scr) {
   using C = FACfg<NX, NU, Real>;
-  constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR = C::NWR;
+  constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR = C::NWR, W = C::W, NCG = C::NCG, NG = C::NG, TPG = C::TPG;
   const Inst I = D.inst[inst];
   const Arena L = arena_layout(NX, NU, I.T, I.n_obs, I.n_link);
   const SlotL SL = slot_layout(NX, NU, I.T);
@@ -368,10 +509,11 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   PhaseTimer tm;
   tm.start(D.phase_cycles != nullptr);
 
-  // this thread's (m, c) columns
+  // this thread's row group and its column groups (block m, components c .. c+W-1)
+  const int grp = tid / TPG, lt = tid - grp * TPG, gwarp = lt >> 5;
   int mk[PAIRS], ck[PAIRS];
 #pragma unroll
-  for (int k = 0; k < PAIRS; ++k) { const int P = tid + k * NT; mk[k] = P / NX; ck[k] = P - mk[k] * NX; }
+  for (int k = 0; k < PAIRS; ++k) { const int P = lt + k * TPG; mk[k] = P / NCG; ck[k] = (P - mk[k] * NCG) * W; }
 
   // ---- initialization (Algorithm 1): λ_p, λ_ν, k, p <- 0 (or a warm start of k, p̃, λ_p) ----
   for (long long e = tid; e < I.n_ent; e += NT) lam[I.ent0 + e] = (Real)0;
@@ -409,13 +551,15 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     const bool block1 = (b <= Lmax);
     const double* gtc_arena = ar + (gsel ? L.Gt1 : L.Gt0);
     const double* gto_arena = ar + (gsel ? L.Gt0 : L.Gt1);
-    Real gc[PAIRS][NU], go[PAIRS][NU], z[PAIRS][NU];
-    load_gt_regs<NX, NU, Real, PAIRS>(gtc_arena, T, mk, ck, gc);
-    load_gt_regs<NX, NU, Real, PAIRS>(gto_arena, T, mk, ck, go);
+    Real gc[PAIRS][NU][W], go[PAIRS][NU][W], z[PAIRS][NU][W];
+    load_gt_regs<NX, NU, Real, PAIRS, W>(gtc_arena, T, mk, ck, gc);
+    load_gt_regs<NX, NU, Real, PAIRS, W>(gto_arena, T, mk, ck, go);
 #pragma unroll
     for (int k = 0; k < PAIRS; ++k)
 #pragma unroll
-      for (int u = 0; u < NU; ++u) z[k][u] = (Real)0;
+      for (int u = 0; u < NU; ++u)
+#pragma unroll
+        for (int w = 0; w < W; ++w) z[k][u][w] = (Real)0;
     Real arp = 0, ard = 0;
     const double rho_prev = rho;   // penalty of iteration b-1
     Real lscale = (Real)1;         // rescale of the scaled dual λ_ν^{b-1} when ρ changes for iteration b
@@ -457,8 +601,9 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
       __syncthreads();
       phase[bi] ^= 1u;
       if (*s_flag == 0) { status = ST_TIMEOUT; goto done; }
-      // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms
-      for (int q = 0; q < nr; ++q) {
+      // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms (row group `grp`
+      // takes rows grp, grp+NG, ...)
+      for (int q = grp; q < nr; q += NG) {
         const RowMeta rm = bf.meta[q];
         const Real so = (Real)bf.sold[soff + q];
         Real pn = 0;
@@ -468,34 +613,37 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
           if (mk[k] <= rm.t) {
             act = true;
             const int e = rm.off + mk[k] * NX + ck[k];
-            const Real* bq = bf.bb + rm.boff + mk[k] * NU;
-            Real bv[NU];
+            Real bv[NU], yb[W], l[W];
+            ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
+            ld_vec<W, Real>(bf.bhat + e, yb);
+            ld_vec<W, Real>(bf.lam + e, l);
 #pragma unroll
-            for (int u = 0; u < NU; ++u) bv[u] = bq[u];
-            const Real yb = bf.bhat[e];
-            Real l = bf.lam[e];
-            Real y = yb;
+            for (int w = 0; w < W; ++w) {
+              Real y = yb[w];
 #pragma unroll
-            for (int u = 0; u < NU; ++u) y += gc[k][u] * bv[u];
-            if (!first) {
-              Real yo = yb;
+              for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
+              if (!first) {
+                Real yo = yb[w];
 #pragma unroll
-              for (int u = 0; u < NU; ++u) yo += go[k][u] * bv[u];
-              const Real nu = so * (yo + l);
-              const Real ln = l + y - nu;
-              arp += (y - nu) * (y - nu);
-              ard += (y - yo) * (y - yo);
-              l = ln * lscale;
-              bf.lam[e] = l;
-              lam[cki.e0 + e] = l;
+                for (int u = 0; u < NU; ++u) yo += go[k][u][w] * bv[u];
+                const Real nu = so * (yo + l[w]);
+                const Real ln = l[w] + y - nu;
+                arp += (y - nu) * (y - nu);
+                ard += (y - yo) * (y - yo);
+                l[w] = ln * lscale;
+              }
+              const Real et = y + l[w];
+              pn += et * et;
             }
-            const Real et = y + l;
-            pn += et * et;
+            if (!first) {
+              st_vec<W, Real>(bf.lam + e, l);
+              st_vec<W, Real>(lam + cki.e0 + e, l);
+            }
           }
         }
-        if (block1 && warp < NWR) {
+        if (block1 && gwarp < NWR) {
           if (__any_sync(0xffffffffu, act)) pn = warp_sum(pn);
-          if (lane == 0) sm.rowpart[q * NWR + warp] = pn;
+          if (lane == 0) sm.rowpart[q * NWR + gwarp] = pn;
         }
       }
       __syncthreads();
@@ -513,25 +661,26 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
         }
         __syncthreads();
         // sub-pass 2: Z'_m[:, c] += b_{j,m} w_{j,m}[c], w = ν - b̂ - λ = s(y + λ) - b̂ - λ
-        for (int q = 0; q < nr; ++q) {
+        for (int q = grp; q < nr; q += NG) {
           const RowMeta rm = bf.meta[q];
           const Real sn = sm.snew[q];
 #pragma unroll
           for (int k = 0; k < PAIRS; ++k) {
             if (mk[k] < rm.t) {
               const int e = rm.off + mk[k] * NX + ck[k];
-              const Real* bq = bf.bb + rm.boff + mk[k] * NU;
-              Real bv[NU];
+              Real bv[NU], yb[W], l[W];
+              ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
+              ld_vec<W, Real>(bf.bhat + e, yb);
+              ld_vec<W, Real>(bf.lam + e, l);
 #pragma unroll
-              for (int u = 0; u < NU; ++u) bv[u] = bq[u];
-              const Real yb = bf.bhat[e];
-              const Real l = bf.lam[e];
-              Real y = yb;
+              for (int w = 0; w < W; ++w) {
+                Real y = yb[w];
 #pragma unroll
-              for (int u = 0; u < NU; ++u) y += gc[k][u] * bv[u];
-              const Real wv = sn * (y + l) - yb - l;
+                for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
+                const Real wv = sn * (y + l[w]) - yb[w] - l[w];
 #pragma unroll
-              for (int u = 0; u < NU; ++u) z[k][u] += bv[u] * wv;
+                for (int u = 0; u < NU; ++u) z[k][u][w] += bv[u] * wv;
+              }
             }
           }
         }
@@ -543,11 +692,34 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
       }
     }
     if (block1) {
+      // Z' = Σ over row groups (fixed order) of the register accumulators; the idle chunk buffers
+      // hold the per-group partials when there is more than one group.
+      if constexpr (NG == 1) {
 #pragma unroll
-      for (int k = 0; k < PAIRS; ++k)
-        if (mk[k] < T)
+        for (int k = 0; k < PAIRS; ++k)
+          if (mk[k] < T)
 #pragma unroll
-          for (int u = 0; u < NU; ++u) ar[L.Zp + (long long)mk[k] * NU * NX + u * NX + ck[k]] = (double)z[k][u];
+            for (int u = 0; u < NU; ++u)
+#pragma unroll
+              for (int w = 0; w < W; ++w) ar[L.Zp + (long long)mk[k] * NU * NX + u * NX + ck[k] + w] = (double)z[k][u][w];
+      } else {
+        Real* part = sm.buf[0].lam;   // NG × T × NU × NX values (checked against the buffer size on the host)
+        const int nz = T * NU * NX;
+#pragma unroll
+        for (int k = 0; k < PAIRS; ++k)
+          if (mk[k] < T)
+#pragma unroll
+            for (int u = 0; u < NU; ++u)
+#pragma unroll
+              for (int w = 0; w < W; ++w) part[grp * nz + mk[k] * NU * NX + u * NX + ck[k] + w] = z[k][u][w];
+        __syncthreads();
+        for (int q = tid; q < nz; q += NT) {
+          Real acc = 0;
+#pragma unroll
+          for (int g2 = 0; g2 < NG; ++g2) acc += part[g2 * nz + q];
+          ar[L.Zp + q] = (double)acc;
+        }
+      }
     }
     __syncthreads();
     tm.mark(PH_ROWS);
@@ -662,9 +834,15 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     gain_solve<NX, NU, Real>(ar, L, T, I.sqrt_tau, rho * I.sqrt_tau, 0.0, ar + L.K1, ar + (gsel ? L.Gt0 : L.Gt1));
     gsel ^= 1;
     tm.mark(PH_GAIN);
-    // ---------------- (b) Block 2: Riccati sweep (warp 0) ----------------
-    if (warp == 0) riccati_sweep<NX, NU, Real>(ar, L, sa, SL, T, sm.vec);
-    __syncthreads();
+    // ---------------- (b) Block 2: Riccati sweep (factors staged in the idle chunk buffers) ----------------
+    {
+      // The two chunk buffers are contiguous in the carve; their total size bounds the staging area.
+      const size_t cap = 2 * FASmem<NX, NU, Real>::buf_bytes(sp.chunk, sp.max_rows) / sizeof(Real);
+      if (!riccati_sweep_staged<NX, NU, Real>(ar, L, sa, SL, T, sm.buf[0].lam, cap, sm.vec)) {
+        if (warp == 0) riccati_sweep<NX, NU, Real>(ar, L, sa, SL, T, sm.vec);
+        __syncthreads();
+      }
+    }
     tm.mark(PH_RICCATI);
     // ---------------- (d) p, scalar duals, scalar residual parts of iteration b ----------------
     double a_rp = 0, a_rd = 0, a_rpp = 0, a_rdp = 0;

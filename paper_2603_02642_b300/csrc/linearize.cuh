@@ -246,7 +246,7 @@ __device__ inline void wmm(double* C, const double* A, bool tA, int lda, const d
 // Run by one warp; `scr` is shared scratch of RIC_SCRATCH doubles.
 constexpr int RIC_SCRATCH = 1176;
 template <typename Real>
-__device__ void riccati_factor_warp(const Dev<Real>& D, int i, double rho, double* scr) {
+__device__ __noinline__ void riccati_factor_warp(const Dev<Real>& D, int i, double rho, double* scr) {
   const Inst I = D.inst[i];
   const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
   const SlotL SL = slot_layout(I.nx, I.nu, I.T);
@@ -350,7 +350,7 @@ __global__ void k_riccati_factor(Dev<Real> D, double rho) {
 
 // Dv_m[u][c] = 1/(1 + coef τ γ_u λ_c) for a new penalty (the eigen factors do not depend on it).
 template <typename Real>
-__device__ void gain_divisors(const Dev<Real>& D, int i, double coef) {
+__device__ __noinline__ void gain_divisors(const Dev<Real>& D, int i, double coef) {
   const Inst I = D.inst[i];
   const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
   double* ar = D.arena + I.arena0;
