@@ -196,8 +196,9 @@ nrto_status nrto_profile(nrto_problem_t p, int enable, double* solver_ms, long l
  * phase boundaries), recorded while nrto_profile recording is enabled; returned and cleared.
  * Phases: 0 initialization, 1 row pass (cone projections, λ_ν update, Z' accumulation), 2 control
  * rows and residual reduction, 3 orthant/ball slacks, 4 Riccati linear terms, 5 gain solve,
- * 6 Riccati sweep, 7 scalar duals.  n must be >= NRTO_NPHASE. */
-#define NRTO_NPHASE 8
+ * 6 Riccati sweep, 7 scalar duals, 8 time spent waiting for row-chunk copies (included in 1).
+ * n must be >= NRTO_NPHASE. */
+#define NRTO_NPHASE 9
 nrto_status nrto_phase_cycles(nrto_problem_t p, long long* cycles, int n);
 
 /* Number of kernel launches the library issued since create (all of its own kernels). */

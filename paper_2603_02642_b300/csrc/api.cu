@@ -43,8 +43,12 @@ int kind_nu(int k) { return k == KIND_UNICYCLE ? 2 : (k == KIND_QUADCOPTER ? 4 :
 int kind_tmax(int k) { return k == KIND_UNICYCLE ? 256 : (k == KIND_QUADCOPTER ? 160 : 128); }
 
 // opt-in shared memory per block on sm_103a is 227 KB; keep 1 KB for static shared variables
-// (static shared memory of the solver: mbarriers, flags and the Riccati scratch, about 9.5 KB)
-constexpr int SMEM_BUDGET = 227 * 1024 - 12 * 1024;
+// Dynamic shared memory per solver CTA: the SM's 228 KB are shared by the resident CTAs, each of which
+// also holds ~9.5 KB of static shared memory (mbarriers, flags, Riccati scratch) and 1 KB reserved.
+template <typename Real>
+constexpr int smem_budget() {
+  return (sizeof(Real) == 4 && NRTO_FA_MINB_F32 > 1) ? (228 * 1024) / NRTO_FA_MINB_F32 - 12 * 1024 : 227 * 1024 - 12 * 1024;
+}
 
 template <typename Real>
 size_t smem_for(int kind, int chunk, int max_rows) {
@@ -434,12 +438,12 @@ void choose_chunk(KindLaunch& kl) {
   const int nx = kind_nx(kl.kind);
   const int minc = ((kl.tmax + 1) * nx + 3) & ~3;
   int chunk = 6144;
-  while (chunk > minc && smem_for<Real>(kl.kind, chunk, chunk / (2 * nx) + 2) > (size_t)SMEM_BUDGET) chunk -= 256;
+  while (chunk > minc && smem_for<Real>(kl.kind, chunk, chunk / (2 * nx) + 2) > (size_t)smem_budget<Real>()) chunk -= 256;
   if (chunk < minc) chunk = minc;
   kl.chunk = chunk;
   kl.max_rows = chunk / (2 * nx) + 2;
   kl.smem = smem_for<Real>(kl.kind, chunk, kl.max_rows);
-  if (kl.smem > (size_t)SMEM_BUDGET) fail(NRTO_ERR_INVALID, "horizon too long for the shared-memory budget of this precision");
+  if (kl.smem > (size_t)smem_budget<Real>()) fail(NRTO_ERR_INVALID, "horizon too long for the shared-memory budget of this precision");
   // the row-group partials of Z' are summed in the (then idle) chunk buffers
   const int nu = kind_nu(kl.kind), ng = (kl.kind == KIND_UNICYCLE) ? 4 : 1;
   size_t bb = 0;

@@ -36,14 +36,23 @@ struct SolveParams {
   double adapt_mu, adapt_tau, rho_min, rho_max, stall_ratio;
 };
 
+// Solver CTA shape for the compute precision float (threads, resident CTAs per SM); FP64 uses 512 × 1.
+#ifndef NRTO_FA_NT_F32
+#define NRTO_FA_NT_F32 1024
+#endif
+#ifndef NRTO_FA_MINB_F32
+#define NRTO_FA_MINB_F32 1
+#endif
+
 template <int NX, int NU, typename Real>
 struct FACfg {
-  static constexpr int NT = sizeof(Real) == 4 ? 1024 : 512;
+  static constexpr int NT = sizeof(Real) == 4 ? NRTO_FA_NT_F32 : 512;
+  static constexpr int MINB = sizeof(Real) == 4 ? NRTO_FA_MINB_F32 : 1;   // resident CTAs per SM
   static constexpr int NW = NT / 32;
   static constexpr int TMAXC = (NX == 3) ? 256 : (NX == 12 ? 160 : 128);
   static constexpr int W = (NX == 3) ? 3 : 2;            // consecutive components of a block per thread
   static constexpr int NCG = NX / W;                     // column groups per ζ-block
-  static constexpr int NG = (NX == 3) ? 4 : 1;           // row groups (CTA slices working on different rows)
+  static constexpr int NG = (NX == 3) ? (NT >= 1024 ? 4 : 2) : 1;   // row groups (CTA slices on different rows)
   static constexpr int TPG = NT / NG;                    // threads per row group
   static constexpr int NCOL = (TMAXC + 1) * NCG;         // column groups of the longest row
   static constexpr int PAIRS = (NCOL + TPG - 1) / TPG;   // column groups per thread
@@ -597,7 +606,11 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
       const ChunkInfo cki = chunks[ch];
       const int nr = cki.r1 - cki.r0;
       const int soff = (int)((I.row0 + cki.r0) & 1LL);
-      if (tid == 0) *s_flag = mbar_wait_bounded(&bars[bi], phase[bi]) ? 1 : 0;
+      if (tid == 0) {
+        const long long tw = clock64();
+        *s_flag = mbar_wait_bounded(&bars[bi], phase[bi]) ? 1 : 0;
+        if (tm.on) tm.acc[PH_WAIT] += (unsigned long long)(clock64() - tw);   // part of PH_ROWS, also counted here
+      }
       __syncthreads();
       phase[bi] ^= 1u;
       if (*s_flag == 0) { status = ST_TIMEOUT; goto done; }
@@ -898,7 +911,7 @@ done:
 }
 
 template <int NX, int NU, typename Real>
-__global__ void __launch_bounds__(FACfg<NX, NU, Real>::NT, 1) k_fulladmm(Dev<Real> D, SolveParams sp) {
+__global__ void __launch_bounds__(FACfg<NX, NU, Real>::NT, FACfg<NX, NU, Real>::MINB) k_fulladmm(Dev<Real> D, SolveParams sp) {
   extern __shared__ __align__(16) char smem_raw[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_next, s_flag;

@@ -149,7 +149,7 @@ struct Dev {
 };
 
 // Phases of one inner iteration timed by the persistent solvers (thread 0 of each CTA, SM cycles).
-enum : int { PH_INIT = 0, PH_ROWS, PH_CTRL, PH_SCAL1, PH_QR, PH_GAIN, PH_RICCATI, PH_DUALS, NPHASE };
+enum : int { PH_INIT = 0, PH_ROWS, PH_CTRL, PH_SCAL1, PH_QR, PH_GAIN, PH_RICCATI, PH_DUALS, PH_WAIT, NPHASE };
 
 // ------------------------------------------------------------------------------------------
 // warp helpers

@@ -10,7 +10,7 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libnrto.so")
+LIB_PATH = os.environ.get("NRTO_LIB", os.path.join(HERE, "libnrto.so"))
 
 PREC_FP64, PREC_MIXED = 0, 1
 SOLVER_DR, SOLVER_FULLADMM = 0, 1
@@ -286,12 +286,13 @@ class Problem:
         _check(load().nrto_profile(self._h, int(enable), C.byref(ms), C.byref(n)))
         return ms.value, n.value
 
-    PHASES = ["init", "rows", "control+reduce", "slacks", "riccati_terms", "gain_solve", "riccati_sweep", "duals"]
+    PHASES = ["init", "rows", "control+reduce", "slacks", "riccati_terms", "gain_solve", "riccati_sweep", "duals",
+              "rows_copy_wait"]
 
     def phase_cycles(self):
         """Per-phase SM cycles (summed over CTAs) recorded while profiling was enabled; clears them."""
-        buf = (C.c_longlong * 8)()
-        _check(load().nrto_phase_cycles(self._h, buf, 8))
+        buf = (C.c_longlong * 9)()
+        _check(load().nrto_phase_cycles(self._h, buf, 9))
         return dict(zip(self.PHASES, [int(x) for x in buf]))
 
     def kernel_launches(self):
