@@ -204,6 +204,26 @@ nrto_status nrto_phase_cycles(nrto_problem_t p, long long* cycles, int n);
 /* Number of kernel launches the library issued since create (all of its own kernels). */
 long long nrto_kernel_launches(nrto_problem_t p);
 
+/* nrto_solve without device allocation.  The paper has no counterpart: this is a library service.
+ * Some callers cannot call cudaMalloc: real-time control loops that must not pay an allocation's
+ * latency and implicit synchronization, and processes whose device memory is held by another
+ * allocator (a framework's caching pool), where an allocation may fail mid-run.  This call does what
+ * nrto_problem_create + nrto_solve + nrto_problem_destroy do, with the same kernels and results, but
+ * every device buffer of the batch is cut from one static 32 MiB device area that the library holds
+ * on every GPU that loads it, until the process exits.  It calls no cudaMalloc or cudaFree.
+ *   descs, n, precision: as nrto_problem_create; opts, n_outer, u_bar, K, merit: as nrto_solve
+ *     (host arrays, may be NULL); stream: CUDA stream (NULL: default stream).
+ *   Errors: NRTO_ERR_INVALID when the batch does not fit in the area (the message says so; use
+ *     nrto_problem_create then), otherwise as nrto_problem_create and nrto_solve.
+ * The first call on a device looks up the device address of the area (cudaGetSymbolAddress); make
+ * that first call before any stream capture on that device.  All calls share the area, which keeps
+ * the previous call's contents: each call clears every buffer it uses before use.  Two calls that
+ * ran on the GPU at the same time would overwrite each other's data, so calls in one process are
+ * serialized by a lock and each returns only after its GPU work has finished. */
+nrto_status nrto_solve_noalloc(const nrto_problem_desc* descs, int n, int precision,
+                               const nrto_solver_opts* opts, int n_outer, void* stream,
+                               double* u_bar, double* K, double* merit);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* nrto_last_error(void);
 

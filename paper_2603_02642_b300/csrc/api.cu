@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <stdexcept>
 #include <string>
@@ -153,6 +154,10 @@ struct nrto_problem {
   std::vector<long long> stage_off, stage_len, uoff;
   long long stage_total = 0, u_total = 0;
   std::vector<void*> allocs;
+  // When carve_base is set (nrto_solve_noalloc), device buffers are cut from that caller-owned area
+  // instead of being allocated.
+  char* carve_base = nullptr;
+  size_t carve_cap = 0, carve_used = 0;
   // device
   Inst* d_inst = nullptr;
   double* d_arena = nullptr;
@@ -192,8 +197,17 @@ struct nrto_problem {
   T* dalloc(size_t count) {
     void* ptr = nullptr;
     size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    CK(cudaMalloc(&ptr, bytes));
-    allocs.push_back(ptr);
+    if (carve_base) {
+      const size_t at = (carve_used + 255) & ~size_t(255);
+      if (at + bytes > carve_cap)
+        fail(NRTO_ERR_INVALID, "batch needs more than the " + std::to_string(carve_cap >> 20) +
+                                   " MiB static device area of nrto_solve_noalloc; use nrto_problem_create");
+      ptr = carve_base + at;
+      carve_used = at + bytes;
+    } else {
+      CK(cudaMalloc(&ptr, bytes));
+      allocs.push_back(ptr);
+    }
     CK(cudaMemsetAsync(ptr, 0, bytes, stream));
     return static_cast<T*>(ptr);
   }
@@ -679,8 +693,14 @@ extern "C" {
 
 const char* nrto_last_error(void) { return g_last_error.c_str(); }
 
-nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int precision, void* stream,
-                                nrto_problem_t* out) {
+}  // extern "C"
+
+namespace {
+
+// Body of nrto_problem_create.  carve_base == nullptr: every device buffer comes from cudaMalloc;
+// otherwise buffers are cut from [carve_base, carve_base + carve_cap).
+nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision, void* stream, char* carve_base,
+                           size_t carve_cap, nrto_problem_t* out) {
   nrto_problem* P = nullptr;
   try {
     g_last_error.clear();
@@ -688,6 +708,8 @@ nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int preci
     if (precision != NRTO_PREC_FP64 && precision != NRTO_PREC_MIXED) fail(NRTO_ERR_INVALID, "unknown precision");
     for (int i = 0; i < n; ++i) validate(descs[i], i);
     P = new nrto_problem();
+    P->carve_base = carve_base;
+    P->carve_cap = carve_cap;
     P->n = n;
     P->prec = precision;
     P->stream = static_cast<cudaStream_t>(stream);
@@ -873,6 +895,15 @@ nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int preci
     delete P;
     return handle(e);
   }
+}
+
+}  // namespace
+
+extern "C" {
+
+nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int precision, void* stream,
+                                nrto_problem_t* out) {
+  return create_problem(descs, n, precision, stream, nullptr, 0, out);
 }
 
 nrto_status nrto_problem_destroy(nrto_problem_t p) {
@@ -1097,6 +1128,62 @@ nrto_status nrto_phase_cycles(nrto_problem_t p, long long* cycles, int n) {
 long long nrto_kernel_launches(nrto_problem_t p) { return p ? p->launches : -1; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// nrto_solve_noalloc: the whole-batch solve of nrto_solve with every device buffer of the batch
+// (row tables, linearization slots, solver arena with its gain-solve scratch, work queue) cut from
+// one static device area instead of cudaMalloc.  For callers that must not allocate device memory
+// after start-up: real-time control loops that cannot afford an allocation's latency or its
+// implicit synchronization, and processes whose device memory is already reserved by another
+// allocator (a framework's caching pool), where a cudaMalloc could fail mid-run.
+namespace {
+
+constexpr size_t NOALLOC_AREA_BYTES = size_t(32) << 20;   // 32 MiB on every device that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_area[NOALLOC_AREA_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;                                  // serializes the calls of this process
+char* g_noalloc_dev_ptr[NOALLOC_MAX_DEVICES] = {};          // device address of the area, per device
+
+}  // namespace
+
+extern "C" nrto_status nrto_solve_noalloc(const nrto_problem_desc* descs, int n, int precision,
+                                          const nrto_solver_opts* opts, int n_outer, void* stream,
+                                          double* u_bar, double* K, double* merit) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  nrto_problem_t p = nullptr;
+  try {
+    g_last_error.clear();
+    check_opts(opts);
+    if (n_outer < 0) fail(NRTO_ERR_INVALID, "n_outer < 0");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) fail(NRTO_ERR_INVALID, "device index out of range");
+    if (!g_noalloc_dev_ptr[dev]) {
+      // First call on this device: look up the device address of the static area (the host-side
+      // symbol is only a stand-in and must never reach a kernel).
+      void* ptr = nullptr;
+      CK(cudaGetSymbolAddress(&ptr, g_noalloc_area));
+      g_noalloc_dev_ptr[dev] = static_cast<char*>(ptr);
+    }
+    const nrto_status cs = create_problem(descs, n, precision, stream, g_noalloc_dev_ptr[dev],
+                                          NOALLOC_AREA_BYTES, &p);
+    if (cs != NRTO_OK) {
+      // create may have queued clears of the area before it gave up; let them finish before the
+      // next call reuses the area.
+      cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+      return cs;
+    }
+    const nrto_status st = nrto_solve(p, opts, n_outer, u_bar, K, merit);
+    const std::string msg = g_last_error;
+    nrto_problem_destroy(p);   // synchronizes the stream: the area is free again when this returns
+    g_last_error = msg;
+    return st;
+  } catch (const std::exception& e) {
+    if (p) nrto_problem_destroy(p);
+    return handle(e);
+  }
+}
 
 template <typename Real>
 void launch_dr(nrto_problem* P, const nrto_solver_opts& o, SolveParams sp) {

@@ -82,12 +82,14 @@ def load():
     lib.nrto_profile.argtypes = [P, C.c_int, _dp, C.POINTER(C.c_longlong)]
     lib.nrto_phase_cycles.argtypes = [P, C.POINTER(C.c_longlong), C.c_int]
     lib.nrto_phase_cycles.restype = C.c_int
+    lib.nrto_solve_noalloc.argtypes = [C.POINTER(ProblemDesc), C.c_int, C.c_int, C.POINTER(SolverOpts), C.c_int,
+                                       C.c_void_p, _dp, _dp, _dp]
     lib.nrto_kernel_launches.argtypes = [P]
     lib.nrto_kernel_launches.restype = C.c_longlong
     lib.nrto_last_error.restype = C.c_char_p
     for name in ["nrto_problem_create", "nrto_problem_destroy", "nrto_problem_info", "nrto_problem_update",
                  "nrto_linearize", "nrto_set_trust_radius", "nrto_solve_socp", "nrto_outer_step", "nrto_solve",
-                 "nrto_set_warm_start", "nrto_export", "nrto_import", "nrto_profile"]:
+                 "nrto_set_warm_start", "nrto_export", "nrto_import", "nrto_profile", "nrto_solve_noalloc"]:
         getattr(lib, name).restype = C.c_int
     _LIB = lib
     return lib
@@ -297,3 +299,25 @@ class Problem:
 
     def kernel_launches(self):
         return int(load().nrto_kernel_launches(self._h))
+
+
+def solve_noalloc(instances, opts: Options, n_outer=10, precision=PREC_FP64, stream=None):
+    """Problem(instances).solve(opts, n_outer) without any device allocation: the batch lives in the
+    library's static device area (for callers that cannot allocate device memory).  Returns the same
+    dict as Problem.solve."""
+    insts = list(instances)
+    keep = []
+    descs = (ProblemDesc * len(insts))(*[_desc(x, keep) for x in insts])
+    u = np.zeros(sum(x.T * x.nu for x in insts))
+    K = np.zeros(sum(x.T * x.nu * x.nx for x in insts))
+    m = np.zeros(len(insts))
+    o = opts.c()
+    _check(load().nrto_solve_noalloc(descs, len(insts), precision, C.byref(o), n_outer, C.c_void_p(stream),
+                                     _ptr(u), _ptr(K), _ptr(m)))
+    us, Ks, a, b = [], [], 0, 0
+    for x in insts:
+        us.append(u[a:a + x.T * x.nu].reshape(x.T, x.nu))
+        Ks.append(K[b:b + x.T * x.nu * x.nx].reshape(x.T, x.nu, x.nx))
+        a += x.T * x.nu
+        b += x.T * x.nu * x.nx
+    return dict(u_bar=us, K=Ks, merit=m)
