@@ -180,8 +180,9 @@ enum {
   NRTO_F_KACC = 14,  /* T*nu*nx    gains of the accepted nominal (outer loop)                 */
   NRTO_F_DX = 15,    /* (T+1)*nx   δx of the last inner solve                                */
   NRTO_F_SCAL = 16,  /* 8: r_p, r_d, r_p(paper), r_d(paper), merit, candidate merit, cost, trust r */
-  NRTO_F_STATS = 17  /* 5, read-only: inner iterations since the last nrto_solve reset, iterations of
-                        the last inner solve, its status, accepted outer steps, its final ρ         */
+  NRTO_F_STATS = 17  /* 6, read-only: inner iterations since the last nrto_solve reset, iterations of
+                        the last inner solve, its status, accepted outer steps, its final ρ, and
+                        (NRTO-DR) the DR iterations summed over its ADMM iterations               */
 };
 nrto_status nrto_export(nrto_problem_t p, int field, int instance, double* dst, long long count);
 nrto_status nrto_import(nrto_problem_t p, int field, int instance, const double* src, long long count);

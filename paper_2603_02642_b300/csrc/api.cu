@@ -571,7 +571,7 @@ long long field_count(const Inst& I, int f) {
     case NRTO_F_K: case NRTO_F_KACC: return (long long)I.T * I.nu * I.nx;
     case NRTO_F_GM: return (long long)I.T * I.nu * I.nu;
     case NRTO_F_SCAL: return 8;
-    case NRTO_F_STATS: return 5;
+    case NRTO_F_STATS: return 6;
   }
   return -1;
 }
@@ -614,7 +614,7 @@ nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long 
         double scv[NSC];
         CK(cudaMemcpy(scv, p->d_sc + (long long)i * NSC, sizeof(scv), cudaMemcpyDeviceToHost));
         buf[0] = is[IS_CUMITERS]; buf[1] = is[IS_ITERS]; buf[2] = is[IS_STATUS]; buf[3] = is[IS_NACC];
-        buf[4] = scv[SC_RHO];
+        buf[4] = scv[SC_RHO]; buf[5] = is[IS_DRITERS];
         return NRTO_OK;
       }
       case NRTO_F_SCAL: {
@@ -1185,8 +1185,45 @@ extern "C" nrto_status nrto_solve_noalloc(const nrto_problem_desc* descs, int n,
   }
 }
 
+template <int NX, int NU, typename Real>
+void launch_dr_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
+  auto kern = k_dr<NX, NU, Real>;
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kl.smem));
+  int dev = 0, nsm = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FACfg<NX, NU, Real>::NT, kl.smem));
+  if (per_sm < 1) fail(NRTO_ERR_CUDA, "DR kernel does not fit on an SM");
+  const int grid = std::min(kl.count, nsm * per_sm);
+  sp.chunk = kl.chunk; sp.max_rows = kl.max_rows; sp.tmax = kl.tmax; sp.n_order = kl.count;
+  sp.order0 = kl.order0; sp.queue_idx = kl.kind;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->profiling) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, P->stream));
+  }
+  kern<<<grid, FACfg<NX, NU, Real>::NT, kl.smem, P->stream>>>(P->dev<Real>(), sp);
+  P->check_launch("k_dr");
+  if (P->profiling) {
+    CK(cudaEventRecord(e1, P->stream));
+    P->prof_events.push_back({e0, e1});
+    P->prof_launches++;
+  }
+}
+
+// NRTO-DR: gain-solve factors for (Q_v + r_χ I + σ Σ Â_jᵀÂ_j), then one persistent launch per kind.
 template <typename Real>
 void launch_dr(nrto_problem* P, const nrto_solver_opts& o, SolveParams sp) {
-  (void)P; (void)o; (void)sp;
-  fail(NRTO_ERR_INVALID, "NRTO-DR solver not available in this build");
+  Dev<Real> D = P->dev<Real>();
+  k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.sigma, o.r_chi);
+  P->check_launch("k_gain_factors");
+  CK(cudaMemsetAsync(P->d_queue, 0, 4 * sizeof(int), P->stream));
+  for (int k = 0; k < 3; ++k) {
+    const KindLaunch& kl = P->kl[k];
+    if (kl.count == 0) continue;
+    if (k == KIND_UNICYCLE) launch_dr_kind<3, 2, Real>(P, kl, sp);
+    else if (k == KIND_QUADCOPTER) launch_dr_kind<12, 4, Real>(P, kl, sp);
+    else launch_dr_kind<14, 7, Real>(P, kl, sp);
+  }
 }

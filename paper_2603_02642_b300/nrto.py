@@ -172,7 +172,7 @@ class Problem:
         F_G0: lambda x: x.n_rows, F_P: lambda x: x.n_rows, F_PT: lambda x: x.n_rows, F_LAMP: lambda x: x.n_rows,
         F_BHAT: lambda x: x.n_entries_state, F_BVEC: lambda x: x.n_entries_state // x.nx * x.nu,
         F_LAMNU: lambda x: x.n_entries, F_K: lambda x: x.T * x.nu * x.nx, F_KACC: lambda x: x.T * x.nu * x.nx,
-        F_GM: lambda x: x.T * x.nu * x.nu, F_SCAL: lambda x: 8, F_STATS: lambda x: 5,
+        F_GM: lambda x: x.T * x.nu * x.nu, F_SCAL: lambda x: 8, F_STATS: lambda x: 6,
     }
 
     def __init__(self, instances, precision=PREC_FP64, stream=None):
