@@ -205,6 +205,34 @@ nrto_status nrto_phase_cycles(nrto_problem_t p, long long* cycles, int n);
 /* Number of kernel launches the library issued since create (all of its own kernels). */
 long long nrto_kernel_launches(nrto_problem_t p);
 
+/* ---- Learned warm start: a GELU multilayer perceptron (the paper names learning a warm start
+ * for the inner solver as future work and fixes no network; this is the library's own).
+ * z_l = h_{l-1} W_lᵀ + b_l, h_l = gelu(z_l) = z_l Φ(z_l) for hidden layers, y = z_L.  Trained on the
+ * masked mean-squared error Σ mask (y - t)² / Σ mask with Adam (β₁ = 0.9, β₂ = 0.999, ε = 1e-8).
+ * FP32 master parameters; bf16 weights and activations on fifth-generation tensor cores with FP32
+ * accumulation.  Parameter layout (flat float array): for each layer l, W_l (out × in, row-major)
+ * then b_l (out).  All array arguments are host pointers, row-major. ---- */
+typedef struct nrto_mlp* nrto_mlp_t;
+
+/* dims: n_dims widths (input, hidden..., output); every width after the input a multiple of 8.
+ * max_batch: a multiple of 8.  Parameters start at zero (set them with nrto_mlp_set_params). */
+nrto_status nrto_mlp_create(const int* dims, int n_dims, int max_batch, void* stream, nrto_mlp_t* out);
+nrto_status nrto_mlp_destroy(nrto_mlp_t m);
+long long nrto_mlp_num_params(nrto_mlp_t m);
+/* Copy all parameters in (resets the Adam moments and step count) or out. */
+nrto_status nrto_mlp_set_params(nrto_mlp_t m, const float* params);
+nrto_status nrto_mlp_get_params(nrto_mlp_t m, float* params);
+/* y (batch × out) = network(x) (batch × in), 1 <= batch <= max_batch. */
+nrto_status nrto_mlp_forward(nrto_mlp_t m, const float* x, int batch, float* y);
+/* One training step on (x, target, mask): forward, backward, then Adam with learning rate lr
+ * (lr = 0: gradients only).  loss (may be NULL) receives the masked MSE before the update; grads
+ * (may be NULL) the gradient in the parameter layout.  batch: a multiple of 8 <= max_batch.
+ * NRTO_ERR_TIMEOUT if a tensor-core pipeline wait gave up (the result is then invalid). */
+nrto_status nrto_mlp_train_step(nrto_mlp_t m, const float* x, const float* target, const float* mask,
+                                int batch, float lr, double* loss, float* grads);
+/* Number of kernel launches issued for this network since create. */
+long long nrto_mlp_kernel_launches(nrto_mlp_t m);
+
 /* nrto_solve without device allocation.  The paper has no counterpart: this is a library service.
  * Some callers cannot call cudaMalloc: real-time control loops that must not pay an allocation's
  * latency and implicit synchronization, and processes whose device memory is held by another

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libnrto.so")
-SOURCES = ["api.cu"]
+SOURCES = ["api.cu", "mlp.cu"]
 FLAGS = ["-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-lineinfo",
          "-gencode", "arch=compute_103a,code=sm_103a", "--expt-relaxed-constexpr"]
 
@@ -28,7 +28,7 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/api.cu (which includes every kernel header) into libnrto.so if stale."""
+    """Compile csrc/api.cu (solver kernels) and csrc/mlp.cu (warm-start network) into libnrto.so if stale."""
     if not force and not _stale():
         return OUT
     cmd = ["nvcc", *FLAGS, "-o", OUT + ".tmp", *[os.path.join(CSRC, s) for s in SOURCES]]

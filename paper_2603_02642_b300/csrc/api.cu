@@ -688,6 +688,9 @@ nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long 
 
 }  // namespace
 
+// Message for nrto_last_error from the other translation units of the library.
+void nrto_internal_set_error(const std::string& msg) { g_last_error = msg; }
+
 // =============================================================================================
 extern "C" {
 

@@ -84,12 +84,25 @@ def load():
     lib.nrto_phase_cycles.restype = C.c_int
     lib.nrto_solve_noalloc.argtypes = [C.POINTER(ProblemDesc), C.c_int, C.c_int, C.POINTER(SolverOpts), C.c_int,
                                        C.c_void_p, _dp, _dp, _dp]
+    _fp = C.POINTER(C.c_float)
+    lib.nrto_mlp_create.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_int, C.c_void_p, C.POINTER(P)]
+    lib.nrto_mlp_destroy.argtypes = [P]
+    lib.nrto_mlp_num_params.argtypes = [P]
+    lib.nrto_mlp_num_params.restype = C.c_longlong
+    lib.nrto_mlp_set_params.argtypes = [P, _fp]
+    lib.nrto_mlp_get_params.argtypes = [P, _fp]
+    lib.nrto_mlp_forward.argtypes = [P, _fp, C.c_int, _fp]
+    lib.nrto_mlp_train_step.argtypes = [P, _fp, _fp, _fp, C.c_int, C.c_float, _dp, _fp]
+    lib.nrto_mlp_kernel_launches.argtypes = [P]
+    lib.nrto_mlp_kernel_launches.restype = C.c_longlong
     lib.nrto_kernel_launches.argtypes = [P]
     lib.nrto_kernel_launches.restype = C.c_longlong
     lib.nrto_last_error.restype = C.c_char_p
     for name in ["nrto_problem_create", "nrto_problem_destroy", "nrto_problem_info", "nrto_problem_update",
                  "nrto_linearize", "nrto_set_trust_radius", "nrto_solve_socp", "nrto_outer_step", "nrto_solve",
-                 "nrto_set_warm_start", "nrto_export", "nrto_import", "nrto_profile", "nrto_solve_noalloc"]:
+                 "nrto_set_warm_start", "nrto_export", "nrto_import", "nrto_profile", "nrto_solve_noalloc",
+                 "nrto_mlp_create", "nrto_mlp_destroy", "nrto_mlp_set_params", "nrto_mlp_get_params",
+                 "nrto_mlp_forward", "nrto_mlp_train_step"]:
         getattr(lib, name).restype = C.c_int
     _LIB = lib
     return lib
@@ -321,3 +334,75 @@ def solve_noalloc(instances, opts: Options, n_outer=10, precision=PREC_FP64, str
         a += x.T * x.nu
         b += x.T * x.nu * x.nx
     return dict(u_bar=us, K=Ks, merit=m)
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+class MLP:
+    """The warm-start network on the GPU (nrto_mlp_*): GELU hidden layers, masked MSE, Adam.
+    Parameters travel as one flat float32 array: per layer W (out, in) row-major, then b."""
+
+    def __init__(self, dims, max_batch, stream=None):
+        lib = load()
+        self.dims = [int(d) for d in dims]
+        self.max_batch = int(max_batch)
+        arr = (C.c_int * len(self.dims))(*self.dims)
+        h = C.c_void_p()
+        _check(lib.nrto_mlp_create(arr, len(self.dims), self.max_batch, C.c_void_p(stream), C.byref(h)))
+        self._h = h
+        self.n_params = int(lib.nrto_mlp_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().nrto_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, W, b):
+        return np.concatenate([np.concatenate([w.reshape(-1), bb.reshape(-1)]) for w, bb in zip(W, b)]).astype(np.float32)
+
+    def unpack(self, flat):
+        W, b, o = [], [], 0
+        for din, dout in zip(self.dims[:-1], self.dims[1:]):
+            W.append(flat[o:o + din * dout].reshape(dout, din))
+            o += din * dout
+            b.append(flat[o:o + dout].copy())
+            o += dout
+        return W, b
+
+    def set_params(self, flat):
+        f = _f32(flat)
+        assert f.size == self.n_params
+        _check(load().nrto_mlp_set_params(self._h, f.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def get_params(self):
+        f = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().nrto_mlp_get_params(self._h, f.ctypes.data_as(C.POINTER(C.c_float))))
+        return f
+
+    def forward(self, x):
+        x = _f32(x)
+        y = np.zeros((x.shape[0], self.dims[-1]), dtype=np.float32)
+        _fp = C.POINTER(C.c_float)
+        _check(load().nrto_mlp_forward(self._h, x.ctypes.data_as(_fp), x.shape[0], y.ctypes.data_as(_fp)))
+        return y
+
+    def train_step(self, x, t, mask, lr, want_grads=False):
+        x, t, mask = _f32(x), _f32(t), _f32(mask)
+        _fp = C.POINTER(C.c_float)
+        loss = C.c_double(0.0)
+        g = np.zeros(self.n_params, dtype=np.float32) if want_grads else None
+        _check(load().nrto_mlp_train_step(self._h, x.ctypes.data_as(_fp), t.ctypes.data_as(_fp),
+                                          mask.ctypes.data_as(_fp), x.shape[0], float(lr), C.byref(loss),
+                                          g.ctypes.data_as(_fp) if g is not None else None))
+        return (loss.value, g) if want_grads else loss.value
+
+    def kernel_launches(self):
+        return int(load().nrto_mlp_kernel_launches(self._h))
