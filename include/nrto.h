@@ -90,8 +90,9 @@ typedef struct {
    * using the residuals of the iteration before last; scaled duals are rescaled.  0 disables it. */
   int adapt_every;
   double adapt_mu, adapt_tau, rho_min, rho_max;
-  /* Stall stop: every stall_every iterations, stop when r_p fell by less than the factor
-   * stall_ratio since the previous checkpoint (status 5).  0 disables it. */
+  /* Stall stop: every stall_every iterations, stop when r_p is above eps_p and fell by less than
+   * the factor stall_ratio since the previous checkpoint (status 5; an infeasible linearization).
+   * 0 disables it. */
   int stall_every;
   double stall_ratio;
 } nrto_solver_opts;

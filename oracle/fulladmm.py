@@ -48,7 +48,9 @@ class FullADMMOptions:
     rho_min: float = 1e-3
     rho_max: float = 1e3
     # Stall stop: at iterations l that are multiples of stall_every (l >= 2·stall_every), stop when
-    # r_p^l > stall_ratio · r_p^{l-stall_every} (and the tolerances are not met).  0 disables it.
+    # r_p^l > ε_p and r_p^l > stall_ratio · r_p^{l-stall_every} (and the tolerances are not met): a
+    # primal residual that is above its tolerance and no longer falls marks an infeasible
+    # linearization.  0 disables it.
     stall_every: int = 0
     stall_ratio: float = 0.9
 
@@ -191,7 +193,7 @@ def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None
             break
         S_ = opts.stall_every
         if opts.check and S_ > 0 and it % S_ == 0:
-            if it >= 2 * S_ and r_p > opts.stall_ratio * rp_mark:
+            if it >= 2 * S_ and r_p > opts.eps_p and r_p > opts.stall_ratio * rp_mark:
                 s.stalled = True
                 break
             rp_mark = r_p

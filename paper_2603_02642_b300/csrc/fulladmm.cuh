@@ -792,7 +792,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
       if (bad) { status = ST_NUMERIC; break; }
       if (sp.check && r_p <= sp.eps_p && r_d <= sp.eps_d) { status = ST_CONVERGED; break; }
       if (sp.check && sp.stall_every > 0 && iters % sp.stall_every == 0) {
-        if (iters >= 2 * sp.stall_every && r_p > sp.stall_ratio * rp_mark) { status = ST_STALLED; break; }
+        if (iters >= 2 * sp.stall_every && r_p > sp.eps_p && r_p > sp.stall_ratio * rp_mark) { status = ST_STALLED; break; }
         rp_mark = r_p;
       }
       if (b - 1 == Lmax) { status = ST_MAXITER; break; }
