@@ -95,6 +95,10 @@ typedef struct {
    * 0 disables it. */
   int stall_every;
   double stall_ratio;
+  /* FullADMM with a warm start (nrto_set_warm_start): when the warm-started run stops on the stall
+   * rule, rerun the instance from the cold initialization of Algorithm 1 with the full iteration
+   * budget (reported iterations count both runs; NRTO_F_STATS flags it).  0 disables it. */
+  int warm_fallback;
 } nrto_solver_opts;
 
 /* Per-instance sizes, for sizing output buffers. */
@@ -181,9 +185,10 @@ enum {
   NRTO_F_KACC = 14,  /* T*nu*nx    gains of the accepted nominal (outer loop)                 */
   NRTO_F_DX = 15,    /* (T+1)*nx   δx of the last inner solve                                */
   NRTO_F_SCAL = 16,  /* 8: r_p, r_d, r_p(paper), r_d(paper), merit, candidate merit, cost, trust r */
-  NRTO_F_STATS = 17  /* 6, read-only: inner iterations since the last nrto_solve reset, iterations of
-                        the last inner solve, its status, accepted outer steps, its final ρ, and
-                        (NRTO-DR) the DR iterations summed over its ADMM iterations               */
+  NRTO_F_STATS = 17  /* 7, read-only: inner iterations since the last nrto_solve reset, iterations of
+                        the last inner solve, its status, accepted outer steps, its final ρ,
+                        (NRTO-DR) the DR iterations summed over its ADMM iterations, and 1 if the
+                        last solve fell back from a warm start to a cold start                    */
 };
 nrto_status nrto_export(nrto_problem_t p, int field, int instance, double* dst, long long count);
 nrto_status nrto_import(nrto_problem_t p, int field, int instance, const double* src, long long count);

@@ -198,3 +198,16 @@ def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None
                 break
             rp_mark = r_p
     return s
+
+
+def solve_warm_with_fallback(inst, lin, opts: FullADMMOptions, K0, pt0, lam_p0):
+    """Learned-warm-start solve with its fallback: iterate from warm_state(K0, p̃0, λ_p0); if that
+    run stops on the stall rule, run the cold solve (zero_state, Algorithm 1 initialization) with
+    the full iteration budget, so the outcome is never worse than without the warm start.
+    Returns (state, fell_back); state.iters counts both runs."""
+    s = iterate(inst, lin, opts, warm_state(lin, K0, pt0, lam_p0))
+    if not s.stalled:
+        return s, False
+    c = iterate(inst, lin, opts, zero_state(lin))
+    c.iters = s.iters + c.iters
+    return c, True

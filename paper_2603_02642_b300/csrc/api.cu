@@ -404,6 +404,7 @@ void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
   sp.adapt_every = o.adapt_every; sp.stall_every = o.stall_every;
   sp.adapt_mu = o.adapt_mu; sp.adapt_tau = o.adapt_tau; sp.rho_min = o.rho_min; sp.rho_max = o.rho_max;
   sp.stall_ratio = o.stall_ratio;
+  sp.fallback = o.warm_fallback;
   P->warm_pending = false;
   if (o.solver == NRTO_SOLVER_FULLADMM) {
     k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.rho, 0.0);
@@ -571,7 +572,7 @@ long long field_count(const Inst& I, int f) {
     case NRTO_F_K: case NRTO_F_KACC: return (long long)I.T * I.nu * I.nx;
     case NRTO_F_GM: return (long long)I.T * I.nu * I.nu;
     case NRTO_F_SCAL: return 8;
-    case NRTO_F_STATS: return 6;
+    case NRTO_F_STATS: return 7;
   }
   return -1;
 }
@@ -614,7 +615,7 @@ nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long 
         double scv[NSC];
         CK(cudaMemcpy(scv, p->d_sc + (long long)i * NSC, sizeof(scv), cudaMemcpyDeviceToHost));
         buf[0] = is[IS_CUMITERS]; buf[1] = is[IS_ITERS]; buf[2] = is[IS_STATUS]; buf[3] = is[IS_NACC];
-        buf[4] = scv[SC_RHO]; buf[5] = is[IS_DRITERS];
+        buf[4] = scv[SC_RHO]; buf[5] = is[IS_DRITERS]; buf[6] = is[IS_FALLBACK];
         return NRTO_OK;
       }
       case NRTO_F_SCAL: {

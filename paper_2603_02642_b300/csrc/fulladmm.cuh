@@ -33,6 +33,7 @@ struct SolveParams {
   int chunk, max_rows, tmax, n_order;   // chunk entries, rows per chunk, max T of the launch, instances
   int order0, queue_idx;
   int adapt_every, stall_every;         // residual balancing / stall stop periods (0 = off)
+  int fallback;                         // warm start: rerun cold when the warm-started run stalls
   double adapt_mu, adapt_tau, rho_min, rho_max, stall_ratio;
 };
 
@@ -932,8 +933,30 @@ __global__ void __launch_bounds__(FACfg<NX, NU, Real>::NT, FACfg<NX, NU, Real>::
     __syncthreads();
     if (q >= sp.n_order) break;
     const int inst = D.order[sp.order0 + q];
+    int* isr = D.is + inst * NIS;
+    if (threadIdx.x == 0) isr[IS_FALLBACK] = 0;
     fulladmm_instance<NX, NU, Real>(D, sp, inst, sm, bars, ph, &s_flag, ric_scr);
-    if (D.is[inst * NIS + IS_STATUS] == ST_TIMEOUT) break;
+    // learned warm start that stalled: rerun from the cold initialization with the full budget
+    if (sp.warm && sp.fallback && isr[IS_STATUS] == ST_STALLED) {
+      const int it1 = isr[IS_ITERS];
+      SolveParams sp2 = sp;
+      sp2.warm = 0;
+      __syncthreads();
+      if (threadIdx.x == 0) isr[IS_FALLBACK] = 1;
+      {
+        // residual balancing may have refactored block 2 and the gain divisors for another ρ
+        if (sp.adapt_every > 0) {
+          gain_divisors<Real>(D, inst, sp.rho);
+          __syncthreads();
+          if ((threadIdx.x >> 5) == 0) riccati_factor_warp<Real>(D, inst, sp.rho, ric_scr);
+          __syncthreads();
+        }
+        fulladmm_instance<NX, NU, Real>(D, sp2, inst, sm, bars, ph, &s_flag, ric_scr);
+        if (threadIdx.x == 0) isr[IS_ITERS] += it1;
+      }
+      __syncthreads();
+    }
+    if (isr[IS_STATUS] == ST_TIMEOUT) break;
   }
 }
 

@@ -116,7 +116,7 @@ NRTO_HD SlotL slot_layout(int nx, int nu, int T) {
 // Per-instance scalar record (double) and integer record.
 enum : int { SC_RTRUST = 0, SC_RP, SC_RD, SC_RPP, SC_RDP, SC_SCAL_RP, SC_SCAL_RD, SC_SCAL_RPP, SC_SCAL_RDP,
              SC_PHI, SC_PHI_CAND, SC_COST, SC_RHO, SC_RDR, NSC = 16 };
-enum : int { IS_STATUS = 0, IS_ITERS, IS_SLOT, IS_ACCEPT, IS_DRITERS, IS_CUMITERS, IS_NACC, NIS = 8 };
+enum : int { IS_STATUS = 0, IS_ITERS, IS_SLOT, IS_ACCEPT, IS_DRITERS, IS_CUMITERS, IS_NACC, IS_FALLBACK, NIS = 8 };
 
 template <typename Real>
 struct LinSlot {

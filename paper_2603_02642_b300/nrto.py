@@ -41,7 +41,7 @@ class SolverOpts(C.Structure):
                 ("r0", C.c_double), ("r_min", C.c_double), ("w_p", C.c_double),
                 ("adapt_every", C.c_int), ("adapt_mu", C.c_double), ("adapt_tau", C.c_double),
                 ("rho_min", C.c_double), ("rho_max", C.c_double),
-                ("stall_every", C.c_int), ("stall_ratio", C.c_double)]
+                ("stall_every", C.c_int), ("stall_ratio", C.c_double), ("warm_fallback", C.c_int)]
 
 
 class InstanceInfo(C.Structure):
@@ -147,12 +147,13 @@ class Options:
     rho_max: float = 1e3
     stall_every: int = 0
     stall_ratio: float = 0.9
+    warm_fallback: int = 0
 
     def c(self) -> SolverOpts:
         return SolverOpts(self.solver, self.rho, self.alpha, self.r_chi, self.sigma, self.eps_p, self.eps_d,
                           self.eps_dr, self.max_inner, self.max_dr, self.check, self.r0, self.r_min, self.w_p,
                           self.adapt_every, self.adapt_mu, self.adapt_tau, self.rho_min, self.rho_max,
-                          self.stall_every, self.stall_ratio)
+                          self.stall_every, self.stall_ratio, self.warm_fallback)
 
 
 def _desc(inst, keep):
@@ -185,7 +186,7 @@ class Problem:
         F_G0: lambda x: x.n_rows, F_P: lambda x: x.n_rows, F_PT: lambda x: x.n_rows, F_LAMP: lambda x: x.n_rows,
         F_BHAT: lambda x: x.n_entries_state, F_BVEC: lambda x: x.n_entries_state // x.nx * x.nu,
         F_LAMNU: lambda x: x.n_entries, F_K: lambda x: x.T * x.nu * x.nx, F_KACC: lambda x: x.T * x.nu * x.nx,
-        F_GM: lambda x: x.T * x.nu * x.nu, F_SCAL: lambda x: 8, F_STATS: lambda x: 6,
+        F_GM: lambda x: x.T * x.nu * x.nu, F_SCAL: lambda x: 8, F_STATS: lambda x: 7,
     }
 
     def __init__(self, instances, precision=PREC_FP64, stream=None):

@@ -152,3 +152,48 @@ def test_stall_stop_matches_oracle():
     prob.set_trust_radius(0.01)
     out = prob.solve_socp(nrto.Options(rho=1.0, max_inner=5000, check=1, stall_every=100))
     assert s.stalled and out["status"][0] == 5 and out["iters"][0] == s.iters
+
+
+def test_warm_start_iterates_parity_fp64(cases):
+    """nrto_set_warm_start (k_v, p̃, λ_p; λ_ν = 0) then 25 iterations: same iterates as the oracle
+    started from warm_state."""
+    inst = cases["quad_T40_o5"]
+    lin = _lin_oracle(inst)
+    w = F.iterate(inst, lin, F.FullADMMOptions(rho=10.0, r_trust=0.5, check=False), n_iter=7)
+    o = F.FullADMMOptions(rho=10.0, r_trust=0.5, check=False)
+    s = F.iterate(inst, lin, o, F.warm_state(lin, w.K, w.pt, w.lam_p), n_iter=25)
+    prob = nrto.Problem([inst], nrto.PREC_FP64)
+    prob.linearize()
+    prob.set_trust_radius(0.5)
+    prob.set_warm_start([w.K], [w.pt], [w.lam_p])
+    out = prob.solve_socp(nrto.Options(rho=10.0, max_inner=25, check=0))
+    assert_close(out["K"][0], s.K, RTOL64, "K")
+    assert_close(out["du"][0], s.du, RTOL64, "du")
+    assert_close(out["pt"][0], s.pt, RTOL64, "p~")
+    assert_close(prob.export(nrto.F_LAMNU, 0), ragged_from_dense(lin, s.lam_nu), RTOL64, "lambda_nu")
+    prob.close()
+
+
+def test_warm_start_fallback_matches_oracle():
+    from .test_oracle_fulladmm import tiny_unicycle
+    inst = tiny_unicycle()
+    inst.obs_center = np.array([[0.5, 0.0]])
+    inst.obs_radius = np.array([0.3])
+    lin = _lin_oracle(inst)
+    w = F.iterate(inst, lin, F.FullADMMOptions(rho=1.0, r_trust=0.01, check=False), n_iter=5)
+    # residual balancing on: the cold rerun must start again from ρ = 1 with matching factors
+    o = F.FullADMMOptions(rho=1.0, r_trust=0.01, max_iter=2000, stall_every=100, adapt_every=25)
+    s, fell = F.solve_warm_with_fallback(inst, lin, o, w.K, w.pt, w.lam_p)
+    prob = nrto.Problem([inst], nrto.PREC_FP64)
+    prob.linearize()
+    prob.set_trust_radius(0.01)
+    prob.set_warm_start([w.K], [w.pt], [w.lam_p])
+    out = prob.solve_socp(nrto.Options(rho=1.0, max_inner=2000, check=1, stall_every=100, adapt_every=25,
+                                       warm_fallback=1))
+    st = prob.export(nrto.F_STATS, 0)
+    assert fell and st[6] == 1
+    assert out["iters"][0] == s.iters
+    # The linearization is infeasible on purpose (that is what makes the warm start stall), so the
+    # iterates drift without bound and only the discrete outcome is compared.
+    assert out["status"][0] == (5 if s.stalled else (1 if s.converged else 2))
+    prob.close()

@@ -184,3 +184,27 @@ def test_stall_stop_on_infeasible_linearization():
     lin = P.linearize(inst, inst.u_init)
     s = F.iterate(inst, lin, F.FullADMMOptions(rho=1.0, r_trust=0.01, max_iter=5000, stall_every=100))
     assert s.stalled and not s.converged and s.iters < 5000 and s.r_p > 1e-3
+
+
+def test_warm_start_fallback_runs_the_cold_solve():
+    """A warm start on an infeasible linearization stalls; the fallback then equals the cold solve
+    with the full budget.  On a feasible problem, a warm start at the solution's (k_v, p̃, λ_p)
+    needs no fallback and converges (λ_ν restarts at zero, so it is not immediate)."""
+    inst = tiny_unicycle()
+    inst.obs_center = np.array([[0.5, 0.0]])
+    inst.obs_radius = np.array([0.3])
+    lin = P.linearize(inst, inst.u_init)
+    o = F.FullADMMOptions(rho=1.0, r_trust=0.01, max_iter=2000, stall_every=100)
+    w = F.iterate(inst, lin, F.FullADMMOptions(rho=1.0, r_trust=0.01, check=False), n_iter=5)
+    s, fell = F.solve_warm_with_fallback(inst, lin, o, w.K, w.pt, w.lam_p)
+    first = F.iterate(inst, lin, o, F.warm_state(lin, w.K, w.pt, w.lam_p))
+    cold = F.iterate(inst, lin, o, F.zero_state(lin))
+    assert fell and first.stalled
+    assert s.iters == first.iters + cold.iters
+    assert np.array_equal(s.K, cold.K) and np.array_equal(s.du, cold.du)
+    feas = tiny_unicycle()
+    linf = P.linearize(feas, feas.u_init)
+    of = F.FullADMMOptions(rho=10.0, r_trust=0.5, eps_p=1e-6, eps_d=1e-6, max_iter=30000, stall_every=100)
+    ref = F.iterate(feas, linf, of)
+    s2, fell2 = F.solve_warm_with_fallback(feas, linf, of, ref.K, ref.pt, ref.lam_p)
+    assert not fell2 and s2.converged and np.allclose(s2.du, ref.du, atol=1e-5)
