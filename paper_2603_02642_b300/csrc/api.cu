@@ -174,6 +174,7 @@ struct nrto_problem {
   void* d_bhat[2] = {nullptr, nullptr};
   void* d_bvec[2] = {nullptr, nullptr};
   void* d_lam = nullptr;
+  void* d_sr = nullptr;
   double *d_p = nullptr, *d_pt = nullptr, *d_ptn = nullptr, *d_lamp = nullptr, *d_w = nullptr, *d_lamw = nullptr,
          *d_s = nullptr, *d_ell = nullptr, *d_dd = nullptr, *d_rnorm = nullptr;
   double* d_sc = nullptr;
@@ -235,6 +236,7 @@ struct nrto_problem {
       D.slot[s].bvec = static_cast<Real*>(d_bvec[s]);
     }
     D.lam = static_cast<Real*>(d_lam);
+    D.sr = static_cast<Real*>(d_sr);
     D.p = d_p; D.pt = d_pt; D.ptn = d_ptn; D.lamp = d_lamp; D.w = d_w; D.lamw = d_lamw; D.s = d_s;
     D.ell = d_ell; D.dd = d_dd; D.rnorm = d_rnorm;
     D.sc = d_sc; D.is = d_is; D.queue = d_queue; D.order = d_order;
@@ -459,13 +461,6 @@ void choose_chunk(KindLaunch& kl) {
   kl.max_rows = chunk / (2 * nx) + 2;
   kl.smem = smem_for<Real>(kl.kind, chunk, kl.max_rows);
   if (kl.smem > (size_t)smem_budget<Real>()) fail(NRTO_ERR_INVALID, "horizon too long for the shared-memory budget of this precision");
-  // the row-group partials of Z' are summed in the (then idle) chunk buffers
-  const int nu = kind_nu(kl.kind), ng = (kl.kind == KIND_UNICYCLE) ? 4 : 1;
-  size_t bb = 0;
-  if (kl.kind == KIND_UNICYCLE) bb = FASmem<3, 2, Real>::buf_bytes(chunk, kl.max_rows);
-  else if (kl.kind == KIND_QUADCOPTER) bb = FASmem<12, 4, Real>::buf_bytes(chunk, kl.max_rows);
-  else bb = FASmem<14, 7, Real>::buf_bytes(chunk, kl.max_rows);
-  if ((size_t)ng * kl.tmax * nu * nx * sizeof(Real) > 2 * bb) fail(NRTO_ERR_INVALID, "internal: chunk buffers too small for the row-group reduction");
 }
 
 // per-instance arena/slot field copy (device → host) of cnt(I) doubles at off(I)
@@ -748,26 +743,41 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
       I.row0 = row; I.ent0 = ent; I.bent0 = bent; I.arena0 = arena; I.slot0 = slot; I.arow0 = arow;
       I.grp0 = grp; I.cb0 = cb;
       I.dt = d.dt; I.tau = d.tau; I.sqrt_tau = std::sqrt(d.tau);
-      // State rows in chunks of whole rows for the persistent solver; every chunk starts on a
+      // State rows in chunks of whole rows for the persistent solver.  Their storage order folds the
+      // time steps (t = 1, T, 2, T-1, ...) so that every chunk mixes short and long rows; the logical
+      // row order (rinfo, per-row arrays, rent/rbent) stays time-major.  Every chunk starts on a
       // 4-element (16-byte) boundary of the entry and b arrays so that it can be bulk-copied.
       const int chunk = P->kl[d.dyn].chunk;
+      const int nsr = (int)srows.size();
+      std::vector<int> order;
+      if (rpt > 0)
+        for (int pidx = 0; pidx < d.T; ++pidx) {
+          const int t = (pidx % 2 == 0) ? pidx / 2 + 1 : d.T - (pidx - 1) / 2;
+          for (int q = 0; q < rpt; ++q) order.push_back((t - 1) * rpt + q);
+        }
+      if ((int)order.size() != nsr) fail(NRTO_ERR_INVALID, "internal: state rows not uniform over steps");
+      rent.resize(row + nsr + crows.size());
+      rbent.resize(row + nsr + crows.size());
+      rmeta.resize(row + nsr + crows.size());
+      for (int r = 0; r < nsr; ++r) P->h_rinfo.push_back(srows[r]);
       int nch = 0;
       long long accn = 0;
       long long n_ent_state = 0;
-      for (int r = 0; r < (int)srows.size(); ++r) {
+      for (int pos = 0; pos < nsr; ++pos) {
+        const int r = order[pos];
         const int4& rr = srows[r];
         const long long len = (long long)(rr.x + 1) * d.nx;
-        if (r == 0 || accn + len > chunk) {
-          if (r > 0) {
+        if (pos == 0 || accn + len > chunk) {
+          if (pos > 0) {
             ChunkInfo& c = chunks.back();
-            c.r1 = r;
+            c.r1 = pos;
             c.ne = (int)(((ent - c.e0) + 3) & ~3LL);
             c.nb = (int)(((bent - c.b0) + 3) & ~3LL);
           }
           ent = (ent + 3) & ~3LL;
           bent = (bent + 3) & ~3LL;
           ChunkInfo c{};
-          c.e0 = ent; c.b0 = bent; c.r0 = r;
+          c.e0 = ent; c.b0 = bent; c.r0 = pos;
           chunks.push_back(c);
           ++nch;
           accn = 0;
@@ -775,18 +785,17 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
         accn += len;
         const ChunkInfo& c = chunks.back();
         RowMeta m{};
-        m.off = (int)(ent - c.e0); m.boff = (int)(bent - c.b0); m.t = rr.x;
-        rmeta.push_back(m);
-        P->h_rinfo.push_back(rr);
-        rent.push_back(ent);
-        rbent.push_back(bent);
+        m.off = (int)(ent - c.e0); m.boff = (int)(bent - c.b0); m.t = rr.x; m.pad = r;
+        rmeta[row + pos] = m;
+        rent[row + r] = ent;
+        rbent[row + r] = bent;
         ent += len;
         bent += (long long)(rr.x + 1) * d.nu;
         n_ent_state += len;
       }
       if (nch > 0) {
         ChunkInfo& c = chunks.back();
-        c.r1 = (int)srows.size();
+        c.r1 = nsr;
         c.ne = (int)(((ent - c.e0) + 3) & ~3LL);
         c.nb = (int)(((bent - c.b0) + 3) & ~3LL);
         ent = (ent + 3) & ~3LL;
@@ -805,9 +814,9 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
           groups.back().y += 1;
         }
         P->h_rinfo.push_back(crows[q]);
-        rmeta.push_back(RowMeta{0, 0, -1, 0});
-        rent.push_back(ent);
-        rbent.push_back(-1);
+        rmeta[R] = RowMeta{0, 0, -1, 0};
+        rent[R] = ent;
+        rbent[R] = -1;
         ent += d.nx;
       }
       I.n_groups = ng;
@@ -854,6 +863,7 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
       P->d_bvec[s] = P->dalloc<char>(rs * (bent + 16));
     }
     P->d_lam = P->dalloc<char>(rs * (ent + 16));
+    P->d_sr = P->dalloc<char>(rs * (row + 4));
     // per-row arrays that are bulk-copied are read from an even row index with an even count
     P->d_p = P->dalloc<double>(row + 4); P->d_pt = P->dalloc<double>(row); P->d_ptn = P->dalloc<double>(row);
     P->d_lamp = P->dalloc<double>(row + 4); P->d_w = P->dalloc<double>(row); P->d_lamw = P->dalloc<double>(row);

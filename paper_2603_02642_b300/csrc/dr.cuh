@@ -409,7 +409,7 @@ template <int NX, int NU, typename Real>
 __device__ void dr_instance(const Dev<Real>& D, const SolveParams& sp, int inst, FASmem<NX, NU, Real>& sm,
                             uint64_t* bars, uint32_t* phase, int* s_flag, double* ric_scr) {
   using C = FACfg<NX, NU, Real>;
-  constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR = C::NWR, W = C::W, NCG = C::NCG, NG = C::NG, TPG = C::TPG;
+  constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR_MAX = C::NWR_MAX, W = C::W;
   const Inst I = D.inst[inst];
   const Arena L = arena_layout(NX, NU, I.T, I.n_obs, I.n_link);
   const SlotL SL = slot_layout(NX, NU, I.T);
@@ -428,10 +428,10 @@ __device__ void dr_instance(const Dev<Real>& D, const SolveParams& sp, int inst,
   PhaseTimer tm;
   tm.start(D.phase_cycles != nullptr);
 
-  const int grp = tid / TPG, lt = tid - grp * TPG, gwarp = lt >> 5;
-  int mk[PAIRS], ck[PAIRS];
-#pragma unroll
-  for (int k = 0; k < PAIRS; ++k) { const int P = lt + k * TPG; mk[k] = P / NCG; ck[k] = (P - mk[k] * NCG) * W; }
+  const ColMap cm = col_map<NX, NU, Real>(I.T, FASmem<NX, NU, Real>::zcap(sp.chunk, sp.max_rows, I.T));
+  const int grp = cm.grp, NG = cm.ng, NWR = cm.nwr, ck = cm.ck;
+  const int gwarp = (tid - (grp < NG ? grp : 0) * NWR * 32) >> 5;
+  const int mk[PAIRS] = {cm.mk[0], cm.mk[1]};
 
   // ---- initialization: ξ̃ = 0, p = λ = 0 (a warm start sets K̃ = K, p̃̃ = p = p̃ and keeps λ) ----
   for (long long e = tid; e < I.n_ent; e += NT) lam[I.ent0 + e] = (Real)0;
@@ -495,7 +495,7 @@ __device__ void dr_instance(const Dev<Real>& D, const SolveParams& sp, int inst,
           for (int k = 0; k < PAIRS; ++k) {
             if (mk[k] <= rm.t) {
               act = true;
-              const int e = rm.off + mk[k] * NX + ck[k];
+              const int e = rm.off + mk[k] * NX + ck;
               Real bv[NU], yb[W], l[W];
               ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
               ld_vec<W, Real>(bf.bhat + e, yb);
@@ -510,17 +510,15 @@ __device__ void dr_instance(const Dev<Real>& D, const SolveParams& sp, int inst,
               }
             }
           }
-          if (gwarp < NWR) {
-            if (__any_sync(0xffffffffu, act)) pn = warp_sum(pn);
-            if (lane == 0) sm.rowpart[q * NWR + gwarp] = pn;
-          }
+          if (__any_sync(0xffffffffu, act)) pn = warp_sum(pn);
+          if (lane == 0) sm.rowpart[q * NWR_MAX + gwarp] = pn;
         }
         __syncthreads();
         // projection of (2p̃ - t̃, 2η - η̃) onto K_j; t̃ relaxation
         for (int q = tid; q < nr; q += NT) {
           Real a2 = 0;
-          for (int w = 0; w < NWR; ++w) a2 += sm.rowpart[q * NWR + w];
-          const long long R = I.row0 + cki.r0 + q;
+          for (int w = 0; w < NWR; ++w) a2 += sm.rowpart[q * NWR_MAX + w];
+          const long long R = I.row0 + bf.meta[q].pad;
           double snew, tpi;
           soc_case(D.ptn[R], sqrt((double)a2), snew, tpi);
           sm.snew[q] = (Real)snew;
@@ -540,7 +538,7 @@ __device__ void dr_instance(const Dev<Real>& D, const SolveParams& sp, int inst,
 #pragma unroll
           for (int k = 0; k < PAIRS; ++k) {
             if (mk[k] <= rm.t) {
-              const int e = rm.off + mk[k] * NX + ck[k];
+              const int e = rm.off + mk[k] * NX + ck;
               Real bv[NU], yb[W], l[W];
               ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
               ld_vec<W, Real>(bf.bhat + e, yb);
@@ -578,14 +576,14 @@ __device__ void dr_instance(const Dev<Real>& D, const SolveParams& sp, int inst,
     }
     if (!ok) return -1.0;
     // Z' = Σ over row groups (fixed order)
-    if constexpr (NG == 1) {
+    if (NG == 1) {
 #pragma unroll
       for (int k = 0; k < PAIRS; ++k)
         if (mk[k] < T)
 #pragma unroll
           for (int u = 0; u < NU; ++u)
 #pragma unroll
-            for (int w = 0; w < W; ++w) ar[L.Zp + (long long)mk[k] * NU * NX + u * NX + ck[k] + w] = (double)z[k][u][w];
+            for (int w = 0; w < W; ++w) ar[L.Zp + (long long)mk[k] * NU * NX + u * NX + ck + w] = (double)z[k][u][w];
     } else {
       Real* part = sm.buf[0].lam;
       const int nz = T * NU * NX;
@@ -595,11 +593,10 @@ __device__ void dr_instance(const Dev<Real>& D, const SolveParams& sp, int inst,
 #pragma unroll
           for (int u = 0; u < NU; ++u)
 #pragma unroll
-            for (int w = 0; w < W; ++w) part[grp * nz + mk[k] * NU * NX + u * NX + ck[k] + w] = z[k][u][w];
+            for (int w = 0; w < W; ++w) part[grp * nz + mk[k] * NU * NX + u * NX + ck + w] = z[k][u][w];
       __syncthreads();
       for (int q = tid; q < nz; q += NT) {
         Real acc = 0;
-#pragma unroll
         for (int g2 = 0; g2 < NG; ++g2) acc += part[g2 * nz + q];
         ar[L.Zp + q] = (double)acc;
       }

@@ -39,7 +39,7 @@ struct SolveParams {
 
 // Solver CTA shape for the compute precision float (threads, resident CTAs per SM); FP64 uses 512 × 1.
 #ifndef NRTO_FA_NT_F32
-#define NRTO_FA_NT_F32 1024
+#define NRTO_FA_NT_F32 512
 #endif
 #ifndef NRTO_FA_MINB_F32
 #define NRTO_FA_MINB_F32 1
@@ -53,13 +53,46 @@ struct FACfg {
   static constexpr int TMAXC = (NX == 3) ? 256 : (NX == 12 ? 160 : 128);
   static constexpr int W = (NX == 3) ? 3 : 2;            // consecutive components of a block per thread
   static constexpr int NCG = NX / W;                     // column groups per ζ-block
-  static constexpr int NG = (NX == 3) ? (NT >= 1024 ? 4 : 2) : 1;   // row groups (CTA slices on different rows)
-  static constexpr int TPG = NT / NG;                    // threads per row group
-  static constexpr int NCOL = (TMAXC + 1) * NCG;         // column groups of the longest row
-  static constexpr int PAIRS = (NCOL + TPG - 1) / TPG;   // column groups per thread
-  static constexpr int NWG = TPG / 32;                   // warps per row group
-  static constexpr int NWR = (NWG < (NCOL + 31) / 32) ? NWG : (NCOL + 31) / 32;   // warps of a group touching a row
+  static constexpr int PAIRS = 2;                        // a thread owns blocks m and T - m
+  static constexpr int NPAIR_MAX = TMAXC / 2 + 1;        // block pairs of the longest horizon
+  static constexpr int TPG_MAX = (NPAIR_MAX * NCG + 31) / 32 * 32;   // threads of one row group
+  static constexpr int NWR_MAX = TPG_MAX / 32;           // warps of a row group (partial row norms)
 };
+
+// Column ownership in the row pass for an instance of horizon T.  Rows at time t hold blocks
+// m = 0..t; thread lt of a row group owns components c .. c+W-1 of block m1 = lt / NCG and of its
+// mirror m2 = T - m1, so that over rows of all lengths every thread has about the same work.  A
+// row group is tpg = roundup32(npair·NCG) threads; ng groups work on different rows of a chunk.
+struct ColMap {
+  int grp, ng, nwr, ck;
+  int mk[2];
+};
+template <int NX, int NU, typename Real>
+__device__ __forceinline__ ColMap col_map(int T, int zcap) {
+  using C = FACfg<NX, NU, Real>;
+  ColMap cm;
+  const int npair = T / 2 + 1;
+  const int tpg = (npair * C::NCG + 31) / 32 * 32;
+  int ng = C::NT / tpg;
+  if (ng < 1) ng = 1;
+  if (ng > zcap) ng = zcap > 0 ? zcap : 1;
+  cm.ng = ng;
+  cm.nwr = tpg / 32;
+  const int tid = threadIdx.x;
+  cm.grp = tid / tpg;
+  const int lt = tid - cm.grp * tpg;
+  constexpr int OFF = 1 << 20;   // no row reaches this block index
+  if (cm.grp >= ng || lt >= npair * C::NCG) {
+    cm.mk[0] = OFF; cm.mk[1] = OFF; cm.ck = 0;
+    if (cm.grp >= ng) cm.grp = OFF;   // idle thread: no rows
+  } else {
+    const int m1 = lt / C::NCG;
+    cm.ck = (lt - m1 * C::NCG) * C::W;
+    cm.mk[0] = m1;
+    cm.mk[1] = (T - m1 != m1) ? T - m1 : OFF;
+  }
+  return cm;
+}
 
 // Supplementary Sec. II-C closed form: (t̂, η̂) ↦ (p̃, s·η̂)
 __device__ __forceinline__ void soc_case(double tt, double a, double& s_new, double& pt_new) {
@@ -73,10 +106,10 @@ __device__ __forceinline__ void soc_case(double tt, double a, double& s_new, dou
 template <int NX, int NU, typename Real>
 struct FASmem {
   struct Buf {
-    Real* lam; Real* bhat; Real* bb; RowMeta* meta; double* sold; double* pp; double* lp;
+    Real* lam; Real* bhat; Real* bb; RowMeta* meta;
   };
   Buf buf[2];
-  Real* rowpart;   // [max_rows][NWR] warp partial norms
+  Real* rowpart;   // [max_rows][NWR_MAX] warp partial norms
   Real* snew;      // [max_rows]
   double* red;     // block reductions
   double* vec;     // Riccati sweep vector
@@ -88,15 +121,18 @@ struct FASmem {
     b += align16((size_t)(chunk + 4) * sizeof(Real));            // bhat
     b += align16((size_t)(chunk / NX * NU + 8) * sizeof(Real));  // b
     b += align16((size_t)max_rows * sizeof(RowMeta));            // meta
-    b += 3 * align16((size_t)(max_rows + 4) * sizeof(double));   // s_old, p, λ_p
     return b;
   }
   NRTO_HD static size_t bytes(int chunk, int max_rows) {
     size_t b = 2 * buf_bytes(chunk, max_rows);
-    b += align16((size_t)max_rows * FACfg<NX, NU, Real>::NWR * sizeof(Real));
+    b += align16((size_t)max_rows * FACfg<NX, NU, Real>::NWR_MAX * sizeof(Real));
     b += align16((size_t)max_rows * sizeof(Real));
     b += (4 * FACfg<NX, NU, Real>::NW + 4 * 16) * sizeof(double);
     return b;
+  }
+  // Row groups whose Z' partials fit in the (then idle) chunk buffers for horizon T.
+  NRTO_HD static int zcap(int chunk, int max_rows, int T) {
+    return (int)(2 * buf_bytes(chunk, max_rows) / sizeof(Real) / ((size_t)T * NU * NX));
   }
   __device__ void carve(char* base, int chunk, int max_rows) {
     char* c = base;
@@ -106,35 +142,26 @@ struct FASmem {
       buf[k].bhat = reinterpret_cast<Real*>(take((size_t)(chunk + 4) * sizeof(Real)));
       buf[k].bb = reinterpret_cast<Real*>(take((size_t)(chunk / NX * NU + 8) * sizeof(Real)));
       buf[k].meta = reinterpret_cast<RowMeta*>(take((size_t)max_rows * sizeof(RowMeta)));
-      buf[k].sold = reinterpret_cast<double*>(take((size_t)(max_rows + 4) * sizeof(double)));
-      buf[k].pp = reinterpret_cast<double*>(take((size_t)(max_rows + 4) * sizeof(double)));
-      buf[k].lp = reinterpret_cast<double*>(take((size_t)(max_rows + 4) * sizeof(double)));
     }
-    rowpart = reinterpret_cast<Real*>(take((size_t)max_rows * FACfg<NX, NU, Real>::NWR * sizeof(Real)));
+    rowpart = reinterpret_cast<Real*>(take((size_t)max_rows * FACfg<NX, NU, Real>::NWR_MAX * sizeof(Real)));
     snew = reinterpret_cast<Real*>(take((size_t)max_rows * sizeof(Real)));
     red = reinterpret_cast<double*>(c);
     vec = red + 4 * FACfg<NX, NU, Real>::NW;
   }
 };
 
-// Issue the bulk copies of one chunk into a buffer (one thread).  Per-row doubles (s, p, λ_p) are
-// fetched from an even row index so that both ends stay 16-byte aligned; the kernel shifts by R0 & 1.
+// Issue the bulk copies of one chunk into a buffer (one thread): the entry ranges of λ and b̂,
+// the b range, and the chunk's row metadata (state rows in storage order, logical index in .pad).
 template <int NX, int NU, typename Real>
 __device__ void issue_chunk(const Dev<Real>& D, const LinSlot<Real>& S, const Inst& I, const ChunkInfo& ck,
-                            typename FASmem<NX, NU, Real>::Buf& bf, uint64_t* bar) {
-  const long long R0 = I.row0 + ck.r0, R1 = I.row0 + ck.r1;
-  const long long Ra = R0 & ~1LL;
-  const long long nd = ((R1 - Ra) + 1) & ~1LL;
+                            const typename FASmem<NX, NU, Real>::Buf& bf, uint64_t* bar) {
   const uint32_t bl = (uint32_t)(ck.ne * sizeof(Real)), bbb = (uint32_t)(ck.nb * sizeof(Real));
-  const uint32_t bm = (uint32_t)((ck.r1 - ck.r0) * sizeof(RowMeta)), bd = (uint32_t)(nd * sizeof(double));
-  mbar_arrive_expect_tx(bar, 2 * bl + bbb + bm + 3 * bd);
+  const uint32_t bm = (uint32_t)((ck.r1 - ck.r0) * sizeof(RowMeta));
+  mbar_arrive_expect_tx(bar, 2 * bl + bbb + bm);
   bulk_g2s(bf.lam, D.lam + ck.e0, bl, bar);
   bulk_g2s(bf.bhat, S.bhat + ck.e0, bl, bar);
   bulk_g2s(bf.bb, S.bvec + ck.b0, bbb, bar);
-  bulk_g2s(bf.meta, D.rmeta + R0, bm, bar);
-  bulk_g2s(bf.sold, D.s + Ra, bd, bar);
-  bulk_g2s(bf.pp, D.p + Ra, bd, bar);
-  bulk_g2s(bf.lp, D.lamp + Ra, bd, bar);
+  bulk_g2s(bf.meta, D.rmeta + I.row0 + ck.r0, bm, bar);
 }
 
 // Per-step gain solve, parallel over (m, u, c) in four phases through arena scratch:
@@ -436,7 +463,7 @@ __device__ __noinline__ bool riccati_sweep_staged(double* ar, const Arena& L, co
 
 // Load the gain-table registers of this thread's column groups from an arena Gtᵀ table ((T+1)×NU×NX).
 template <int NX, int NU, typename Real, int PAIRS, int W>
-__device__ __forceinline__ void load_gt_regs(const double* gt, int T, const int (&mk)[PAIRS], const int (&ck)[PAIRS],
+__device__ __forceinline__ void load_gt_regs(const double* gt, int T, const int (&mk)[PAIRS], int ck,
                                              Real (&g)[PAIRS][NU][W]) {
 #pragma unroll
   for (int k = 0; k < PAIRS; ++k)
@@ -444,7 +471,7 @@ __device__ __forceinline__ void load_gt_regs(const double* gt, int T, const int 
     for (int u = 0; u < NU; ++u)
 #pragma unroll
       for (int w = 0; w < W; ++w)
-        g[k][u][w] = (mk[k] < T) ? (Real)gt[(long long)mk[k] * NU * NX + u * NX + ck[k] + w] : (Real)0;
+        g[k][u][w] = (mk[k] < T) ? (Real)gt[(long long)mk[k] * NU * NX + u * NX + ck + w] : (Real)0;
 }
 
 // Vector loads/stores of W consecutive shared-memory values (8- or 16-byte aligned by the layout:
@@ -494,11 +521,194 @@ struct PhaseTimer {
   }
 };
 
+// Row pass of one FullADMM iteration over the state rows: chunks arrive by bulk copies (double
+// buffered); sub-pass 1 applies the λ_ν update of the previous iteration and forms the row norms of
+// η̂ = Â_j k + b̂_j + λ_ν,j, the projection gives each row's scale s_j and p̃_j, and sub-pass 2
+// accumulates Z'_m = Σ_j b_{j,m} w_{j,m}ᵀ.  Pointers are hoisted into registers and the chunk
+// buffer descriptors copied per chunk, so the loops touch only registers and shared memory besides
+// the row data.  Returns false if a chunk copy timed out.
+template <int NX, int NU, typename Real>
+__device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Real>& S, const Inst& I,
+                                         FASmem<NX, NU, Real>& sm, uint64_t* bars, uint32_t* phase, int* s_flag,
+                                         const ColMap cm, const double* gtc, const double* gto, double* Zp,
+                                         bool first, bool block1, Real lscale, Real* arp_out, Real* ard_out,
+                                         unsigned long long* wait_cycles) {
+  using C = FACfg<NX, NU, Real>;
+  constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR_MAX = C::NWR_MAX, W = C::W;
+  const int T = I.T, tid = threadIdx.x, lane = tid & 31;
+  const int grp = cm.grp, NG = cm.ng, NWR = cm.nwr, ck = cm.ck;
+  const int gwarp = (tid - (grp < NG ? grp : 0) * NWR * 32) >> 5;
+  const int mk[PAIRS] = {cm.mk[0], cm.mk[1]};
+  const long long row0 = I.row0;
+  const ChunkInfo* chunks = D.chunks + I.cb0;
+  Real* const lam = D.lam;
+  Real* const sr = D.sr;
+  double* const sarr = D.s;
+  const double* const parr = D.p;
+  const double* const lamparr = D.lamp;
+  double* const ptnarr = D.ptn;
+  Real* const rowpart = sm.rowpart;
+  Real* const snew_s = sm.snew;
+  Real gc[PAIRS][NU][W], go[PAIRS][NU][W], z[PAIRS][NU][W];
+  load_gt_regs<NX, NU, Real, PAIRS, W>(gtc, T, mk, ck, gc);
+  load_gt_regs<NX, NU, Real, PAIRS, W>(gto, T, mk, ck, go);
+#pragma unroll
+  for (int k = 0; k < PAIRS; ++k)
+#pragma unroll
+    for (int u = 0; u < NU; ++u)
+#pragma unroll
+      for (int w = 0; w < W; ++w) z[k][u][w] = (Real)0;
+  Real arp = 0, ard = 0;
+  // ---------------- row pass over state rows, chunk by chunk (bulk copies, double buffered) --------
+  __syncthreads();
+  if (tid == 0) {
+    fence_proxy_async();
+    for (int c0 = 0; c0 < 2 && c0 < I.n_chunks; ++c0) issue_chunk<NX, NU, Real>(D, S, I, chunks[c0], sm.buf[c0], &bars[c0]);
+  }
+  for (int ch = 0; ch < I.n_chunks; ++ch) {
+    const int bi = ch & 1;
+    const typename FASmem<NX, NU, Real>::Buf bf = sm.buf[bi];
+    const ChunkInfo cki = chunks[ch];
+    const int nr = cki.r1 - cki.r0;
+    if (tid == 0) {
+      const long long tw = clock64();
+      *s_flag = mbar_wait_bounded(&bars[bi], phase[bi]) ? 1 : 0;
+      if (wait_cycles) *wait_cycles += (unsigned long long)(clock64() - tw);
+    }
+    __syncthreads();
+    phase[bi] ^= 1u;
+    if (*s_flag == 0) return false;
+    // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms (row group `grp`
+    // takes rows grp, grp+NG, ...)
+    for (int q = grp; q < nr; q += NG) {
+      const RowMeta rm = bf.meta[q];
+      const Real so = sr[row0 + rm.pad];
+      Real pn = 0;
+      bool act = false;
+#pragma unroll
+      for (int k = 0; k < PAIRS; ++k) {
+        if (mk[k] <= rm.t) {
+          act = true;
+          const int e = rm.off + mk[k] * NX + ck;
+          Real bv[NU], yb[W], l[W];
+          ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
+          ld_vec<W, Real>(bf.bhat + e, yb);
+          ld_vec<W, Real>(bf.lam + e, l);
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            Real y = yb[w];
+#pragma unroll
+            for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
+            if (!first) {
+              Real yo = yb[w];
+#pragma unroll
+              for (int u = 0; u < NU; ++u) yo += go[k][u][w] * bv[u];
+              const Real nu = so * (yo + l[w]);
+              const Real ln = l[w] + y - nu;
+              arp += (y - nu) * (y - nu);
+              ard += (y - yo) * (y - yo);
+              l[w] = ln * lscale;
+            }
+            const Real et = y + l[w];
+            pn += et * et;
+          }
+          if (!first) {
+            st_vec<W, Real>(bf.lam + e, l);
+            st_vec<W, Real>(lam + cki.e0 + e, l);
+          }
+        }
+      }
+      if (block1) {
+        if (__any_sync(0xffffffffu, act)) pn = warp_sum(pn);
+        if (lane == 0) rowpart[q * NWR_MAX + gwarp] = pn;
+      }
+    }
+    __syncthreads();
+    if (block1) {
+      // SOC projection per row (Supplementary Sec. II-C) with t̂ = p + λ_p
+      for (int q = tid; q < nr; q += NT) {
+        Real a2 = 0;
+        for (int w = 0; w < NWR; ++w) a2 += rowpart[q * NWR_MAX + w];
+        const long long R = row0 + bf.meta[q].pad;
+        double snew, ptn;
+        soc_case(parr[R] + lamparr[R], sqrt((double)a2), snew, ptn);
+        snew_s[q] = (Real)snew;
+        sarr[R] = snew;
+        sr[R] = (Real)snew;
+        ptnarr[R] = ptn;
+      }
+      __syncthreads();
+      // sub-pass 2: Z'_m[:, c] += b_{j,m} w_{j,m}[c], w = ν - b̂ - λ = s(y + λ) - b̂ - λ
+      for (int q = grp; q < nr; q += NG) {
+        const RowMeta rm = bf.meta[q];
+        const Real sn = snew_s[q];
+#pragma unroll
+        for (int k = 0; k < PAIRS; ++k) {
+          if (mk[k] < rm.t) {
+            const int e = rm.off + mk[k] * NX + ck;
+            Real bv[NU], yb[W], l[W];
+            ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
+            ld_vec<W, Real>(bf.bhat + e, yb);
+            ld_vec<W, Real>(bf.lam + e, l);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+              Real y = yb[w];
+#pragma unroll
+              for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
+              const Real wv = sn * (y + l[w]) - yb[w] - l[w];
+#pragma unroll
+              for (int u = 0; u < NU; ++u) z[k][u][w] += bv[u] * wv;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && ch + 2 < I.n_chunks) {
+      fence_proxy_async();
+      issue_chunk<NX, NU, Real>(D, S, I, chunks[ch + 2], bf, &bars[bi]);
+    }
+  }
+  if (block1) {
+    // Z' = Σ over row groups (fixed order) of the register accumulators; the idle chunk buffers
+    // hold the per-group partials when there is more than one group.
+    if (NG == 1) {
+#pragma unroll
+      for (int k = 0; k < PAIRS; ++k)
+        if (mk[k] < T)
+#pragma unroll
+          for (int u = 0; u < NU; ++u)
+#pragma unroll
+            for (int w = 0; w < W; ++w) Zp[(long long)mk[k] * NU * NX + u * NX + ck + w] = (double)z[k][u][w];
+    } else {
+      Real* part = sm.buf[0].lam;   // NG × T × NU × NX values (NG is capped so that they fit)
+      const int nz = T * NU * NX;
+#pragma unroll
+      for (int k = 0; k < PAIRS; ++k)
+        if (mk[k] < T)
+#pragma unroll
+          for (int u = 0; u < NU; ++u)
+#pragma unroll
+            for (int w = 0; w < W; ++w) part[grp * nz + mk[k] * NU * NX + u * NX + ck + w] = z[k][u][w];
+      __syncthreads();
+      for (int q = tid; q < nz; q += NT) {
+        Real acc = 0;
+        for (int g2 = 0; g2 < NG; ++g2) acc += part[g2 * nz + q];
+        Zp[q] = (double)acc;
+      }
+    }
+  }
+  __syncthreads();
+  *arp_out = arp;
+  *ard_out = ard;
+  return true;
+}
+
 template <int NX, int NU, typename Real>
 __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int inst, FASmem<NX, NU, Real>& sm,
                                   uint64_t* bars, uint32_t* phase, int* s_flag, double* ric_scr) {
   using C = FACfg<NX, NU, Real>;
-  constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR = C::NWR, W = C::W, NCG = C::NCG, NG = C::NG, TPG = C::TPG;
+  constexpr int NT = C::NT;
   const Inst I = D.inst[inst];
   const Arena L = arena_layout(NX, NU, I.T, I.n_obs, I.n_link);
   const SlotL SL = slot_layout(NX, NU, I.T);
@@ -507,7 +717,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   const LinSlot<Real> S = D.slot[sl];
   const double* sa = S.arena + I.slot0;
   const int T = I.T;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
   double rho = sp.rho;        // penalty of the current iteration (residual balancing may change it)
   double rho_done = rho;      // penalty of the last iteration whose residuals were checked
   double rp_mark = 0.0;       // r_p at the previous stall checkpoint
@@ -519,11 +729,8 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   PhaseTimer tm;
   tm.start(D.phase_cycles != nullptr);
 
-  // this thread's row group and its column groups (block m, components c .. c+W-1)
-  const int grp = tid / TPG, lt = tid - grp * TPG, gwarp = lt >> 5;
-  int mk[PAIRS], ck[PAIRS];
-#pragma unroll
-  for (int k = 0; k < PAIRS; ++k) { const int P = lt + k * TPG; mk[k] = P / NCG; ck[k] = (P - mk[k] * NCG) * W; }
+  // this thread's row group and its two column groups (blocks m and T - m, components ck .. ck+W-1)
+  const ColMap cm = col_map<NX, NU, Real>(I.T, FASmem<NX, NU, Real>::zcap(sp.chunk, sp.max_rows, I.T));
 
   // ---- initialization (Algorithm 1): λ_p, λ_ν, k, p <- 0 (or a warm start of k, p̃, λ_p) ----
   for (long long e = tid; e < I.n_ent; e += NT) lam[I.ent0 + e] = (Real)0;
@@ -531,7 +738,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     const long long R = I.row0 + r;
     if (!sp.warm) { D.p[R] = 0.0; D.pt[R] = 0.0; D.lamp[R] = 0.0; }
     else { D.p[R] = D.pt[R]; }
-    D.w[R] = 0.0; D.lamw[R] = 0.0; D.s[R] = 1.0; D.ell[R] = 0.0;
+    D.w[R] = 0.0; D.lamw[R] = 0.0; D.s[R] = 1.0; D.sr[R] = (Real)1; D.ell[R] = 0.0;
   }
   for (int q = tid; q < T * NU; q += NT) ar[L.du + q] = 0.0;
   for (int q = tid; q < (T + 1) * NX; q += NT) { ar[L.dx + q] = 0.0; ar[L.e + q] = 0.0; ar[L.lam_e + q] = 0.0; }
@@ -561,15 +768,6 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     const bool block1 = (b <= Lmax);
     const double* gtc_arena = ar + (gsel ? L.Gt1 : L.Gt0);
     const double* gto_arena = ar + (gsel ? L.Gt0 : L.Gt1);
-    Real gc[PAIRS][NU][W], go[PAIRS][NU][W], z[PAIRS][NU][W];
-    load_gt_regs<NX, NU, Real, PAIRS, W>(gtc_arena, T, mk, ck, gc);
-    load_gt_regs<NX, NU, Real, PAIRS, W>(gto_arena, T, mk, ck, go);
-#pragma unroll
-    for (int k = 0; k < PAIRS; ++k)
-#pragma unroll
-      for (int u = 0; u < NU; ++u)
-#pragma unroll
-        for (int w = 0; w < W; ++w) z[k][u][w] = (Real)0;
     Real arp = 0, ard = 0;
     const double rho_prev = rho;   // penalty of iteration b-1
     Real lscale = (Real)1;         // rescale of the scaled dual λ_ν^{b-1} when ρ changes for iteration b
@@ -595,145 +793,11 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
       }
     }
 
-    // ---------------- row pass over state rows, chunk by chunk (bulk copies, double buffered) --------
-    __syncthreads();
-    if (tid == 0) {
-      fence_proxy_async();
-      for (int c0 = 0; c0 < 2 && c0 < I.n_chunks; ++c0) issue_chunk<NX, NU, Real>(D, S, I, chunks[c0], sm.buf[c0], &bars[c0]);
-    }
-    for (int ch = 0; ch < I.n_chunks; ++ch) {
-      const int bi = ch & 1;
-      typename FASmem<NX, NU, Real>::Buf& bf = sm.buf[bi];
-      const ChunkInfo cki = chunks[ch];
-      const int nr = cki.r1 - cki.r0;
-      const int soff = (int)((I.row0 + cki.r0) & 1LL);
-      if (tid == 0) {
-        const long long tw = clock64();
-        *s_flag = mbar_wait_bounded(&bars[bi], phase[bi]) ? 1 : 0;
-        if (tm.on) tm.acc[PH_WAIT] += (unsigned long long)(clock64() - tw);   // part of PH_ROWS, also counted here
-      }
-      __syncthreads();
-      phase[bi] ^= 1u;
-      if (*s_flag == 0) { status = ST_TIMEOUT; goto done; }
-      // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms (row group `grp`
-      // takes rows grp, grp+NG, ...)
-      for (int q = grp; q < nr; q += NG) {
-        const RowMeta rm = bf.meta[q];
-        const Real so = (Real)bf.sold[soff + q];
-        Real pn = 0;
-        bool act = false;
-#pragma unroll
-        for (int k = 0; k < PAIRS; ++k) {
-          if (mk[k] <= rm.t) {
-            act = true;
-            const int e = rm.off + mk[k] * NX + ck[k];
-            Real bv[NU], yb[W], l[W];
-            ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
-            ld_vec<W, Real>(bf.bhat + e, yb);
-            ld_vec<W, Real>(bf.lam + e, l);
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-              Real y = yb[w];
-#pragma unroll
-              for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
-              if (!first) {
-                Real yo = yb[w];
-#pragma unroll
-                for (int u = 0; u < NU; ++u) yo += go[k][u][w] * bv[u];
-                const Real nu = so * (yo + l[w]);
-                const Real ln = l[w] + y - nu;
-                arp += (y - nu) * (y - nu);
-                ard += (y - yo) * (y - yo);
-                l[w] = ln * lscale;
-              }
-              const Real et = y + l[w];
-              pn += et * et;
-            }
-            if (!first) {
-              st_vec<W, Real>(bf.lam + e, l);
-              st_vec<W, Real>(lam + cki.e0 + e, l);
-            }
-          }
-        }
-        if (block1 && gwarp < NWR) {
-          if (__any_sync(0xffffffffu, act)) pn = warp_sum(pn);
-          if (lane == 0) sm.rowpart[q * NWR + gwarp] = pn;
-        }
-      }
-      __syncthreads();
-      if (block1) {
-        // SOC projection per row (Supplementary Sec. II-C) with t̂ = p + λ_p
-        for (int q = tid; q < nr; q += NT) {
-          Real a2 = 0;
-          for (int w = 0; w < NWR; ++w) a2 += sm.rowpart[q * NWR + w];
-          double snew, ptn;
-          soc_case(bf.pp[soff + q] + bf.lp[soff + q], sqrt((double)a2), snew, ptn);
-          sm.snew[q] = (Real)snew;
-          const long long R = I.row0 + cki.r0 + q;
-          D.s[R] = snew;
-          D.ptn[R] = ptn;
-        }
-        __syncthreads();
-        // sub-pass 2: Z'_m[:, c] += b_{j,m} w_{j,m}[c], w = ν - b̂ - λ = s(y + λ) - b̂ - λ
-        for (int q = grp; q < nr; q += NG) {
-          const RowMeta rm = bf.meta[q];
-          const Real sn = sm.snew[q];
-#pragma unroll
-          for (int k = 0; k < PAIRS; ++k) {
-            if (mk[k] < rm.t) {
-              const int e = rm.off + mk[k] * NX + ck[k];
-              Real bv[NU], yb[W], l[W];
-              ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
-              ld_vec<W, Real>(bf.bhat + e, yb);
-              ld_vec<W, Real>(bf.lam + e, l);
-#pragma unroll
-              for (int w = 0; w < W; ++w) {
-                Real y = yb[w];
-#pragma unroll
-                for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
-                const Real wv = sn * (y + l[w]) - yb[w] - l[w];
-#pragma unroll
-                for (int u = 0; u < NU; ++u) z[k][u][w] += bv[u] * wv;
-              }
-            }
-          }
-        }
-      }
-      __syncthreads();
-      if (tid == 0 && ch + 2 < I.n_chunks) {
-        fence_proxy_async();
-        issue_chunk<NX, NU, Real>(D, S, I, chunks[ch + 2], bf, &bars[bi]);
-      }
-    }
-    if (block1) {
-      // Z' = Σ over row groups (fixed order) of the register accumulators; the idle chunk buffers
-      // hold the per-group partials when there is more than one group.
-      if constexpr (NG == 1) {
-#pragma unroll
-        for (int k = 0; k < PAIRS; ++k)
-          if (mk[k] < T)
-#pragma unroll
-            for (int u = 0; u < NU; ++u)
-#pragma unroll
-              for (int w = 0; w < W; ++w) ar[L.Zp + (long long)mk[k] * NU * NX + u * NX + ck[k] + w] = (double)z[k][u][w];
-      } else {
-        Real* part = sm.buf[0].lam;   // NG × T × NU × NX values (checked against the buffer size on the host)
-        const int nz = T * NU * NX;
-#pragma unroll
-        for (int k = 0; k < PAIRS; ++k)
-          if (mk[k] < T)
-#pragma unroll
-            for (int u = 0; u < NU; ++u)
-#pragma unroll
-              for (int w = 0; w < W; ++w) part[grp * nz + mk[k] * NU * NX + u * NX + ck[k] + w] = z[k][u][w];
-        __syncthreads();
-        for (int q = tid; q < nz; q += NT) {
-          Real acc = 0;
-#pragma unroll
-          for (int g2 = 0; g2 < NG; ++g2) acc += part[g2 * nz + q];
-          ar[L.Zp + q] = (double)acc;
-        }
-      }
+    // ---------------- row pass over state rows (bulk copies, double buffered) ----------------
+    if (!fa_row_pass<NX, NU, Real>(D, S, I, sm, bars, phase, s_flag, cm, gtc_arena, gto_arena, ar + L.Zp, first, block1,
+                                   lscale, &arp, &ard, tm.on ? &tm.acc[PH_WAIT] : nullptr)) {
+      status = ST_TIMEOUT;
+      goto done;
     }
     __syncthreads();
     tm.mark(PH_ROWS);
