@@ -94,11 +94,17 @@ __device__ __forceinline__ ColMap col_map(int T, int zcap) {
   return cm;
 }
 
-// Supplementary Sec. II-C closed form: (t̂, η̂) ↦ (p̃, s·η̂)
+// Supplementary Sec. II-C closed form: (t̂, η̂) ↦ (p̃, s·η̂), a = ‖η̂‖
 __device__ __forceinline__ void soc_case(double tt, double a, double& s_new, double& pt_new) {
   if (a <= tt) { s_new = 1.0; pt_new = tt; }
   else if (a <= -tt) { s_new = 0.0; pt_new = 0.0; }
   else { pt_new = 0.5 * (tt + a); s_new = pt_new / a; }
+}
+template <typename Real>
+__device__ __forceinline__ void soc_case_r(Real tt, Real a, Real& s_new, Real& pt_new) {
+  if (a <= tt) { s_new = (Real)1; pt_new = tt; }
+  else if (a <= -tt) { s_new = (Real)0; pt_new = (Real)0; }
+  else { pt_new = (Real)0.5 * (tt + a); s_new = pt_new / a; }
 }
 
 // Shared memory of one CTA: two chunk buffers plus per-chunk scratch.  Host and device use the
@@ -167,11 +173,19 @@ __device__ void issue_chunk(const Dev<Real>& D, const LinSlot<Real>& S, const In
 // Per-step gain solve, parallel over (m, u, c) in four phases through arena scratch:
 //   Y = coefA Z' Φ + coefK K̃ U;  X = (Pfᵀ Y) ⊙ Dv;  PX = Pf X;  K = PX Uᵀ;  Gtᵀ = √τ PX Φᵀ.
 // (FullADMM: coefA = ρ√τ, coefK = 0; DR: coefA = σ√τ, coefK = r_χ.)  All threads of the block.
+// Threads t0 .. t0+nthr-1 take part; they synchronize with barrier `bar_id` (0: the whole block).
+__device__ __forceinline__ void group_sync(int bar_id, int nthr) {
+  if (bar_id == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthr) : "memory");
+}
+
 template <int NX, int NU, typename Real>
 __device__ __noinline__ void gain_solve(double* ar, const Arena& L, int T, double sqrt_tau, double coefA, double coefK,
-                           double* Kout, double* gt_out) {
+                           double* Kout, double* gt_out, int t0 = 0, int nthr = 0, int bar_id = 0) {
   const int n = T * NU * NX;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+  if (nthr == 0) nthr = blockDim.x;
+  const int me = threadIdx.x - t0;
+  for (int q = me; q < n; q += nthr) {
     const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
     const double* Zp = ar + L.Zp + (long long)m * NU * NX + u * NX;
     const double* Phi = ar + L.Phi + (long long)m * NX * NX;
@@ -189,8 +203,8 @@ __device__ __noinline__ void gain_solve(double* ar, const Arena& L, int T, doubl
     }
     ar[L.Ws1 + q] = (double)acc;
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+  group_sync(bar_id, nthr);
+  for (int q = me; q < n; q += nthr) {
     const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
     const double* Pf = ar + L.Pf + (long long)m * NU * NU;
     const double* Y = ar + L.Ws1 + (long long)m * NU * NX;
@@ -199,8 +213,8 @@ __device__ __noinline__ void gain_solve(double* ar, const Arena& L, int T, doubl
     for (int v = 0; v < NU; ++v) acc += (Real)Pf[v * NU + u] * (Real)Y[v * NX + c];
     ar[L.Ws2 + q] = (double)(acc * (Real)ar[L.Dv + q]);
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+  group_sync(bar_id, nthr);
+  for (int q = me; q < n; q += nthr) {
     const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
     const double* Pf = ar + L.Pf + (long long)m * NU * NU;
     const double* X = ar + L.Ws2 + (long long)m * NU * NX;
@@ -209,8 +223,8 @@ __device__ __noinline__ void gain_solve(double* ar, const Arena& L, int T, doubl
     for (int v = 0; v < NU; ++v) acc += (Real)Pf[u * NU + v] * (Real)X[v * NX + c];
     ar[L.Ws1 + q] = (double)acc;
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+  group_sync(bar_id, nthr);
+  for (int q = me; q < n; q += nthr) {
     const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
     const double* PX = ar + L.Ws1 + (long long)m * NU * NX + u * NX;
     const double* U = ar + L.SigU + (long long)m * NX * NX + c * NX;
@@ -225,8 +239,8 @@ __device__ __noinline__ void gain_solve(double* ar, const Arena& L, int T, doubl
     Kout[q] = (double)k;
     gt_out[q] = (double)(g * (Real)sqrt_tau);
   }
-  for (int q = threadIdx.x; q < NU * NX; q += blockDim.x) gt_out[(long long)T * NU * NX + q] = 0.0;
-  __syncthreads();
+  for (int q = me; q < NU * NX; q += nthr) gt_out[(long long)T * NU * NX + q] = 0.0;
+  group_sync(bar_id, nthr);
 }
 
 // Block-2 (δû) LQ sweep with fixed factors (warp 0 only).  Linear terms q_t (t = 0..T, index t
@@ -360,7 +374,8 @@ __device__ __noinline__ void riccati_sweep(double* ar, const Arena& L, const dou
 // factors do not fit; the caller then uses riccati_sweep.
 template <int NX, int NU, typename Real>
 __device__ __noinline__ bool riccati_sweep_staged(double* ar, const Arena& L, const double* sa, const SlotL& SL, int T,
-                                     Real* st, size_t cap, double* pv) {
+                                     Real* st, size_t cap, double* pv, const double* gain_args = nullptr,
+                                     double* Kout = nullptr, double* gt_out = nullptr) {
   constexpr int BW = NU * NU + 2 * NU * NX + NX * NX + NX + NU;   // N, M, L, Acl, q, r per step
   constexpr int FW = NU * NX + NX * NX + NX * NU;                 // L, A, B per step
   if ((size_t)T * (BW > FW ? BW : FW) > cap) return false;
@@ -378,6 +393,11 @@ __device__ __noinline__ bool riccati_sweep_staged(double* ar, const Arena& L, co
     st[q] = (Real)v;
   }
   __syncthreads();
+  if (tid >= 32 && gain_args) {
+    // the gain solve (independent of block 2) on the other warps meanwhile
+    gain_solve<NX, NU, Real>(ar, L, T, gain_args[0], gain_args[1], gain_args[2], Kout, gt_out, 32,
+                             (int)blockDim.x - 32, 1);
+  }
   if (tid < 32) {
     if (lane < NX) pv[lane] = ar[L.qv + (long long)T * NX + lane];
     __syncwarp();
@@ -590,7 +610,7 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
         if (mk[k] <= rm.t) {
           act = true;
           const int e = rm.off + mk[k] * NX + ck;
-          Real bv[NU], yb[W], l[W];
+          Real bv[NU], yb[W], l[W], lg[W];
           ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
           ld_vec<W, Real>(bf.bhat + e, yb);
           ld_vec<W, Real>(bf.lam + e, l);
@@ -611,10 +631,14 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
             }
             const Real et = y + l[w];
             pn += et * et;
+            lg[w] = l[w];
+            yb[w] += l[w];     // b̂ + λ, kept for sub-pass 2
+            l[w] = et;         // η̂, kept for sub-pass 2
           }
-          if (!first) {
+          if (!first) st_vec<W, Real>(lam + cki.e0 + e, lg);
+          if (block1) {
             st_vec<W, Real>(bf.lam + e, l);
-            st_vec<W, Real>(lam + cki.e0 + e, l);
+            st_vec<W, Real>(bf.bhat + e, yb);
           }
         }
       }
@@ -630,15 +654,16 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
         Real a2 = 0;
         for (int w = 0; w < NWR; ++w) a2 += rowpart[q * NWR_MAX + w];
         const long long R = row0 + bf.meta[q].pad;
-        double snew, ptn;
-        soc_case(parr[R] + lamparr[R], sqrt((double)a2), snew, ptn);
-        snew_s[q] = (Real)snew;
-        sarr[R] = snew;
-        sr[R] = (Real)snew;
-        ptnarr[R] = ptn;
+        Real snew, ptn;   // in the compute precision (FP32 cones in mixed mode)
+        soc_case_r<Real>((Real)(parr[R] + lamparr[R]), sqrt(a2), snew, ptn);
+        snew_s[q] = snew;
+        sarr[R] = (double)snew;
+        sr[R] = snew;
+        ptnarr[R] = (double)ptn;
       }
       __syncthreads();
-      // sub-pass 2: Z'_m[:, c] += b_{j,m} w_{j,m}[c], w = ν - b̂ - λ = s(y + λ) - b̂ - λ
+      // sub-pass 2: Z'_m[:, c] += b_{j,m} w_{j,m}[c], w = ν - b̂ - λ = s η̂ - (b̂ + λ), from the η̂ and
+      // b̂ + λ that sub-pass 1 left in the chunk buffer (λ_ν itself was stored to global memory)
       for (int q = grp; q < nr; q += NG) {
         const RowMeta rm = bf.meta[q];
         const Real sn = snew_s[q];
@@ -646,16 +671,13 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
         for (int k = 0; k < PAIRS; ++k) {
           if (mk[k] < rm.t) {
             const int e = rm.off + mk[k] * NX + ck;
-            Real bv[NU], yb[W], l[W];
+            Real bv[NU], bl[W], et[W];
             ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
-            ld_vec<W, Real>(bf.bhat + e, yb);
-            ld_vec<W, Real>(bf.lam + e, l);
+            ld_vec<W, Real>(bf.bhat + e, bl);   // b̂ + λ
+            ld_vec<W, Real>(bf.lam + e, et);    // η̂ = y + λ
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-              Real y = yb[w];
-#pragma unroll
-              for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
-              const Real wv = sn * (y + l[w]) - yb[w] - l[w];
+              const Real wv = sn * et[w] - bl[w];
 #pragma unroll
               for (int u = 0; u < NU; ++u) z[k][u][w] += bv[u] * wv;
             }
@@ -909,17 +931,21 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     __syncthreads();
     tm.mark(PH_QR);
     // ---------------- (c) gain update: K^b from Z'; Gtᵀ^b replaces the previous table ----------------
-    gain_solve<NX, NU, Real>(ar, L, T, I.sqrt_tau, rho * I.sqrt_tau, 0.0, ar + L.K1, ar + (gsel ? L.Gt0 : L.Gt1));
-    gsel ^= 1;
-    tm.mark(PH_GAIN);
-    // ---------------- (b) Block 2: Riccati sweep (factors staged in the idle chunk buffers) ----------------
+    // ---------------- (c) gain update and (b) Block 2, which are independent: the Riccati sweep runs
+    // on warp 0 from factors staged in the idle chunk buffers while the other warps solve for K^b
+    // (its Gtᵀ^b replaces the previous table) ----------------
     {
+      const double gargs[3] = {I.sqrt_tau, rho * I.sqrt_tau, 0.0};
+      double* gt_new = ar + (gsel ? L.Gt0 : L.Gt1);
       // The two chunk buffers are contiguous in the carve; their total size bounds the staging area.
       const size_t cap = 2 * FASmem<NX, NU, Real>::buf_bytes(sp.chunk, sp.max_rows) / sizeof(Real);
-      if (!riccati_sweep_staged<NX, NU, Real>(ar, L, sa, SL, T, sm.buf[0].lam, cap, sm.vec)) {
+      if (!riccati_sweep_staged<NX, NU, Real>(ar, L, sa, SL, T, sm.buf[0].lam, cap, sm.vec, gargs, ar + L.K1, gt_new)) {
+        gain_solve<NX, NU, Real>(ar, L, T, gargs[0], gargs[1], gargs[2], ar + L.K1, gt_new);
+        tm.mark(PH_GAIN);
         if (warp == 0) riccati_sweep<NX, NU, Real>(ar, L, sa, SL, T, sm.vec);
         __syncthreads();
       }
+      gsel ^= 1;
     }
     tm.mark(PH_RICCATI);
     // ---------------- (d) p, scalar duals, scalar residual parts of iteration b ----------------
