@@ -461,6 +461,18 @@ void choose_chunk(KindLaunch& kl) {
   kl.max_rows = chunk / (2 * nx) + 2;
   kl.smem = smem_for<Real>(kl.kind, chunk, kl.max_rows);
   if (kl.smem > (size_t)smem_budget<Real>()) fail(NRTO_ERR_INVALID, "horizon too long for the shared-memory budget of this precision");
+  // the block-2 sweep keeps q, r, l and a ring of >= 2 factor records in the chunk buffers
+  const int nu = kind_nu(kl.kind);
+  size_t bb = 0;
+  if (kl.kind == KIND_UNICYCLE) bb = FASmem<3, 2, Real>::buf_bytes(chunk, kl.max_rows);
+  else if (kl.kind == KIND_QUADCOPTER) bb = FASmem<12, 4, Real>::buf_bytes(chunk, kl.max_rows);
+  else bb = FASmem<14, 7, Real>::buf_bytes(chunk, kl.max_rows);
+  size_t fixed = 0;
+  if (kl.kind == KIND_UNICYCLE) fixed = B2Smem<3, 2, Real>::fixed_bytes(kl.tmax);
+  else if (kl.kind == KIND_QUADCOPTER) fixed = B2Smem<12, 4, Real>::fixed_bytes(kl.tmax);
+  else fixed = B2Smem<14, 7, Real>::fixed_bytes(kl.tmax);
+  const size_t need = fixed + 2 * (size_t)pk_stride(nx, nu) * sizeof(Real);
+  if (need > 2 * bb) fail(NRTO_ERR_INVALID, "internal: chunk buffers too small for the block-2 sweep");
 }
 
 // per-instance arena/slot field copy (device → host) of cnt(I) doubles at off(I)

@@ -368,120 +368,209 @@ __device__ __noinline__ void riccati_sweep(double* ar, const Arena& L, const dou
   __syncwarp();
 }
 
-// Block-2 sweep from shared memory: all threads first copy the per-step factors of one pass into
-// `st` (the idle chunk buffers, `cap` Real values), then warp 0 runs the dependent recursion on
-// shared-memory operands.  Same arithmetic as riccati_sweep.  Returns false (nothing done) when the
-// factors do not fit; the caller then uses riccati_sweep.
+// Shared-memory areas of the block-2 sweep, cut from the chunk buffers (idle after the row pass):
+// linear terms q_t (t = 0..T) and r_k, feed-forward l_k, c_k / d_k, the costates p_t or states δx_t,
+// and a two-half ring of packed factor records (pk_stride values per step) that bulk copies fill
+// ahead of the serial recursions.
 template <int NX, int NU, typename Real>
-__device__ __noinline__ bool riccati_sweep_staged(double* ar, const Arena& L, const double* sa, const SlotL& SL, int T,
-                                     Real* st, size_t cap, double* pv, const double* gain_args = nullptr,
-                                     double* Kout = nullptr, double* gt_out = nullptr) {
-  constexpr int BW = NU * NU + 2 * NU * NX + NX * NX + NX + NU;   // N, M, L, Acl, q, r per step
-  constexpr int FW = NU * NX + NX * NX + NX * NU;                 // L, A, B per step
-  if ((size_t)T * (BW > FW ? BW : FW) > cap) return false;
-  const int tid = threadIdx.x, lane = tid & 31;
-  // ---- backward pass factors ----
-  for (int q = tid; q < T * BW; q += blockDim.x) {
-    const int k = q / BW, o = q - k * BW;
-    double v;
-    if (o < NU * NU) v = ar[L.RicN + (long long)k * NU * NU + o];
-    else if (o < NU * NU + NU * NX) v = ar[L.RicM + (long long)k * NU * NX + (o - NU * NU)];
-    else if (o < NU * NU + 2 * NU * NX) v = ar[L.RicL + (long long)k * NU * NX + (o - NU * NU - NU * NX)];
-    else if (o < NU * NU + 2 * NU * NX + NX * NX) v = ar[L.RicAcl + (long long)k * NX * NX + (o - NU * NU - 2 * NU * NX)];
-    else if (o < NU * NU + 2 * NU * NX + NX * NX + NX) v = ar[L.qv + (long long)k * NX + (o - NU * NU - 2 * NU * NX - NX * NX)];
-    else v = ar[L.rv + (long long)k * NU + (o - NU * NU - 2 * NU * NX - NX * NX - NX)];
-    st[q] = (Real)v;
+struct B2Smem {
+  Real* qs;    // (T+1)·NX
+  Real* rs;    // T·NU
+  Real* ls;    // T·NU
+  Real* cd;    // T·NX: c_k (backward), then d_k (forward)
+  Real* px;    // (T+1)·NX: p_t (backward), then δx_t (forward)
+  Real* ring;
+  int nbs;     // steps per ring half
+  __device__ void carve(char* base, size_t bytes, int T) {
+    auto a16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    char* c = base;
+    qs = reinterpret_cast<Real*>(c); c += a16((size_t)(T + 1) * NX * sizeof(Real));
+    rs = reinterpret_cast<Real*>(c); c += a16((size_t)T * NU * sizeof(Real));
+    ls = reinterpret_cast<Real*>(c); c += a16((size_t)T * NU * sizeof(Real));
+    cd = reinterpret_cast<Real*>(c); c += a16((size_t)T * NX * sizeof(Real));
+    px = reinterpret_cast<Real*>(c); c += a16((size_t)(T + 1) * NX * sizeof(Real));
+    ring = reinterpret_cast<Real*>(c);
+    const size_t used = (size_t)(c - base);
+    const size_t rec = (size_t)pk_stride(NX, NU) * sizeof(Real);
+    nbs = used < bytes ? (int)((bytes - used) / (2 * rec)) : 0;
+  }
+  NRTO_HD static size_t fixed_bytes(int T) {
+    auto a16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    return a16((size_t)(T + 1) * NX * sizeof(Real)) + 2 * a16((size_t)T * NU * sizeof(Real)) +
+           a16((size_t)T * NX * sizeof(Real)) + a16((size_t)(T + 1) * NX * sizeof(Real));
+  }
+};
+
+// Block-2 (δû) solve with the fixed factorization and the gain solve (independent of block 2).
+// Only the A_cl products are serial in k, so everything else runs in parallel passes over k:
+//   c_k = q_k + L_kᵀ r_k                                     (all threads)
+//   p_T = q_T,  p_k = c_k + A_cl,kᵀ p_{k+1}                   (warp 0; warps 1.. solve for the gains)
+//   l_k = -(N_k r_k + M_k p_{k+1}),  d_k = B_k l_k             (all threads)
+//   δx_0 = 0,  δx_{k+1} = A_cl,k δx_k + d_k                    (warp 0)
+//   δu_k = L_k δx_k + l_k                                     (all threads)
+// which is the Riccati backward/forward sweep (δx_{k+1} = A_k δx_k + B_k δu_k) reordered.  The
+// records for the serial passes stream through the ring by bulk copies (lane 0 of warp 0, mbarriers
+// `bars` with phases `phase`); the parallel passes read the records from global memory.  Returns
+// false if a copy did not arrive.
+template <int NX, int NU, typename Real>
+__device__ __noinline__ bool block2_sweep_and_gain(double* ar, const Arena& L, int T, const B2Smem<NX, NU, Real> b2,
+                                                   uint64_t* bars, uint32_t* phase, int* s_flag, Real* pv,
+                                                   const double* gargs, double* Kout, double* gt_out) {
+  constexpr int BW = pk_stride(NX, NU);
+  constexpr int oM = NU * NU, oL = oM + NU * NX, oA = oL + NU * NX, oB = oA + NX * NX;
+  const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
+  const Real* pk = reinterpret_cast<const Real*>(ar + L.RicPk);
+  const int nbs = b2.nbs;
+  const int nblk = (T + nbs - 1) / nbs;
+  (void)pv;
+  // one block of records [lo, hi] into ring half h (lane 0 of warp 0)
+  auto issue = [&](int lo, int hi, int h) {
+    const uint32_t bytes = (uint32_t)((hi - lo + 1) * BW * sizeof(Real));
+    mbar_arrive_expect_tx(&bars[h], bytes);
+    bulk_g2s(b2.ring + (size_t)h * nbs * BW, pk + (size_t)lo * BW, bytes, &bars[h]);
+  };
+  auto wait = [&](int h) {
+    int got = 1;
+    if (lane == 0) got = mbar_wait_bounded(&bars[h], phase[h]) ? 1 : 0;
+    got = __shfl_sync(0xffffffffu, got, 0);
+    phase[h] ^= 1u;
+    return got != 0;
+  };
+  auto bwd_lo = [&](int j) { const int hi = T - 1 - j * nbs; return hi - nbs + 1 > 0 ? hi - nbs + 1 : 0; };
+  if (tid == 0) {
+    // the ring reuses chunk-buffer memory last written by generic stores
+    fence_proxy_async();
+    issue(bwd_lo(0), T - 1, 0);
+    if (nblk > 1) issue(bwd_lo(1), T - 1 - nbs, 1);
+  }
+  // ---- c_k = q_k + L_kᵀ r_k ----
+  for (int q = tid; q < T * NX; q += nthr) {
+    const int k = q / NX, j = q - k * NX;
+    const Real* f = pk + (size_t)k * BW;
+    Real v = b2.qs[(size_t)k * NX + j];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) v += f[oL + u * NX + j] * b2.rs[(size_t)k * NU + u];
+    b2.cd[q] = v;
   }
   __syncthreads();
-  if (tid >= 32 && gain_args) {
-    // the gain solve (independent of block 2) on the other warps meanwhile
-    gain_solve<NX, NU, Real>(ar, L, T, gain_args[0], gain_args[1], gain_args[2], Kout, gt_out, 32,
-                             (int)blockDim.x - 32, 1);
-  }
-  if (tid < 32) {
-    if (lane < NX) pv[lane] = ar[L.qv + (long long)T * NX + lane];
-    __syncwarp();
-    for (int k = T - 1; k >= 0; --k) {
-      const Real* f = st + (long long)k * BW;
-      const Real* N = f;
-      const Real* M = N + NU * NU;
-      const Real* Lk = M + NU * NX;
-      const Real* Acl = Lk + NU * NX;
-      const Real* q = Acl + NX * NX;
-      const Real* r = q + NX;
-      Real p_in[NX];
+  bool ok = true;
+  if (tid >= 32) {
+    gain_solve<NX, NU, Real>(ar, L, T, gargs[0], gargs[1], gargs[2], Kout, gt_out, 32, nthr - 32, 1);
+  } else {
+    // ---- backward: p_k = c_k + A_cl,kᵀ p_{k+1}; lane j < NX owns p_j ----
+    Real p = (lane < NX) ? b2.qs[(size_t)T * NX + lane] : (Real)0;
+    if (lane < NX) b2.px[(size_t)T * NX + lane] = p;
+    for (int j = 0; j < nblk && ok; ++j) {
+      const int h = j & 1, hi = T - 1 - j * nbs, lo = bwd_lo(j);
+      if (!wait(h)) { ok = false; break; }
+      const Real* base = b2.ring + (size_t)h * nbs * BW;
+      for (int k = hi; k >= lo; --k) {
+        const Real* A = base + (size_t)(k - lo) * BW + oA;
+        Real pc[NX];
 #pragma unroll
-      for (int c = 0; c < NX; ++c) p_in[c] = (Real)pv[c];
-      if (lane < NU) {
-        Real lv = 0;
+        for (int c = 0; c < NX; ++c) pc[c] = __shfl_sync(0xffffffffu, p, c);
+        if (k >= 1) {
+          Real s0 = (lane < NX) ? b2.cd[(size_t)k * NX + lane] : (Real)0, s1 = 0;
+          if (lane < NX) {
 #pragma unroll
-        for (int v = 0; v < NU; ++v) lv += N[lane * NU + v] * r[v];
-#pragma unroll
-        for (int c = 0; c < NX; ++c) lv += M[lane * NX + c] * p_in[c];
-        ar[L.du + (long long)k * NU + lane] = -(double)lv;
-      }
-      Real pn = 0;
-      if (lane < NX && k >= 1) {
-        pn = q[lane];
-#pragma unroll
-        for (int c = 0; c < NX; ++c) pn += Acl[c * NX + lane] * p_in[c];
-#pragma unroll
-        for (int v = 0; v < NU; ++v) pn += Lk[v * NX + lane] * r[v];
+            for (int c = 0; c < NX; c += 2) {
+              s0 += A[c * NX + lane] * pc[c];
+              if (c + 1 < NX) s1 += A[(c + 1) * NX + lane] * pc[c + 1];
+            }
+          }
+          p = s0 + s1;
+          if (lane < NX) b2.px[(size_t)k * NX + lane] = p;
+        }
       }
       __syncwarp();
-      if (lane < NX && k >= 1) pv[lane] = (double)pn;
-      __syncwarp();
+      if (lane == 0 && j + 2 < nblk) {
+        fence_proxy_async();
+        issue(bwd_lo(j + 2), T - 1 - (j + 2) * nbs, h);
+      }
     }
+    if (lane == 0) *s_flag = ok ? 1 : 0;
   }
   __syncthreads();
-  // ---- forward pass factors ----
-  for (int q = tid; q < T * FW; q += blockDim.x) {
-    const int k = q / FW, o = q - k * FW;
-    double v;
-    if (o < NU * NX) v = ar[L.RicL + (long long)k * NU * NX + o];
-    else if (o < NU * NX + NX * NX) v = sa[SL.A + (long long)k * NX * NX + (o - NU * NX)];
-    else v = sa[SL.B + (long long)k * NX * NU + (o - NU * NX - NX * NX)];
-    st[q] = (Real)v;
+  if (*s_flag == 0) return false;
+  // forward records into the ring while l_k and d_k are formed
+  if (tid == 0) {
+    fence_proxy_async();
+    issue(0, nbs - 1 < T - 1 ? nbs - 1 : T - 1, 0);
+    if (nblk > 1) issue(nbs, 2 * nbs - 1 < T - 1 ? 2 * nbs - 1 : T - 1, 1);
+  }
+  // ---- l_k = -(N_k r_k + M_k p_{k+1}) ----
+  for (int q = tid; q < T * NU; q += nthr) {
+    const int k = q / NU, u = q - k * NU;
+    const Real* f = pk + (size_t)k * BW;
+    Real v = 0;
+#pragma unroll
+    for (int w = 0; w < NU; ++w) v += f[u * NU + w] * b2.rs[(size_t)k * NU + w];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) v += f[oM + u * NX + c] * b2.px[(size_t)(k + 1) * NX + c];
+    b2.ls[q] = -v;
+  }
+  __syncthreads();
+  // ---- d_k = B_k l_k ----
+  for (int q = tid; q < T * NX; q += nthr) {
+    const int k = q / NX, j = q - k * NX;
+    const Real* f = pk + (size_t)k * BW;
+    Real v = 0;
+#pragma unroll
+    for (int u = 0; u < NU; ++u) v += f[oB + j * NU + u] * b2.ls[(size_t)k * NU + u];
+    b2.cd[q] = v;
   }
   __syncthreads();
   if (tid < 32) {
-    double* dx = ar + L.dx;
-    double* du = ar + L.du;
-    Real xk[NX];
+    // ---- forward: δx_{k+1} = A_cl,k δx_k + d_k; lane j < NX owns δx_j ----
+    Real x = 0;
+    if (lane < NX) b2.px[lane] = (Real)0;
+    for (int j = 0; j < nblk && ok; ++j) {
+      const int h = j & 1, lo = j * nbs, hi = lo + nbs - 1 < T - 1 ? lo + nbs - 1 : T - 1;
+      if (!wait(h)) { ok = false; break; }
+      const Real* base = b2.ring + (size_t)h * nbs * BW;
+      for (int k = lo; k <= hi; ++k) {
+        const Real* A = base + (size_t)(k - lo) * BW + oA;
+        Real xc[NX];
 #pragma unroll
-    for (int c = 0; c < NX; ++c) xk[c] = 0;
-    if (lane < NX) dx[lane] = 0.0;
-    for (int k = 0; k < T; ++k) {
-      const Real* Lk = st + (long long)k * FW;
-      const Real* A = Lk + NU * NX;
-      const Real* B = A + NX * NX;
-      Real u = 0;
-      if (lane < NU) {
-        u = (Real)du[(long long)k * NU + lane];
+        for (int c = 0; c < NX; ++c) xc[c] = __shfl_sync(0xffffffffu, x, c);
+        Real s0 = (lane < NX) ? b2.cd[(size_t)k * NX + lane] : (Real)0, s1 = 0;
+        if (lane < NX) {
 #pragma unroll
-        for (int c = 0; c < NX; ++c) u += Lk[lane * NX + c] * xk[c];
-        du[(long long)k * NU + lane] = (double)u;
+          for (int c = 0; c < NX; c += 2) {
+            s0 += A[lane * NX + c] * xc[c];
+            if (c + 1 < NX) s1 += A[lane * NX + c + 1] * xc[c + 1];
+          }
+        }
+        x = s0 + s1;
+        if (lane < NX) b2.px[(size_t)(k + 1) * NX + lane] = x;
       }
-      Real uk[NU];
-#pragma unroll
-      for (int v = 0; v < NU; ++v) uk[v] = __shfl_sync(0xffffffffu, u, v);
-      Real xn = 0;
-      if (lane < NX) {
-#pragma unroll
-        for (int c = 0; c < NX; ++c) xn += A[lane * NX + c] * xk[c];
-#pragma unroll
-        for (int v = 0; v < NU; ++v) xn += B[lane * NU + v] * uk[v];
-        dx[(long long)(k + 1) * NX + lane] = (double)xn;
+      __syncwarp();
+      if (lane == 0 && j + 2 < nblk) {
+        fence_proxy_async();
+        const int lo2 = (j + 2) * nbs;
+        issue(lo2, lo2 + nbs - 1 < T - 1 ? lo2 + nbs - 1 : T - 1, h);
       }
-#pragma unroll
-      for (int c = 0; c < NX; ++c) xk[c] = __shfl_sync(0xffffffffu, xn, c);
     }
+    if (lane == 0) *s_flag = ok ? 1 : 0;
   }
+  __syncthreads();
+  if (*s_flag == 0) return false;
+  // ---- δu_k = L_k δx_k + l_k, and δx to global memory ----
+  double* du = ar + L.du;
+  double* dx = ar + L.dx;
+  for (int q = tid; q < T * NU; q += nthr) {
+    const int k = q / NU, u = q - k * NU;
+    const Real* f = pk + (size_t)k * BW;
+    Real v = b2.ls[q];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) v += f[oL + u * NX + c] * b2.px[(size_t)k * NX + c];
+    du[q] = (double)v;
+  }
+  for (int q = tid; q < (T + 1) * NX; q += nthr) dx[q] = (double)b2.px[q];
   __syncthreads();
   return true;
 }
 
-// Load the gain-table registers of this thread's column groups from an arena Gtᵀ table ((T+1)×NU×NX).
 template <int NX, int NU, typename Real, int PAIRS, int W>
 __device__ __forceinline__ void load_gt_regs(const double* gt, int T, const int (&mk)[PAIRS], int ck,
                                              Real (&g)[PAIRS][NU][W]) {
@@ -753,6 +842,10 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
 
   // this thread's row group and its two column groups (blocks m and T - m, components ck .. ck+W-1)
   const ColMap cm = col_map<NX, NU, Real>(I.T, FASmem<NX, NU, Real>::zcap(sp.chunk, sp.max_rows, I.T));
+  // block-2 sweep areas in the chunk buffers (checked on the host to hold a ring of >= 1 step)
+  B2Smem<NX, NU, Real> b2;
+  b2.carve(reinterpret_cast<char*>(sm.buf[0].lam), 2 * FASmem<NX, NU, Real>::buf_bytes(sp.chunk, sp.max_rows), I.T);
+  Real* const b2pv = reinterpret_cast<Real*>(sm.vec);
 
   // ---- initialization (Algorithm 1): λ_p, λ_ν, k, p <- 0 (or a warm start of k, p̃, λ_p) ----
   for (long long e = tid; e < I.n_ent; e += NT) lam[I.ent0 + e] = (Real)0;
@@ -912,7 +1005,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
         const long long rr = (long long)(t - 1) * I.rows_per_t + s2;
         v += 0.5 * rho * D.dd[I.row0 + rr] * S.arow[I.arow0 + rr * NX + c];
       }
-      ar[L.qv + (long long)t * NX + c] = v;
+      b2.qs[(size_t)t * NX + c] = (Real)v;
     }
     //   r_k = 2R_u(û_k - u_ref) + (ρ/2) Σ_{control rows at (k,i)} σ_j d_j e_i
     for (int q = tid; q < T * NU; q += NT) {
@@ -925,25 +1018,20 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
           if (ri.z == iu) v += 0.5 * rho * ((ri.y == ROW_UHI) ? 1.0 : -1.0) * D.dd[gr.x + qq];
         }
       }
-      ar[L.rv + q] = v;
+      b2.rs[q] = (Real)v;
     }
     for (int q = tid; q < (T + 1) * NX; q += NT) ar[L.dx_prev + q] = ar[L.dx + q];
     __syncthreads();
     tm.mark(PH_QR);
     // ---------------- (c) gain update: K^b from Z'; Gtᵀ^b replaces the previous table ----------------
     // ---------------- (c) gain update and (b) Block 2, which are independent: the Riccati sweep runs
-    // on warp 0 from factors staged in the idle chunk buffers while the other warps solve for K^b
-    // (its Gtᵀ^b replaces the previous table) ----------------
+    // on warp 0 while the other warps solve for K^b (its Gtᵀ^b replaces the previous table) ----------------
     {
       const double gargs[3] = {I.sqrt_tau, rho * I.sqrt_tau, 0.0};
       double* gt_new = ar + (gsel ? L.Gt0 : L.Gt1);
-      // The two chunk buffers are contiguous in the carve; their total size bounds the staging area.
-      const size_t cap = 2 * FASmem<NX, NU, Real>::buf_bytes(sp.chunk, sp.max_rows) / sizeof(Real);
-      if (!riccati_sweep_staged<NX, NU, Real>(ar, L, sa, SL, T, sm.buf[0].lam, cap, sm.vec, gargs, ar + L.K1, gt_new)) {
-        gain_solve<NX, NU, Real>(ar, L, T, gargs[0], gargs[1], gargs[2], ar + L.K1, gt_new);
-        tm.mark(PH_GAIN);
-        if (warp == 0) riccati_sweep<NX, NU, Real>(ar, L, sa, SL, T, sm.vec);
-        __syncthreads();
+      if (!block2_sweep_and_gain<NX, NU, Real>(ar, L, T, b2, bars, phase, s_flag, b2pv, gargs, ar + L.K1, gt_new)) {
+        status = ST_TIMEOUT;
+        goto done;
       }
       gsel ^= 1;
     }

@@ -328,6 +328,15 @@ __device__ __noinline__ void riccati_factor_warp(const Dev<Real>& D, int i, doub
     for (int q = lane; q < nx * nx; q += 32) gAcl[q] = Ak[q];
     __syncwarp();
     wmm(gAcl, Bk, false, nu, Lm, false, nx, nx, nx, nu, 1.0, true);
+    {
+      // packed record of step k in the compute precision: N, M, L, A_cl, B
+      Real* pk = reinterpret_cast<Real*>(ar + L.RicPk) + (long long)k * pk_stride(nx, nu);
+      const int oM = nu * nu, oL = oM + nu * nx, oA = oL + nu * nx, oB = oA + nx * nx;
+      for (int q = lane; q < nu * nu; q += 32) pk[q] = (Real)Nm[q];
+      for (int q = lane; q < nu * nx; q += 32) { pk[oM + q] = (Real)gM[q]; pk[oL + q] = (Real)Lm[q]; pk[oB + q] = (Real)Bk[q]; }
+      for (int q = lane; q < nx * nx; q += 32) pk[oA + q] = (Real)gAcl[q];
+      __syncwarp();
+    }
     if (k >= 1) {
       build_Q(k);
       wmm(tmp, Ak, true, nx, PA, false, nx, nx, nx, nx, 1.0, false);        // AᵀPA

@@ -68,9 +68,13 @@ struct Arena {
   long long Psi, SigU, SigL, Phi;
   long long K0, K1, Kt, Kacc, Gt0, Gt1, Zp;
   long long du, dx, du_prev, dx_prev, e, lam_e, qv, rv;
-  long long Pf, Gam, Dv, RicL, RicAcl, RicN, RicM, Ws1, Ws2;
+  long long Pf, Gam, Dv, RicL, RicAcl, RicN, RicM, Ws1, Ws2, RicPk;
   long long total;
 };
+
+// Per-step record of the block-2 factors in the compute precision (N, M, L, A_cl, B), padded to a
+// multiple of 4 values so that every record starts on a 16-byte boundary.
+NRTO_HD constexpr int pk_stride(int nx, int nu) { return ((nu * nu + 3 * nu * nx + nx * nx) + 3) & ~3; }
 
 NRTO_HD Arena arena_layout(int nx, int nu, int T, int n_obs, int n_link) {
   Arena a;
@@ -91,6 +95,7 @@ NRTO_HD Arena arena_layout(int nx, int nu, int T, int n_obs, int n_link) {
   a.Pf = take((long long)T * nu * nu); a.Gam = take((long long)T * nu); a.Dv = take(g);
   a.RicL = take(g); a.RicAcl = take((long long)T * nx * nx); a.RicN = take((long long)T * nu * nu);
   a.RicM = take(g); a.Ws1 = take(g); a.Ws2 = take(g);
+  a.RicPk = take((long long)T * pk_stride(nx, nu));   // sized for double records
   a.total = o;
   return a;
 }
