@@ -103,9 +103,118 @@ __global__ void k_rows(Dev<Real> D, int slot_sel) {
   }
 }
 
-// Adjoint sweep per state row, G lanes per row (G = 4 for nx <= 4, else 16).  Block per instance.
+// Adjoint rows of one instance (Supplementary Sec. I): for state row j at time t_j with gradient
+// a_j, v_{j,t_j} = a_j, v_{j,i} = A_iᵀ v_{j,i+1}; b̂_{j,i} = √τ Ψ_i v_{j,i} (i = 0..t_j) and
+// b_{j,i} = B_iᵀ v_{j,i+1} (i < t_j), b_{j,t_j} = 0.  One sweep over i = T..0 for all rows at once:
+// each thread keeps RB rows' v in registers, the step's Ψ_i, A_{i-1}, B_{i-1} are staged in shared
+// memory (double buffered, prefetched one step ahead) and shared by every row.  Arithmetic in the
+// compute precision.
+template <int NX, int NU, int RB, typename Real>
+__device__ void adjoint_rows(const Dev<Real>& D, const Inst& I, const double* ar, const Arena& L, const double* sa,
+                             const SlotL& SL, LinSlot<Real>& S, Real* smem) {
+  constexpr int MW = NX * NX + NX * NX + NX * NU;   // Ψ_i, A_{i-1}, B_{i-1} of one step
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int rpt = I.rows_per_t, nsr = I.n_sr;
+  const Real sq = (Real)I.sqrt_tau;
+  const double* Psi = ar + L.Psi;
+  const double* A = sa + SL.A;
+  const double* B = sa + SL.B;
+  // step i's matrices: [Ψ_i | A_{i-1} | B_{i-1}] (A, B only for i >= 1)
+  auto fetch = [&](int i, int q) -> Real {
+    if (q < NX * NX) return (Real)Psi[(long long)i * NX * NX + q];
+    if (i < 1) return (Real)0;
+    if (q < 2 * NX * NX) return (Real)A[(long long)(i - 1) * NX * NX + (q - NX * NX)];
+    return (Real)B[(long long)(i - 1) * NX * NU + (q - 2 * NX * NX)];
+  };
+  constexpr int PF = (MW + 127) / 128;   // values per thread for blockDim >= 128
+  for (int r0 = 0; r0 < nsr; r0 += RB * nthr) {
+    Real v[RB][NX];
+    int tr[RB];
+    long long e0[RB], b0[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      const int r = r0 + b * nthr + tid;
+      tr[b] = -1;
+      if (r < nsr) {
+        const long long R = I.row0 + r;
+        tr[b] = D.rinfo[R].x;
+        e0[b] = D.rent[R];
+        b0[b] = D.rbent[R];
+      }
+    }
+    const int r_last = min(nsr - 1, r0 + RB * nthr - 1);
+    const int kmax = r_last / rpt + 1;   // rows are ordered by t = 1..T
+    // stage step kmax
+    __syncthreads();
+    for (int q = tid; q < MW; q += nthr) smem[(kmax & 1) * MW + q] = fetch(kmax, q);
+    __syncthreads();
+    for (int k = kmax; k >= 0; --k) {
+      const Real* m = smem + (k & 1) * MW;
+      const Real* sPsi = m;
+      const Real* sA = m + NX * NX;
+      const Real* sB = m + 2 * NX * NX;
+      // prefetch step k-1 into registers
+      Real nxt[PF];
+#pragma unroll
+      for (int w = 0; w < PF; ++w) {
+        const int q = tid + w * nthr;
+        nxt[w] = (k >= 1 && q < MW) ? fetch(k - 1, q) : (Real)0;
+      }
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        if (tr[b] < k) continue;
+        const int r = r0 + b * nthr + tid;
+        if (tr[b] == k) {
+#pragma unroll
+          for (int c = 0; c < NX; ++c) v[b][c] = (Real)S.arow[I.arow0 + (long long)r * NX + c];
+#pragma unroll
+          for (int u = 0; u < NU; ++u) S.bvec[b0[b] + (long long)k * NU + u] = (Real)0;
+        }
+#pragma unroll
+        for (int c = 0; c < NX; ++c) {
+          Real acc = 0;
+#pragma unroll
+          for (int q = 0; q < NX; ++q) acc += sPsi[c * NX + q] * v[b][q];
+          S.bhat[e0[b] + (long long)k * NX + c] = sq * acc;
+        }
+        if (k >= 1) {
+#pragma unroll
+          for (int u = 0; u < NU; ++u) {
+            Real acc = 0;
+#pragma unroll
+            for (int q = 0; q < NX; ++q) acc += sB[q * NU + u] * v[b][q];
+            S.bvec[b0[b] + (long long)(k - 1) * NU + u] = acc;
+          }
+          Real vn[NX];
+#pragma unroll
+          for (int c = 0; c < NX; ++c) {
+            Real acc = 0;
+#pragma unroll
+            for (int q = 0; q < NX; ++q) acc += sA[q * NX + c] * v[b][q];
+            vn[c] = acc;
+          }
+#pragma unroll
+          for (int c = 0; c < NX; ++c) v[b][c] = vn[c];
+        }
+      }
+      if (k >= 1) {
+        Real* mn = smem + ((k - 1) & 1) * MW;
+#pragma unroll
+        for (int w = 0; w < PF; ++w) {
+          const int q = tid + w * nthr;
+          if (q < MW) mn[q] = nxt[w];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+constexpr int ADJ_SMEM = 2 * (14 * 14 * 2 + 14 * 7);   // two steps of the largest kind
+
 template <typename Real>
-__global__ void k_adjoint(Dev<Real> D, int slot_sel) {
+__global__ void __launch_bounds__(256) k_adjoint(Dev<Real> D, int slot_sel) {
+  __shared__ Real smem[ADJ_SMEM];
   const int i = blockIdx.x;
   const int slot = resolve_slot(D.is, i, slot_sel);
   const Inst I = D.inst[i];
@@ -114,51 +223,10 @@ __global__ void k_adjoint(Dev<Real> D, int slot_sel) {
   const double* ar = D.arena + I.arena0;
   const double* sa = D.slot[slot].arena + I.slot0;
   LinSlot<Real> S = D.slot[slot];
-  const int nx = I.nx, nu = I.nu;
-  const int G = (nx <= 4) ? 4 : 16;
-  const int lane = threadIdx.x & 31;
-  const int sub = lane % G;
-  const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
-  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - sub));
-  const double sq = I.sqrt_tau;
-  const double* A = sa + SL.A;
-  const double* B = sa + SL.B;
-  const double* Psi = ar + L.Psi;
-  for (int r = grp; r < I.n_sr; r += ngrp) {
-    const long long R = I.row0 + r;
-    const int t = D.rinfo[R].x;
-    const long long e0 = D.rent[R], b0 = D.rbent[R];
-    double v = (sub < nx) ? S.arow[I.arow0 + (long long)r * nx + sub] : 0.0;
-    // block t: b̂_t = √τ Ψ_t v_t, b_t = 0
-    {
-      double acc = 0.0;
-      for (int q = 0; q < nx; ++q) {
-        double vq = __shfl_sync(mask, v, q, G);
-        if (sub < nx) acc += Psi[(long long)t * nx * nx + sub * nx + q] * vq;
-      }
-      if (sub < nx) S.bhat[e0 + (long long)t * nx + sub] = (Real)(sq * acc);
-      if (sub < nu) S.bvec[b0 + (long long)t * nu + sub] = (Real)0.0;
-    }
-    for (int k = t - 1; k >= 0; --k) {
-      const double* Ak = A + (long long)k * nx * nx;
-      const double* Bk = B + (long long)k * nx * nu;
-      const double* Pk = Psi + (long long)k * nx * nx;
-      double bu = 0.0, vn = 0.0;
-      for (int q = 0; q < nx; ++q) {
-        double vq = __shfl_sync(mask, v, q, G);
-        if (sub < nu) bu += Bk[q * nu + sub] * vq;
-        if (sub < nx) vn += Ak[q * nx + sub] * vq;
-      }
-      v = vn;
-      double acc = 0.0;
-      for (int q = 0; q < nx; ++q) {
-        double vq = __shfl_sync(mask, v, q, G);
-        if (sub < nx) acc += Pk[sub * nx + q] * vq;
-      }
-      if (sub < nx) S.bhat[e0 + (long long)k * nx + sub] = (Real)(sq * acc);
-      if (sub < nu) S.bvec[b0 + (long long)k * nu + sub] = (Real)bu;
-    }
-  }
+  if (I.n_sr == 0) return;
+  if (I.kind == KIND_UNICYCLE) adjoint_rows<3, 2, 8, Real>(D, I, ar, L, sa, SL, S, smem);
+  else if (I.kind == KIND_QUADCOPTER) adjoint_rows<12, 4, 4, Real>(D, I, ar, L, sa, SL, S, smem);
+  else adjoint_rows<14, 7, 2, Real>(D, I, ar, L, sa, SL, S, smem);
 }
 
 // G_m = Σ_j b_{j,m} b_{j,m}ᵀ over state rows (from the stored, possibly rounded b) plus e_ie_iᵀ per
