@@ -426,13 +426,24 @@ void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
   }
 }
 
+// k_merit with the Gtᵀ table of the longest horizon of the batch in dynamic shared memory
+template <typename Real>
+void launch_merit(nrto_problem* P, int slot_sel, int kbuf, int gtbuf, double w_p, int out_idx) {
+  size_t bytes = 0;
+  for (int k = 0; k < 3; ++k)
+    if (P->kl[k].count > 0)
+      bytes = std::max(bytes, (size_t)(P->kl[k].tmax + 1) * kind_nu(k) * kind_nx(k) * sizeof(Real));
+  CK(cudaFuncSetAttribute(k_merit<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  k_merit<Real><<<P->n, 256, bytes, P->stream>>>(P->dev<Real>(), slot_sel, kbuf, gtbuf, w_p, out_idx);
+  P->check_launch("k_merit");
+}
+
 template <typename Real>
 void launch_merit_current(nrto_problem* P, double w_p) {
   Dev<Real> D = P->dev<Real>();
   k_gain_to_gt<Real><<<P->n, 256, 0, P->stream>>>(D, 3, 0);
   P->check_launch("k_gain_to_gt");
-  k_merit<Real><<<P->n, 256, 0, P->stream>>>(D, -1, 3, 0, w_p, SC_PHI);
-  P->check_launch("k_merit");
+  launch_merit<Real>(P, -1, 3, 0, w_p, SC_PHI);
 }
 
 template <typename Real>
@@ -444,8 +455,7 @@ void launch_outer_step(nrto_problem* P, const nrto_solver_opts& o) {
   launch_linearize<Real>(P, -2);
   k_gain_to_gt<Real><<<P->n, 256, 0, P->stream>>>(D, 1, 1);
   P->check_launch("k_gain_to_gt");
-  k_merit<Real><<<P->n, 256, 0, P->stream>>>(D, -2, 1, 1, o.w_p, SC_PHI_CAND);
-  P->check_launch("k_merit");
+  launch_merit<Real>(P, -2, 1, 1, o.w_p, SC_PHI_CAND);
   k_accept<Real><<<P->n, 128, 0, P->stream>>>(D, o.r0, o.r_min);
   P->check_launch("k_accept");
 }

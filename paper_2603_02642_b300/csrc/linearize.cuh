@@ -462,9 +462,43 @@ __global__ void k_gain_to_gt(Dev<Real> D, int kbuf, int gtbuf) {
 // Merit of Problem 1 at the nominal of the selected slot with the gains in `kbuf` (Gtᵀ in `gtbuf`):
 // φ = Σ_k (ū_k-u_ref)ᵀR_u(·) + Σ_{t≥1}(x̄_t-x_goal)ᵀQ_x(·) + Σ_k‖R_K K_k‖_F²
 //     + w_p Σ_j max(0, g_j(x̄) + ‖Â_j k_v + b̂_j‖).
-// Block per instance; writes sc[out_idx] and the cost to sc[SC_COST].
+// Block per instance; writes sc[out_idx] and the cost to sc[SC_COST].  The row norms stream the
+// ragged b̂, b rows once (warp per row) against the Gtᵀ table staged in shared memory; row values in
+// the compute precision, sums in FP64.
+template <int NX, int NU, typename Real>
+__device__ void merit_rows(const Dev<Real>& D, const Inst& I, const double* Gt, const LinSlot<Real>& S,
+                           Real* gts, double& vio) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = threadIdx.x; q < (I.T + 1) * NU * NX; q += blockDim.x) gts[q] = (Real)Gt[q];
+  __syncthreads();
+  for (int r = wid; r < I.n_sr + I.n_cr; r += nw) {
+    const long long R = I.row0 + r;
+    const int4 ri = D.rinfo[R];
+    Real n2 = 0;
+    if (r < I.n_sr) {
+      const long long e0 = D.rent[R], b0 = D.rbent[R];
+      const int len = (ri.x + 1) * NX;
+      for (int e = lane; e < len; e += 32) {
+        const int m = e / NX, c = e - m * NX;
+        Real y = S.bhat[e0 + e];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) y += gts[m * NU * NX + u * NX + c] * S.bvec[b0 + (long long)m * NU + u];
+        n2 += y * y;
+      }
+    } else {
+      for (int c = lane; c < NX; c += 32) {
+        const Real y = gts[ri.x * NU * NX + ri.z * NX + c];
+        n2 += y * y;
+      }
+    }
+    n2 = warp_sum(n2);
+    if (lane == 0) vio += fmax(0.0, S.g0[R] + sqrt((double)n2));
+  }
+}
+
 template <typename Real>
 __global__ void k_merit(Dev<Real> D, int slot_sel, int kbuf, int gtbuf, double w_p, int out_idx) {
+  extern __shared__ __align__(16) char merit_smem[];
   const int i = blockIdx.x;
   const int slot = resolve_slot(D.is, i, slot_sel);
   const Inst I = D.inst[i];
@@ -490,29 +524,10 @@ __global__ void k_merit(Dev<Real> D, int slot_sel, int kbuf, int gtbuf, double w
     double kv = K[q] * ar[L.RK + (q / nx) % nu];
     cst += kv * kv;
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = wid; r < I.n_sr + I.n_cr; r += nw) {
-    const long long R = I.row0 + r;
-    const int4 ri = D.rinfo[R];
-    double n2 = 0.0;
-    if (r < I.n_sr) {
-      const long long e0 = D.rent[R], b0 = D.rbent[R];
-      const int len = (ri.x + 1) * nx;
-      for (int e = lane; e < len; e += 32) {
-        int m = e / nx, c = e % nx;
-        double y = (double)S.bhat[e0 + e];
-        for (int u = 0; u < nu; ++u) y += Gt[(long long)m * nu * nx + u * nx + c] * (double)S.bvec[b0 + (long long)m * nu + u];
-        n2 += y * y;
-      }
-    } else {
-      for (int c = lane; c < nx; c += 32) {
-        double y = Gt[(long long)ri.x * nu * nx + ri.z * nx + c];
-        n2 += y * y;
-      }
-    }
-    n2 = warp_sum(n2);
-    if (lane == 0) vio += fmax(0.0, S.g0[R] + sqrt(n2));
-  }
+  Real* gts = reinterpret_cast<Real*>(merit_smem);
+  if (I.kind == KIND_UNICYCLE) merit_rows<3, 2, Real>(D, I, Gt, S, gts, vio);
+  else if (I.kind == KIND_QUADCOPTER) merit_rows<12, 4, Real>(D, I, Gt, S, gts, vio);
+  else merit_rows<14, 7, Real>(D, I, Gt, S, gts, vio);
   block_sum4(cst, vio, z0, z1, red);
   if (threadIdx.x == 0) {
     D.sc[i * NSC + out_idx] = cst + w_p * vio;
