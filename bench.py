@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--stall", type=int, default=0, help="stall-stop period (0 = off)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned-warm-start study")
     return ap.parse_args()
 
 
@@ -164,6 +165,83 @@ def kernel_sources_sha():
         with open(os.path.join(ROOT, "paper_2603_02642_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def measured_peak_bf16():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["bf16_tflops"]), "measured (burst)"
+    except Exception:
+        return 1800.0, "fallback"
+
+
+def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
+    """Learned warm start on the quadcopter workload (T = 100, 1-15 obstacles): targets from cold
+    FullADMM solves of the first outer step, training by the library's kernels, then cold vs
+    warm-started solves (to full residuals <= 1e-4, <= 5000 iterations, residual balancing every 25)
+    of held-out instances, and the network's tensor-core GEMM rate on an inference batch."""
+    import torch
+    from paper_2603_02642_b300 import nrto, warmstart as WS, workloads as W
+    opts = dict(rho=10.0, max_inner=5000, eps_p=1e-4, eps_d=1e-4, check=1, adapt_every=25)
+    t0 = time.perf_counter()
+    train = [W.warmstart_quad(s) for s in range(n_train)]
+    prob = nrto.Problem(train, nrto.PREC_MIXED, stream=stream.cuda_stream)
+    prob.linearize()
+    prob.set_trust_radius(2.0)
+    out = prob.solve_socp(nrto.Options(**opts))
+    X, Y, Mk = WS.collect_targets(prob, train, out["status"])
+    prob.close()
+    t_data = time.perf_counter() - t0
+    ws = WS.WarmStart(max_batch=n_infer, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    hist = ws.fit(X, Y, Mk, steps=steps, batch=256, lr=1e-3)
+    t_fit = time.perf_counter() - t0
+    test = [W.warmstart_quad(1_000_000 + s) for s in range(n_eval)]
+    res = {}
+    for mode in ("cold", "warm"):
+        q = nrto.Problem(test, nrto.PREC_MIXED, stream=stream.cuda_stream)
+        q.linearize()
+        q.set_trust_radius(2.0)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        if mode == "warm":
+            ws.apply(q, test)
+        e1.record(stream)
+        o = q.solve_socp(nrto.Options(stall_every=1000 if mode == "warm" else 0, stall_ratio=0.99, warm_fallback=1,
+                                      **opts))
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fb = sum(int(q.export(nrto.F_STATS, i)[6]) for i in range(n_eval))
+        res[mode] = dict(iters=o["iters"].copy(), conv=o["status"] == 1, solve_ms=e1.elapsed_time(e2),
+                         predict_ms=e0.elapsed_time(e1), fallbacks=fb)
+        q.close()
+    both = res["cold"]["conv"] & res["warm"]["conv"]
+    # tensor-core rate of the network's GEMMs on an inference batch
+    feats = WS.features([W.warmstart_quad(2_000_000 + s) for s in range(n_infer)])
+    ws.net.forward(feats)
+    ws.net.profile(True)
+    ws.net.forward(feats)
+    gms, gfl, gn = ws.net.profile(False)
+    peak, peak_kind = measured_peak_bf16()
+    achieved = gfl / (gms / 1e3) / 1e12
+    ws.net.close()
+    c, w = res["cold"], res["warm"]
+    return {
+        "workload": f"quadcopter T=100, 1-15 obstacles (warmstart_quad); train seeds 0..{n_train - 1}, "
+                    f"held-out seeds 1000000..{1000000 + n_eval - 1}",
+        "targets": int(X.shape[0]), "train_steps": steps, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+        "data_s": round(t_data, 2), "fit_s": round(t_fit, 2),
+        "cold": {"converged": int(c["conv"].sum()), "solve_ms": c["solve_ms"],
+                 "solves_per_s": n_eval / (c["solve_ms"] / 1e3)},
+        "warm": {"converged": int(w["conv"].sum()), "solve_ms": w["solve_ms"], "predict_ms": w["predict_ms"],
+                 "solves_per_s": n_eval / ((w["solve_ms"] + w["predict_ms"]) / 1e3), "fallbacks": w["fallbacks"]},
+        "iters_mean_both_converged": {"cold": float(c["iters"][both].mean()) if both.any() else None,
+                                      "warm": float(w["iters"][both].mean()) if both.any() else None},
+        "mlp_roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_source": peak_kind, "batch": n_infer,
+                         "gemm_launches": int(gn), "gemm_ms": gms},
+    }
 
 
 def measured_peak_gbs():
@@ -297,6 +375,10 @@ def main():
         e2e = {"value": ws * args.n * args.steps / float(tt.item()), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    warm = None
+    if rank == 0 and not args.no_warm:
+        prob.close()
+        warm = warm_start_study(stream)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = oracle_estimate(insts, args.n_outer, args.max_inner)
@@ -325,6 +407,7 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "warm_start": warm,
         }
         print(json.dumps(line))
     prob.close()

@@ -238,6 +238,11 @@ nrto_status nrto_mlp_train_step(nrto_mlp_t m, const float* x, const float* targe
                                 int batch, float lr, double* loss, float* grads);
 /* Number of kernel launches issued for this network since create. */
 long long nrto_mlp_kernel_launches(nrto_mlp_t m);
+/* Tensor-core GEMM timing: CUDA events on the network's stream around every GEMM launch while
+ * enabled.  Returns (and clears) the milliseconds, the algorithmic FLOPs (2·M·N·K) and the launch
+ * count since the previous call, then enables (enable != 0) or disables recording. */
+nrto_status nrto_mlp_profile(nrto_mlp_t m, int enable, double* gemm_ms, double* gemm_flops,
+                             long long* gemm_launches);
 
 /* nrto_solve without device allocation.  The paper has no counterpart: this is a library service.
  * Some callers cannot call cudaMalloc: real-time control loops that must not pay an allocation's

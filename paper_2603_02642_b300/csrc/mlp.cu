@@ -144,7 +144,57 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
     float v[32];
     tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
     const int nb = n0 + c * 32;
-    if (row < ep.M && nb < ep.N) {
+    // full 32-column chunks with 16-byte aligned rows: vector stores; ragged edges: scalar
+    auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    bool vec = (nb + 32 <= ep.N);
+    if constexpr (EPI == EPI_BIAS_GELU)
+      vec = vec && (ep.ld_f32 % 4 == 0) && (ep.ld_bf16 % 8 == 0) && al16(ep.out_f32) && al16(ep.out_bf16);
+    else if constexpr (EPI == EPI_GELU_BWD)
+      vec = vec && (ep.ld_bf16 % 8 == 0) && (ep.ld_zin % 4 == 0) && al16(ep.out_bf16) && al16(ep.zin);
+    else vec = vec && (ep.ld_f32 % 4 == 0) && al16(ep.out_f32);
+    if (row < ep.M && vec) {
+      if constexpr (EPI == EPI_BIAS_GELU) {
+        float4* zo = reinterpret_cast<float4*>(ep.out_f32 + (long long)row * ep.ld_f32 + nb);
+        uint4* ho = reinterpret_cast<uint4*>(ep.out_bf16 + (long long)row * ep.ld_bf16 + nb);
+#pragma unroll
+        for (int j8 = 0; j8 < 4; ++j8) {
+          float z[8];
+          __align__(16) bf16 h[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            z[t] = v[j8 * 8 + t] + ep.bias[nb + j8 * 8 + t];
+            h[t] = __float2bfloat16_rn(gelu_f(z[t]));
+          }
+          zo[2 * j8] = make_float4(z[0], z[1], z[2], z[3]);
+          zo[2 * j8 + 1] = make_float4(z[4], z[5], z[6], z[7]);
+          ho[j8] = *reinterpret_cast<const uint4*>(h);
+        }
+      } else if constexpr (EPI == EPI_GELU_BWD) {
+        const float4* zi = reinterpret_cast<const float4*>(ep.zin + (long long)row * ep.ld_zin + nb);
+        uint4* ho = reinterpret_cast<uint4*>(ep.out_bf16 + (long long)row * ep.ld_bf16 + nb);
+#pragma unroll
+        for (int j8 = 0; j8 < 4; ++j8) {
+          const float4 za = zi[2 * j8], zb = zi[2 * j8 + 1];
+          const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+          __align__(16) bf16 h[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) h[t] = __float2bfloat16_rn(v[j8 * 8 + t] * gelu_grad_f(zz[t]));
+          ho[j8] = *reinterpret_cast<const uint4*>(h);
+        }
+      } else {
+        float4* o = reinterpret_cast<float4*>(ep.out_f32 + (long long)row * ep.ld_f32 + nb);
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          float a[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            a[t] = v[j4 * 4 + t];
+            if constexpr (EPI == EPI_BIAS) a[t] += ep.bias[nb + j4 * 4 + t];
+          }
+          o[j4] = make_float4(a[0], a[1], a[2], a[3]);
+        }
+      }
+    } else if (row < ep.M && nb < ep.N) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int n = nb + j;
@@ -331,6 +381,25 @@ struct nrto_mlp {
   int* d_err = nullptr;
   long long adam_t = 0;
   long long launches = 0;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gemm_events;   // around each GEMM launch
+  double gemm_flops = 0.0;                                         // 2·M·N·K of the timed launches
+
+  template <int BN, int EPI>
+  void gemm(const bf16* A, long long lda, const bf16* B, long long ldb, int M, int N, int K, const EpiArgs& ep) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (profiling) {
+      MK(cudaEventCreate(&e0));
+      MK(cudaEventCreate(&e1));
+      MK(cudaEventRecord(e0, stream));
+    }
+    launch_gemm<BN, EPI>(stream, A, lda, B, ldb, M, N, K, ep);
+    if (profiling) {
+      MK(cudaEventRecord(e1, stream));
+      gemm_events.push_back({e0, e1});
+      gemm_flops += 2.0 * M * N * K;
+    }
+  }
 
   template <typename T>
   T* dalloc(size_t count) {
@@ -342,6 +411,7 @@ struct nrto_mlp {
   }
   ~nrto_mlp() {
     if (stream) cudaStreamSynchronize(stream);
+    for (auto& ev : gemm_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
     for (void* p : allocs) cudaFree(p);
   }
   void refresh_bf16() {
@@ -367,10 +437,10 @@ struct nrto_mlp {
       ep.M = B; ep.N = dims[l + 1]; ep.bias = theta + boff[l]; ep.err = d_err;
       if (l < L - 1) {
         ep.out_f32 = Z[l + 1]; ep.ld_f32 = dims[l + 1]; ep.out_bf16 = H[l + 1]; ep.ld_bf16 = dims[l + 1];
-        launch_gemm<128, EPI_BIAS_GELU>(stream, A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
+        gemm<128, EPI_BIAS_GELU>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
       } else {
         ep.out_f32 = Y; ep.ld_f32 = dims[L];
-        launch_gemm<256, EPI_BIAS>(stream, A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
+        gemm<256, EPI_BIAS>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
       }
       ++launches;
     }
@@ -393,7 +463,7 @@ struct nrto_mlp {
       MK(cudaGetLastError());
       EpiArgs ew{};
       ew.M = dout; ew.N = din; ew.out_f32 = grad + woff[l]; ew.ld_f32 = din; ew.err = d_err;
-      launch_gemm<256, EPI_F32>(stream, tA, B, tB, B, dout, din, B, ew);
+      gemm<256, EPI_F32>(tA, B, tB, B, dout, din, B, ew);
       k_colsum_bf16<<<(dout + 255) / 256, 256, 0, stream>>>(dZ[l + 1], B, dout, dout, grad + boff[l]);
       MK(cudaGetLastError());
       launches += 4;
@@ -401,7 +471,7 @@ struct nrto_mlp {
         // dZ_l = (dZ_{l+1} · W_l) ⊙ gelu'(Z_l)
         EpiArgs eb{};
         eb.M = B; eb.N = din; eb.out_bf16 = dZ[l]; eb.ld_bf16 = din; eb.zin = Z[l]; eb.ld_zin = din; eb.err = d_err;
-        launch_gemm<128, EPI_GELU_BWD>(stream, dZ[l + 1], dout, Wkn[l], dout, B, din, dout, eb);
+        gemm<128, EPI_GELU_BWD>(dZ[l + 1], dout, Wkn[l], dout, B, din, dout, eb);
         ++launches;
       }
     }
@@ -570,5 +640,32 @@ nrto_status nrto_mlp_train_step(nrto_mlp_t m, const float* x, const float* targe
 }
 
 long long nrto_mlp_kernel_launches(nrto_mlp_t m) { return m ? m->launches : -1; }
+
+nrto_status nrto_mlp_profile(nrto_mlp_t m, int enable, double* gemm_ms, double* gemm_flops, long long* gemm_launches) {
+  try {
+    if (!m) mfail(NRTO_ERR_INVALID, "null network");
+    double ms = 0.0;
+    if (!m->gemm_events.empty()) {
+      MK(cudaStreamSynchronize(m->stream));
+      for (auto& ev : m->gemm_events) {
+        float t = 0.f;
+        MK(cudaEventElapsedTime(&t, ev.first, ev.second));
+        ms += t;
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+      }
+    }
+    if (gemm_ms) *gemm_ms = ms;
+    if (gemm_flops) *gemm_flops = m->gemm_flops;
+    if (gemm_launches) *gemm_launches = (long long)m->gemm_events.size();
+    m->gemm_events.clear();
+    m->gemm_flops = 0.0;
+    m->profiling = enable != 0;
+    return NRTO_OK;
+  } catch (const MlpError& e) {
+    nrto_mlp_set_error_internal(e);
+    return e.st;
+  }
+}
 
 }  // extern "C"

@@ -93,6 +93,8 @@ def load():
     lib.nrto_mlp_get_params.argtypes = [P, _fp]
     lib.nrto_mlp_forward.argtypes = [P, _fp, C.c_int, _fp]
     lib.nrto_mlp_train_step.argtypes = [P, _fp, _fp, _fp, C.c_int, C.c_float, _dp, _fp]
+    lib.nrto_mlp_profile.argtypes = [P, C.c_int, _dp, _dp, C.POINTER(C.c_longlong)]
+    lib.nrto_mlp_profile.restype = C.c_int
     lib.nrto_mlp_kernel_launches.argtypes = [P]
     lib.nrto_mlp_kernel_launches.restype = C.c_longlong
     lib.nrto_kernel_launches.argtypes = [P]
@@ -407,3 +409,9 @@ class MLP:
 
     def kernel_launches(self):
         return int(load().nrto_mlp_kernel_launches(self._h))
+
+    def profile(self, enable=True):
+        """(GEMM ms, GEMM FLOPs, GEMM launches) since the previous call; then enable/disable timing."""
+        ms, fl, n = C.c_double(0), C.c_double(0), C.c_longlong(0)
+        _check(load().nrto_mlp_profile(self._h, int(enable), C.byref(ms), C.byref(fl), C.byref(n)))
+        return ms.value, fl.value, n.value

@@ -148,3 +148,15 @@ def test_training_reduces_loss_on_a_teacher_network():
     assert l1 < 0.1 * l0
     assert net.kernel_launches() > 0
     net.close()
+
+
+def test_gemm_profile_counts_the_forward_gemms():
+    dims, batch = [99, 256, 256, 256, 9400], 1024
+    net, _ = make(dims, batch, seed=3)
+    x = RNG.normal(size=(batch, dims[0]))
+    net.profile(True)
+    net.forward(x)
+    ms, flops, n = net.profile(False)
+    assert n == len(dims) - 1 and ms > 0
+    assert flops == 2.0 * batch * sum(a * b for a, b in zip([104] + dims[1:-1], dims[1:]))
+    net.close()
