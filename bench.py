@@ -198,17 +198,20 @@ def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
     t_fit = time.perf_counter() - t0
     test = [W.warmstart_quad(1_000_000 + s) for s in range(n_eval)]
     res = {}
-    for mode in ("cold", "warm"):
+    # cold start; warm start; warm start with the cold fallback on a residual plateau (r_p above its
+    # tolerance and down by less than 1% over 1000 iterations)
+    for mode in ("cold", "warm", "warm_fallback"):
         q = nrto.Problem(test, nrto.PREC_MIXED, stream=stream.cuda_stream)
         q.linearize()
         q.set_trust_radius(2.0)
         torch.cuda.synchronize()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        if mode == "warm":
+        if mode != "cold":
             ws.apply(q, test)
         e1.record(stream)
-        o = q.solve_socp(nrto.Options(stall_every=1000 if mode == "warm" else 0, stall_ratio=0.99, warm_fallback=1,
+        fbk = mode == "warm_fallback"
+        o = q.solve_socp(nrto.Options(stall_every=1000 if fbk else 0, stall_ratio=0.99, warm_fallback=int(fbk),
                                       **opts))
         e2.record(stream)
         torch.cuda.synchronize()
@@ -216,7 +219,7 @@ def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
         res[mode] = dict(iters=o["iters"].copy(), conv=o["status"] == 1, solve_ms=e1.elapsed_time(e2),
                          predict_ms=e0.elapsed_time(e1), fallbacks=fb)
         q.close()
-    both = res["cold"]["conv"] & res["warm"]["conv"]
+    both = res["cold"]["conv"] & res["warm"]["conv"] & res["warm_fallback"]["conv"]
     # tensor-core rate of the network's GEMMs on an inference batch
     feats = WS.features([W.warmstart_quad(2_000_000 + s) for s in range(n_infer)])
     ws.net.forward(feats)
@@ -226,18 +229,26 @@ def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
     peak, peak_kind = measured_peak_bf16()
     achieved = gfl / (gms / 1e3) / 1e12
     ws.net.close()
-    c, w = res["cold"], res["warm"]
+    def summary(r, warm):
+        total_ms = r["solve_ms"] + (r["predict_ms"] if warm else 0.0)
+        d = {"converged": int(r["conv"].sum()), "solve_ms": r["solve_ms"],
+             "solves_per_s": n_eval / (total_ms / 1e3),
+             "converged_per_s": int(r["conv"].sum()) / (total_ms / 1e3),
+             "iters_mean_all_converged": float(r["iters"][both].mean()) if both.any() else None}
+        if warm:
+            d["predict_ms"] = r["predict_ms"]
+            d["fallbacks"] = r["fallbacks"]
+        return d
+
     return {
         "workload": f"quadcopter T=100, 1-15 obstacles (warmstart_quad); train seeds 0..{n_train - 1}, "
                     f"held-out seeds 1000000..{1000000 + n_eval - 1}",
         "targets": int(X.shape[0]), "train_steps": steps, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
         "data_s": round(t_data, 2), "fit_s": round(t_fit, 2),
-        "cold": {"converged": int(c["conv"].sum()), "solve_ms": c["solve_ms"],
-                 "solves_per_s": n_eval / (c["solve_ms"] / 1e3)},
-        "warm": {"converged": int(w["conv"].sum()), "solve_ms": w["solve_ms"], "predict_ms": w["predict_ms"],
-                 "solves_per_s": n_eval / ((w["solve_ms"] + w["predict_ms"]) / 1e3), "fallbacks": w["fallbacks"]},
-        "iters_mean_both_converged": {"cold": float(c["iters"][both].mean()) if both.any() else None,
-                                      "warm": float(w["iters"][both].mean()) if both.any() else None},
+        "held_out": n_eval, "converged_in_all_three": int(both.sum()),
+        "cold": summary(res["cold"], False),
+        "warm": summary(res["warm"], True),
+        "warm_fallback": summary(res["warm_fallback"], True),
         "mlp_roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "peak_source": peak_kind, "batch": n_infer,
                          "gemm_launches": int(gn), "gemm_ms": gms},

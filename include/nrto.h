@@ -123,6 +123,7 @@ typedef struct {
 } nrto_socp_out;
 
 typedef struct nrto_problem* nrto_problem_t;
+typedef struct nrto_mlp* nrto_mlp_t;   /* the warm-start network (nrto_mlp_*) */
 
 /* Create a batch of n_instances problems (descs[0..n-1]) in the given precision on `cuda_stream`
  * (a cudaStream_t, or NULL for the default stream).  Copies all inputs to the device, allocates all
@@ -160,6 +161,15 @@ nrto_status nrto_outer_step(nrto_problem_t p, const nrto_solver_opts* opts, int*
  * (host, may be NULL): u_bar Σ T*nu, K Σ T*nu*nx, merit n. */
 nrto_status nrto_solve(nrto_problem_t p, const nrto_solver_opts* opts, int n_outer,
                        double* u_bar, double* K, double* merit);
+
+/* Warm start of the next inner solve from a network (the library's learned warm start; the paper
+ * names it as future work): runs nrto_mlp_forward on features (host, n × network input) with the
+ * output kept on the device, then for instance i sets K from output[i][k_off ..] (T*nu*nx values,
+ * the K layout of nrto_export), and p̃ / λ_p of its row r from output[i][pt_off + row_map[R]] /
+ * output[i][lp_off + row_map[R]] (R: row index over all instances in problem order; row_map < 0
+ * gives 0).  λ_ν = 0.  The network's max_batch must be >= n.  Synchronizes both streams. */
+nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, const float* features,
+                                            const int* row_map, int k_off, int pt_off, int lp_off);
 
 /* Warm start for the next inner solve only: K (Σ T*nu*nx), p̃ and λ_p (Σ n_rows each); λ_ν = 0. */
 nrto_status nrto_set_warm_start(nrto_problem_t p, const double* K, const double* ptilde,
@@ -218,7 +228,6 @@ long long nrto_kernel_launches(nrto_problem_t p);
  * FP32 master parameters; bf16 weights and activations on fifth-generation tensor cores with FP32
  * accumulation.  Parameter layout (flat float array): for each layer l, W_l (out × in, row-major)
  * then b_l (out).  All array arguments are host pointers, row-major. ---- */
-typedef struct nrto_mlp* nrto_mlp_t;
 
 /* dims: n_dims widths (input, hidden..., output); every width after the input a multiple of 8.
  * max_batch: a multiple of 8.  Parameters start at zero (set them with nrto_mlp_set_params). */

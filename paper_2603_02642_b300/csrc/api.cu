@@ -181,6 +181,7 @@ struct nrto_problem {
   int* d_is = nullptr;
   int* d_queue = nullptr;
   int* d_order = nullptr;
+  int* d_wsmap = nullptr;          // row map of nrto_set_warm_start_from_network
   unsigned long long* d_phase = nullptr;
   double* d_stage = nullptr;
   long long* d_stage_off = nullptr;
@@ -706,6 +707,28 @@ nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long 
 
 }  // namespace
 
+// Warm start from network outputs Y (device, n × out_dim): K from Y[i][k_off ..], p̃ and λ_p of
+// instance row r from Y[i][pt_off + map[r]] and Y[i][lp_off + map[r]] (map < 0: zero).
+template <typename Real>
+__global__ void k_scatter_warm(Dev<Real> D, const float* Y, int out_dim, const int* map, int k_off, int pt_off,
+                               int lp_off) {
+  const int i = blockIdx.x;
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  double* ar = D.arena + I.arena0;
+  const float* y = Y + (long long)i * out_dim;
+  for (int q = threadIdx.x; q < I.T * I.nu * I.nx; q += blockDim.x) ar[L.K1 + q] = (double)y[k_off + q];
+  for (int r = threadIdx.x; r < I.n_sr + I.n_cr; r += blockDim.x) {
+    const long long R = I.row0 + r;
+    const int m = map[R];
+    D.pt[R] = m >= 0 ? (double)y[pt_off + m] : 0.0;
+    D.lamp[R] = m >= 0 ? (double)y[lp_off + m] : 0.0;
+  }
+}
+
+const float* nrto_mlp_internal_forward_device(nrto_mlp_t m, const float* x, int batch, int* out_dim,
+                                              cudaStream_t* stream);   // mlp.cu
+
 // Message for nrto_last_error from the other translation units of the library.
 void nrto_internal_set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -1107,6 +1130,40 @@ nrto_status nrto_set_warm_start(nrto_problem_t p, const double* K, const double*
     CK(cudaMemcpyAsync(p->d_pt, ptilde, sizeof(double) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
     CK(cudaMemcpyAsync(p->d_lamp, lambda_p, sizeof(double) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
     CK(cudaStreamSynchronize(p->stream));
+    p->warm_pending = true;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, const float* features,
+                                            const int* row_map, int k_off, int pt_off, int lp_off) {
+  try {
+    if (!p || !m || !features || !row_map) fail(NRTO_ERR_INVALID, "null argument");
+    for (long long r = 0; r < p->n_rows; ++r)
+      if (row_map[r] < -1) fail(NRTO_ERR_INVALID, "row_map entries must be >= -1");
+    int out_dim = 0;
+    cudaStream_t ms = nullptr;
+    const float* Y = nrto_mlp_internal_forward_device(m, features, p->n, &out_dim, &ms);
+    if (!Y) return NRTO_ERR_INVALID;
+    long long kmax = 0;
+    for (int i = 0; i < p->n; ++i)
+      kmax = std::max(kmax, (long long)p->h_inst[i].T * p->h_inst[i].nu * p->h_inst[i].nx);
+    int mmax = -1;
+    for (long long r = 0; r < p->n_rows; ++r) mmax = std::max(mmax, row_map[r]);
+    if (k_off < 0 || pt_off < 0 || lp_off < 0 || k_off + kmax > out_dim || pt_off + mmax >= out_dim ||
+        lp_off + mmax >= out_dim)
+      fail(NRTO_ERR_INVALID, "offsets and row map do not fit the network output");
+    if (!p->d_wsmap) p->d_wsmap = p->dalloc<int>(p->n_rows);
+    CK(cudaMemcpyAsync(p->d_wsmap, row_map, sizeof(int) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(ms));   // network output ready
+    if (p->prec == NRTO_PREC_FP64)
+      k_scatter_warm<double><<<p->n, 256, 0, p->stream>>>(p->dev<double>(), Y, out_dim, p->d_wsmap, k_off, pt_off, lp_off);
+    else
+      k_scatter_warm<float><<<p->n, 256, 0, p->stream>>>(p->dev<float>(), Y, out_dim, p->d_wsmap, k_off, pt_off, lp_off);
+    p->check_launch("k_scatter_warm");
+    CK(cudaStreamSynchronize(p->stream));   // the network's output buffer may be reused after return
     p->warm_pending = true;
     return NRTO_OK;
   } catch (const std::exception& e) {

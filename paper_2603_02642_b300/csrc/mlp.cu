@@ -641,6 +641,31 @@ nrto_status nrto_mlp_train_step(nrto_mlp_t m, const float* x, const float* targe
 
 long long nrto_mlp_kernel_launches(nrto_mlp_t m) { return m ? m->launches : -1; }
 
+}  // extern "C"
+
+// For the library's own use (warm start from the network): forward of a host batch with the output
+// left on the device (stream-ordered on the network's stream).  Returns null on error (message set).
+const float* nrto_mlp_internal_forward_device(nrto_mlp_t m, const float* x, int batch, int* out_dim,
+                                              cudaStream_t* stream) {
+  try {
+    if (!m || !x) mfail(NRTO_ERR_INVALID, "null argument");
+    if (batch < 1 || batch > m->max_batch) mfail(NRTO_ERR_INVALID, "batch exceeds the network's max_batch");
+    MK(cudaMemcpyAsync(m->stage_in, x, sizeof(float) * (size_t)batch * m->dims[0], cudaMemcpyHostToDevice, m->stream));
+    k_to_bf16_pad<<<512, 256, 0, m->stream>>>(m->stage_in, batch, m->dims[0], m->X, m->in_pad);
+    MK(cudaGetLastError());
+    ++m->launches;
+    m->forward(batch);
+    *out_dim = m->dims[m->L];
+    *stream = m->stream;
+    return m->Y;
+  } catch (const MlpError& e) {
+    nrto_mlp_set_error_internal(e);
+    return nullptr;
+  }
+}
+
+extern "C" {
+
 nrto_status nrto_mlp_profile(nrto_mlp_t m, int enable, double* gemm_ms, double* gemm_flops, long long* gemm_launches) {
   try {
     if (!m) mfail(NRTO_ERR_INVALID, "null network");

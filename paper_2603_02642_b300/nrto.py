@@ -93,6 +93,8 @@ def load():
     lib.nrto_mlp_get_params.argtypes = [P, _fp]
     lib.nrto_mlp_forward.argtypes = [P, _fp, C.c_int, _fp]
     lib.nrto_mlp_train_step.argtypes = [P, _fp, _fp, _fp, C.c_int, C.c_float, _dp, _fp]
+    lib.nrto_set_warm_start_from_network.argtypes = [P, P, C.POINTER(C.c_float), _ip, C.c_int, C.c_int, C.c_int]
+    lib.nrto_set_warm_start_from_network.restype = C.c_int
     lib.nrto_mlp_profile.argtypes = [P, C.c_int, _dp, _dp, C.POINTER(C.c_longlong)]
     lib.nrto_mlp_profile.restype = C.c_int
     lib.nrto_mlp_kernel_launches.argtypes = [P]
@@ -286,6 +288,14 @@ class Problem:
         pt = np.ascontiguousarray(np.concatenate([np.asarray(k).reshape(-1) for k in pt]))
         lp = np.ascontiguousarray(np.concatenate([np.asarray(k).reshape(-1) for k in lam_p]))
         _check(load().nrto_set_warm_start(self._h, _ptr(K), _ptr(pt), _ptr(lp)))
+
+    def set_warm_start_from_network(self, net, features, row_map, k_off, pt_off, lp_off):
+        """Network forward on the device and scatter into the next inner solve's (K, p̃, λ_p)."""
+        f = np.ascontiguousarray(np.asarray(features, dtype=np.float32))
+        m = np.ascontiguousarray(np.asarray(row_map, dtype=np.int32))
+        assert f.shape[0] == self.n and m.size == self.n_rows()
+        _check(load().nrto_set_warm_start_from_network(self._h, net._h, f.ctypes.data_as(C.POINTER(C.c_float)),
+                                                       m.ctypes.data_as(_ip), int(k_off), int(pt_off), int(lp_off)))
 
     def export(self, field, i):
         n = int(self._COUNTS[field](self.info[i]))

@@ -146,7 +146,15 @@ class WarmStart:
         return out
 
     def apply(self, prob, insts):
-        """Predict and install the warm start of the problem's next inner solve."""
+        """Install the network's warm start for the problem's next inner solve: the forward pass and
+        the scatter into each instance's (K, p̃, λ_p) run on the device."""
+        if not self.deployed:
+            raise RuntimeError("fit() the network first")
+        row_map = np.concatenate([row_index(inst) for inst in insts]).astype(np.int32)
+        prob.set_warm_start_from_network(self.net, features(insts), row_map, 0, N_K, N_K + N_ROWS)
+
+    def apply_host(self, prob, insts):
+        """Same warm start through host arrays (predict, then nrto_set_warm_start)."""
         pred = self.predict(insts)
         K = np.concatenate([p[0].reshape(-1) for p in pred])
         pt = np.concatenate([p[1] for p in pred])

@@ -48,3 +48,21 @@ def test_learned_warm_start_gains_over_cold_start():
     assert conv_w.sum() >= conv_c.sum()
     assert ratio < 0.9
     ws.net.close()
+
+
+def test_device_warm_start_equals_host_path():
+    """nrto_set_warm_start_from_network installs exactly what predict + nrto_set_warm_start does."""
+    insts = [W.warmstart_quad(3_000_000 + s) for s in range(16)]
+    ws = WS.WarmStart(max_batch=64, seed=4)
+    ws.deployed = True          # untrained network: the mapping, not the values, is under test
+    outs = []
+    for apply in (ws.apply, ws.apply_host):
+        prob = nrto.Problem(insts, nrto.PREC_FP64)
+        prob.linearize()
+        apply(prob, insts)
+        prob.solve_socp(nrto.Options(rho=10.0, max_inner=1, check=0))
+        outs.append([(prob.export(nrto.F_K, i), prob.export(nrto.F_LAMP, i)) for i in range(len(insts))])
+        prob.close()
+    for (ka, la), (kb, lb) in zip(*outs):
+        assert np.array_equal(ka, kb) and np.array_equal(la, lb)
+    ws.net.close()
