@@ -465,7 +465,7 @@ template <typename Real>
 void choose_chunk(KindLaunch& kl) {
   const int nx = kind_nx(kl.kind);
   const int minc = ((kl.tmax + 1) * nx + 3) & ~3;
-  int chunk = 6144;
+  int chunk = 12288;
   while (chunk > minc && smem_for<Real>(kl.kind, chunk, chunk / (2 * nx) + 2) > (size_t)smem_budget<Real>()) chunk -= 256;
   if (chunk < minc) chunk = minc;
   kl.chunk = chunk;

@@ -669,24 +669,31 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
       for (int w = 0; w < W; ++w) z[k][u][w] = (Real)0;
   Real arp = 0, ard = 0;
   // ---------------- row pass over state rows, chunk by chunk (bulk copies, double buffered) --------
+  // Thread 0 waits for a chunk's copies before the block barrier that precedes its use: for chunk 0
+  // here, for chunk ch+1 at the end of chunk ch, where that barrier also frees chunk ch's buffer.
+  auto wait_chunk = [&](int c) {
+    if (tid == 0) {
+      const long long tw = clock64();
+      *s_flag = mbar_wait_bounded(&bars[c & 1], phase[c & 1]) ? 1 : 0;
+      if (wait_cycles) *wait_cycles += (unsigned long long)(clock64() - tw);
+    }
+  };
   __syncthreads();
   if (tid == 0) {
     fence_proxy_async();
     for (int c0 = 0; c0 < 2 && c0 < I.n_chunks; ++c0) issue_chunk<NX, NU, Real>(D, S, I, chunks[c0], sm.buf[c0], &bars[c0]);
+  }
+  if (I.n_chunks > 0) {
+    wait_chunk(0);
+    __syncthreads();
+    phase[0] ^= 1u;
+    if (*s_flag == 0) return false;
   }
   for (int ch = 0; ch < I.n_chunks; ++ch) {
     const int bi = ch & 1;
     const typename FASmem<NX, NU, Real>::Buf bf = sm.buf[bi];
     const ChunkInfo cki = chunks[ch];
     const int nr = cki.r1 - cki.r0;
-    if (tid == 0) {
-      const long long tw = clock64();
-      *s_flag = mbar_wait_bounded(&bars[bi], phase[bi]) ? 1 : 0;
-      if (wait_cycles) *wait_cycles += (unsigned long long)(clock64() - tw);
-    }
-    __syncthreads();
-    phase[bi] ^= 1u;
-    if (*s_flag == 0) return false;
     // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms (row group `grp`
     // takes rows grp, grp+NG, ...)
     for (int q = grp; q < nr; q += NG) {
@@ -774,7 +781,12 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
         }
       }
     }
+    if (ch + 1 < I.n_chunks) wait_chunk(ch + 1);
     __syncthreads();
+    if (ch + 1 < I.n_chunks) {
+      phase[bi ^ 1] ^= 1u;
+      if (*s_flag == 0) return false;
+    }
     if (tid == 0 && ch + 2 < I.n_chunks) {
       fence_proxy_async();
       issue_chunk<NX, NU, Real>(D, S, I, chunks[ch + 2], bf, &bars[bi]);
