@@ -41,6 +41,9 @@ struct SolveParams {
 #ifndef NRTO_FA_NT_F32
 #define NRTO_FA_NT_F32 512
 #endif
+#ifndef NRTO_FA_RB
+#define NRTO_FA_RB 4
+#endif
 #ifndef NRTO_FA_MINB_F32
 #define NRTO_FA_MINB_F32 1
 #endif
@@ -57,6 +60,7 @@ struct FACfg {
   static constexpr int NPAIR_MAX = TMAXC / 2 + 1;        // block pairs of the longest horizon
   static constexpr int TPG_MAX = (NPAIR_MAX * NCG + 31) / 32 * 32;   // threads of one row group
   static constexpr int NWR_MAX = TPG_MAX / 32;           // warps of a row group (partial row norms)
+  static constexpr int RB = NRTO_FA_RB;                  // rows per warp reduction in sub-pass 1
 };
 
 // Column ownership in the row pass for an instance of horizon T.  Rows at time t hold blocks
@@ -94,6 +98,35 @@ __device__ __forceinline__ ColMap col_map(int T, int zcap) {
   return cm;
 }
 
+// Sums RB per-lane values over the warp in one butterfly: the first log2(RB) levels halve the set
+// of values each lane carries (a lane keeps the half selected by its lane bit and sends the other),
+// the remaining levels are a plain butterfly.  Lanes [r·32/RB, (r+1)·32/RB) return the sum of
+// v[r]; every sum uses the same pairing tree as warp_sum.
+template <int RB, typename T>
+__device__ __forceinline__ T warp_sum_rows(const T (&v)[RB], int lane) {
+  static_assert(RB == 1 || RB == 2 || RB == 4, "RB must be 1, 2 or 4");
+  if constexpr (RB == 1) {
+    return warp_sum(v[0]);
+  } else if constexpr (RB == 2) {
+    const bool hi = (lane & 16) != 0;
+    T a = hi ? v[1] : v[0];
+    a += __shfl_xor_sync(0xffffffffu, hi ? v[0] : v[1], 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+  } else {
+    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
+    T a0 = h4 ? v[2] : v[0], a1 = h4 ? v[3] : v[1];
+    a0 += __shfl_xor_sync(0xffffffffu, h4 ? v[0] : v[2], 16);
+    a1 += __shfl_xor_sync(0xffffffffu, h4 ? v[1] : v[3], 16);
+    T a = h3 ? a1 : a0;
+    a += __shfl_xor_sync(0xffffffffu, h3 ? a0 : a1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+  }
+}
+
 // Supplementary Sec. II-C closed form: (t̂, η̂) ↦ (p̃, s·η̂), a = ‖η̂‖
 __device__ __forceinline__ void soc_case(double tt, double a, double& s_new, double& pt_new) {
   if (a <= tt) { s_new = 1.0; pt_new = tt; }
@@ -113,7 +146,10 @@ template <int NX, int NU, typename Real>
 struct FASmem {
   struct Buf {
     Real* lam; Real* bhat; Real* bb; RowMeta* meta;
+    Real* so;   // the chunk's row scales s_j (storage order) from a 16-byte-aligned window
   };
+  // elements of the row-scale window in front of a chunk's first row
+  static constexpr int SO_ALIGN = 16 / (int)sizeof(Real);
   Buf buf[2];
   Real* rowpart;   // [max_rows][NWR_MAX] warp partial norms
   Real* snew;      // [max_rows]
@@ -127,6 +163,7 @@ struct FASmem {
     b += align16((size_t)(chunk + 4) * sizeof(Real));            // bhat
     b += align16((size_t)(chunk / NX * NU + 8) * sizeof(Real));  // b
     b += align16((size_t)max_rows * sizeof(RowMeta));            // meta
+    b += align16((size_t)(max_rows + 2 * SO_ALIGN) * sizeof(Real));   // row scales
     return b;
   }
   NRTO_HD static size_t bytes(int chunk, int max_rows) {
@@ -148,6 +185,7 @@ struct FASmem {
       buf[k].bhat = reinterpret_cast<Real*>(take((size_t)(chunk + 4) * sizeof(Real)));
       buf[k].bb = reinterpret_cast<Real*>(take((size_t)(chunk / NX * NU + 8) * sizeof(Real)));
       buf[k].meta = reinterpret_cast<RowMeta*>(take((size_t)max_rows * sizeof(RowMeta)));
+      buf[k].so = reinterpret_cast<Real*>(take((size_t)(max_rows + 2 * SO_ALIGN) * sizeof(Real)));
     }
     rowpart = reinterpret_cast<Real*>(take((size_t)max_rows * FACfg<NX, NU, Real>::NWR_MAX * sizeof(Real)));
     snew = reinterpret_cast<Real*>(take((size_t)max_rows * sizeof(Real)));
@@ -157,17 +195,28 @@ struct FASmem {
 };
 
 // Issue the bulk copies of one chunk into a buffer (one thread): the entry ranges of λ and b̂,
-// the b range, and the chunk's row metadata (state rows in storage order, logical index in .pad).
+// the b range, the chunk's row metadata (state rows in storage order, logical index in .pad) and
+// its row scales.  The row scales are kept in storage order; their window starts at the 16-byte
+// boundary at or before the chunk's first row (so_offset() elements earlier) and is rounded up to a
+// 16-byte multiple, which stays inside the array's 4-element tail padding.
+template <int NX, int NU, typename Real>
+__device__ __forceinline__ int so_offset(const Inst& I, const ChunkInfo& ck) {
+  return (int)((I.row0 + ck.r0) & (FASmem<NX, NU, Real>::SO_ALIGN - 1));
+}
 template <int NX, int NU, typename Real>
 __device__ void issue_chunk(const Dev<Real>& D, const LinSlot<Real>& S, const Inst& I, const ChunkInfo& ck,
                             const typename FASmem<NX, NU, Real>::Buf& bf, uint64_t* bar) {
+  constexpr int A = FASmem<NX, NU, Real>::SO_ALIGN;
+  const int nr = ck.r1 - ck.r0, so0 = so_offset<NX, NU, Real>(I, ck);
   const uint32_t bl = (uint32_t)(ck.ne * sizeof(Real)), bbb = (uint32_t)(ck.nb * sizeof(Real));
-  const uint32_t bm = (uint32_t)((ck.r1 - ck.r0) * sizeof(RowMeta));
-  mbar_arrive_expect_tx(bar, 2 * bl + bbb + bm);
+  const uint32_t bm = (uint32_t)(nr * sizeof(RowMeta));
+  const uint32_t bs = (uint32_t)(((so0 + nr + A - 1) & ~(A - 1)) * sizeof(Real));
+  mbar_arrive_expect_tx(bar, 2 * bl + bbb + bm + bs);
   bulk_g2s(bf.lam, D.lam + ck.e0, bl, bar);
   bulk_g2s(bf.bhat, S.bhat + ck.e0, bl, bar);
   bulk_g2s(bf.bb, S.bvec + ck.b0, bbb, bar);
   bulk_g2s(bf.meta, D.rmeta + I.row0 + ck.r0, bm, bar);
+  bulk_g2s(bf.so, D.sr + (I.row0 + ck.r0 - so0), bs, bar);
 }
 
 // Per-step gain solve, parallel over (m, u, c) in four phases through arena scratch:
@@ -643,7 +692,7 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
                                          bool first, bool block1, Real lscale, Real* arp_out, Real* ard_out,
                                          unsigned long long* wait_cycles) {
   using C = FACfg<NX, NU, Real>;
-  constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR_MAX = C::NWR_MAX, W = C::W;
+  constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR_MAX = C::NWR_MAX, W = C::W, RB = C::RB;
   const int T = I.T, tid = threadIdx.x, lane = tid & 31;
   const int grp = cm.grp, NG = cm.ng, NWR = cm.nwr, ck = cm.ck;
   const int gwarp = (tid - (grp < NG ? grp : 0) * NWR * 32) >> 5;
@@ -694,53 +743,64 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
     const typename FASmem<NX, NU, Real>::Buf bf = sm.buf[bi];
     const ChunkInfo cki = chunks[ch];
     const int nr = cki.r1 - cki.r0;
-    // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms (row group `grp`
-    // takes rows grp, grp+NG, ...)
-    for (int q = grp; q < nr; q += NG) {
-      const RowMeta rm = bf.meta[q];
-      const Real so = sr[row0 + rm.pad];
-      Real pn = 0;
-      bool act = false;
+    const Real* const so_s = bf.so + so_offset<NX, NU, Real>(I, cki);
+    // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms.  Row group `grp` takes
+    // rows grp, grp+NG, ...; a warp runs RB rows back to back and reduces their partial norms together
+    // (one transposing butterfly), so the rows' reduction latencies overlap.
+    for (int q0 = grp; q0 < nr; q0 += RB * NG) {
+      Real pnv[RB];
 #pragma unroll
-      for (int k = 0; k < PAIRS; ++k) {
-        if (mk[k] <= rm.t) {
-          act = true;
-          const int e = rm.off + mk[k] * NX + ck;
-          Real bv[NU], yb[W], l[W], lg[W];
-          ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
-          ld_vec<W, Real>(bf.bhat + e, yb);
-          ld_vec<W, Real>(bf.lam + e, l);
+      for (int r = 0; r < RB; ++r) {
+        const int q = q0 + r * NG;
+        pnv[r] = (Real)0;
+        if (q >= nr) continue;
+        const RowMeta rm = bf.meta[q];
+        const Real so = so_s[q];
+        Real pn = 0;
 #pragma unroll
-          for (int w = 0; w < W; ++w) {
-            Real y = yb[w];
+        for (int k = 0; k < PAIRS; ++k) {
+          if (mk[k] <= rm.t) {
+            const int e = rm.off + mk[k] * NX + ck;
+            Real bv[NU], yb[W], l[W], lg[W];
+            ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
+            ld_vec<W, Real>(bf.bhat + e, yb);
+            ld_vec<W, Real>(bf.lam + e, l);
 #pragma unroll
-            for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
-            if (!first) {
-              Real yo = yb[w];
+            for (int w = 0; w < W; ++w) {
+              Real y = yb[w];
 #pragma unroll
-              for (int u = 0; u < NU; ++u) yo += go[k][u][w] * bv[u];
-              const Real nu = so * (yo + l[w]);
-              const Real ln = l[w] + y - nu;
-              arp += (y - nu) * (y - nu);
-              ard += (y - yo) * (y - yo);
-              l[w] = ln * lscale;
+              for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
+              if (!first) {
+                Real yo = yb[w];
+#pragma unroll
+                for (int u = 0; u < NU; ++u) yo += go[k][u][w] * bv[u];
+                const Real nu = so * (yo + l[w]);
+                const Real ln = l[w] + y - nu;
+                arp += (y - nu) * (y - nu);
+                ard += (y - yo) * (y - yo);
+                l[w] = ln * lscale;
+              }
+              const Real et = y + l[w];
+              pn += et * et;
+              lg[w] = l[w];
+              yb[w] += l[w];     // b̂ + λ, kept for sub-pass 2
+              l[w] = et;         // η̂, kept for sub-pass 2
             }
-            const Real et = y + l[w];
-            pn += et * et;
-            lg[w] = l[w];
-            yb[w] += l[w];     // b̂ + λ, kept for sub-pass 2
-            l[w] = et;         // η̂, kept for sub-pass 2
-          }
-          if (!first) st_vec<W, Real>(lam + cki.e0 + e, lg);
-          if (block1) {
-            st_vec<W, Real>(bf.lam + e, l);
-            st_vec<W, Real>(bf.bhat + e, yb);
+            if (!first) st_vec<W, Real>(lam + cki.e0 + e, lg);
+            if (block1) {
+              st_vec<W, Real>(bf.lam + e, l);
+              st_vec<W, Real>(bf.bhat + e, yb);
+            }
           }
         }
+        pnv[r] = pn;
       }
       if (block1) {
-        if (__any_sync(0xffffffffu, act)) pn = warp_sum(pn);
-        if (lane == 0) rowpart[q * NWR_MAX + gwarp] = pn;
+        // lanes [r·32/RB, (r+1)·32/RB) end with the warp's sum for row q0 + r·NG
+        const Real tot = warp_sum_rows<RB>(pnv, lane);
+        const int r = lane / (32 / RB);
+        const int q = q0 + r * NG;
+        if ((lane & (32 / RB - 1)) == 0 && q < nr) rowpart[q * NWR_MAX + gwarp] = tot;
       }
     }
     __syncthreads();
@@ -754,7 +814,7 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
         soc_case_r<Real>((Real)(parr[R] + lamparr[R]), sqrt(a2), snew, ptn);
         snew_s[q] = snew;
         sarr[R] = (double)snew;
-        sr[R] = snew;
+        sr[row0 + cki.r0 + q] = snew;   // storage order: the next iteration's chunk copy brings it
         ptnarr[R] = (double)ptn;
       }
       __syncthreads();

@@ -145,7 +145,8 @@ struct Dev {
   const int2* groups;           // control groups: {first global row, count}, per instance at grp0
   LinSlot<Real> slot[2];
   Real* lam;                    // λ_ν or η̃ rows
-  Real* sr;                     // per row: projection scale s_j in the compute precision (FullADMM row pass)
+  Real* sr;                     // per row: projection scale s_j in the compute precision (FullADMM row pass;
+                                // state rows in their chunk storage order), 4 elements of tail padding
   double *p, *pt, *ptn, *lamp, *w, *lamw, *s, *ell, *dd, *rnorm;   // per row
   double* sc;                   // NSC per instance
   int* is;                      // NIS per instance
