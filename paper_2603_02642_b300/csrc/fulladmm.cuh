@@ -684,12 +684,13 @@ struct PhaseTimer {
 // η̂ = Â_j k + b̂_j + λ_ν,j, the projection gives each row's scale s_j and p̃_j, and sub-pass 2
 // accumulates Z'_m = Σ_j b_{j,m} w_{j,m}ᵀ.  Pointers are hoisted into registers and the chunk
 // buffer descriptors copied per chunk, so the loops touch only registers and shared memory besides
-// the row data.  Returns false if a chunk copy timed out.
-template <int NX, int NU, typename Real>
+// the row data.  `first` (iteration 1: no λ update) is a template parameter so that the common path
+// carries no code or registers of the other.  Returns false if a chunk copy timed out.
+template <int NX, int NU, typename Real, bool first>
 __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Real>& S, const Inst& I,
                                          FASmem<NX, NU, Real>& sm, uint64_t* bars, uint32_t* phase, int* s_flag,
                                          const ColMap cm, const double* gtc, const double* gto, double* Zp,
-                                         bool first, bool block1, Real lscale, Real* arp_out, Real* ard_out,
+                                         bool block1, Real lscale, Real* arp_out, Real* ard_out,
                                          unsigned long long* wait_cycles) {
   using C = FACfg<NX, NU, Real>;
   constexpr int NT = C::NT, PAIRS = C::PAIRS, NWR_MAX = C::NWR_MAX, W = C::W, RB = C::RB;
@@ -730,7 +731,8 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
   __syncthreads();
   if (tid == 0) {
     fence_proxy_async();
-    for (int c0 = 0; c0 < 2 && c0 < I.n_chunks; ++c0) issue_chunk<NX, NU, Real>(D, S, I, chunks[c0], sm.buf[c0], &bars[c0]);
+    if (I.n_chunks > 0) issue_chunk<NX, NU, Real>(D, S, I, chunks[0], sm.buf[0], &bars[0]);
+    if (I.n_chunks > 1) issue_chunk<NX, NU, Real>(D, S, I, chunks[1], sm.buf[1], &bars[1]);
   }
   if (I.n_chunks > 0) {
     wait_chunk(0);
@@ -740,7 +742,9 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
   }
   for (int ch = 0; ch < I.n_chunks; ++ch) {
     const int bi = ch & 1;
-    const typename FASmem<NX, NU, Real>::Buf bf = sm.buf[bi];
+    // selected with constant indices: a run-time index would move the descriptors to local memory
+    // and the compiler would lose that they point to shared memory
+    const typename FASmem<NX, NU, Real>::Buf bf = bi ? sm.buf[1] : sm.buf[0];
     const ChunkInfo cki = chunks[ch];
     const int nr = cki.r1 - cki.r0;
     const Real* const so_s = bf.so + so_offset<NX, NU, Real>(I, cki);
@@ -981,8 +985,13 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     }
 
     // ---------------- row pass over state rows (bulk copies, double buffered) ----------------
-    if (!fa_row_pass<NX, NU, Real>(D, S, I, sm, bars, phase, s_flag, cm, gtc_arena, gto_arena, ar + L.Zp, first, block1,
-                                   lscale, &arp, &ard, tm.on ? &tm.acc[PH_WAIT] : nullptr)) {
+    unsigned long long* const wc = tm.on ? &tm.acc[PH_WAIT] : nullptr;
+    const bool rows_ok =
+        first ? fa_row_pass<NX, NU, Real, true>(D, S, I, sm, bars, phase, s_flag, cm, gtc_arena, gto_arena, ar + L.Zp,
+                                                block1, lscale, &arp, &ard, wc)
+              : fa_row_pass<NX, NU, Real, false>(D, S, I, sm, bars, phase, s_flag, cm, gtc_arena, gto_arena, ar + L.Zp,
+                                                 block1, lscale, &arp, &ard, wc);
+    if (!rows_ok) {
       status = ST_TIMEOUT;
       goto done;
     }
