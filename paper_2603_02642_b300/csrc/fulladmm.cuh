@@ -140,6 +140,21 @@ __device__ __forceinline__ void soc_case_r(Real tt, Real a, Real& s_new, Real& p
   else { pt_new = (Real)0.5 * (tt + a); s_new = pt_new / a; }
 }
 
+// Per-warp shared scratch of the FullADMM gain solve (gain_solve_warps): the step's operands and
+// two intermediates, in compute precision.
+template <int NX, int NU, typename Real>
+struct GainScratch {
+  static constexpr int NE = NU * NX;
+  static constexpr int oPhi = 0, oU = NX * NX, oPf = 2 * NX * NX, oDv = oPf + NU * NU, oZ = oDv + NE;
+  static constexpr int oY = oZ + NE, oX = oY + NE, PER_WARP = (oX + NE + 3) / 4 * 4;   // values per warp
+  // gain warps whose scratch fits in about 32 KB (at least one)
+  static constexpr int warps(int avail) {
+    const int cap = (int)((32 * 1024) / (PER_WARP * sizeof(Real)));
+    const int w = avail < cap ? avail : cap;
+    return w > 0 ? w : 1;
+  }
+};
+
 // Shared memory of one CTA: two chunk buffers plus per-chunk scratch.  Host and device use the
 // same size function.
 template <int NX, int NU, typename Real>
@@ -151,12 +166,18 @@ struct FASmem {
   // elements of the row-scale window in front of a chunk's first row
   static constexpr int SO_ALIGN = 16 / (int)sizeof(Real);
   Buf buf[2];
-  Real* rowpart;   // [max_rows][NWR_MAX] warp partial norms
+  Real* rowpart;   // [max_rows][NWR_MAX] warp partial norms; in block 2 the gain solve's per-warp scratch
   Real* snew;      // [max_rows]
   double* red;     // block reductions
   double* vec;     // Riccati sweep vector
 
   NRTO_HD static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+  NRTO_HD static size_t rowpart_count(int max_rows) {
+    using G = GainScratch<NX, NU, Real>;
+    const size_t a = (size_t)max_rows * FACfg<NX, NU, Real>::NWR_MAX;
+    const size_t g = (size_t)G::warps(FACfg<NX, NU, Real>::NW - 1) * G::PER_WARP;
+    return a > g ? a : g;
+  }
   NRTO_HD static size_t buf_bytes(int chunk, int max_rows) {
     size_t b = 0;
     b += align16((size_t)(chunk + 4) * sizeof(Real));            // lam
@@ -168,7 +189,7 @@ struct FASmem {
   }
   NRTO_HD static size_t bytes(int chunk, int max_rows) {
     size_t b = 2 * buf_bytes(chunk, max_rows);
-    b += align16((size_t)max_rows * FACfg<NX, NU, Real>::NWR_MAX * sizeof(Real));
+    b += align16(rowpart_count(max_rows) * sizeof(Real));
     b += align16((size_t)max_rows * sizeof(Real));
     b += (4 * FACfg<NX, NU, Real>::NW + 4 * 16) * sizeof(double);
     return b;
@@ -187,7 +208,7 @@ struct FASmem {
       buf[k].meta = reinterpret_cast<RowMeta*>(take((size_t)max_rows * sizeof(RowMeta)));
       buf[k].so = reinterpret_cast<Real*>(take((size_t)(max_rows + 2 * SO_ALIGN) * sizeof(Real)));
     }
-    rowpart = reinterpret_cast<Real*>(take((size_t)max_rows * FACfg<NX, NU, Real>::NWR_MAX * sizeof(Real)));
+    rowpart = reinterpret_cast<Real*>(take(rowpart_count(max_rows) * sizeof(Real)));
     snew = reinterpret_cast<Real*>(take((size_t)max_rows * sizeof(Real)));
     red = reinterpret_cast<double*>(c);
     vec = red + 4 * FACfg<NX, NU, Real>::NW;
@@ -290,6 +311,104 @@ __device__ __noinline__ void gain_solve(double* ar, const Arena& L, int T, doubl
   }
   for (int q = me; q < NU * NX; q += nthr) gt_out[(long long)T * NU * NX + q] = 0.0;
   group_sync(bar_id, nthr);
+}
+
+// The FullADMM gain solve (coefK = 0) with one warp per step: warps w0 .. w0+nw-1 take steps
+// m = w - w0, w - w0 + nw, ...  A warp first stages its step's operands (Z', Φ, U = Σ_U, P_f, D_v)
+// into its shared scratch as compute-precision values with coalesced, independent loads, then runs
+// the four products of gain_solve from shared memory, so no block-wide barrier separates them and
+// each operand costs one memory latency per step.  Every element is summed in the same order as in
+// gain_solve from the same compute-precision values, so the results are identical.
+
+template <int NX, int NU, typename Real>
+__device__ __forceinline__ void gain_solve_warps(const double* ar, const Arena& L, int T, double sqrt_tau, double coefA,
+                                                 double* Kout, double* gt_out, int w0, int nw, Real* scr) {
+  using G = GainScratch<NX, NU, Real>;
+  constexpr int NE = G::NE, EPL = (NE + 31) / 32;
+  const int lane = threadIdx.x & 31, wv = (int)(threadIdx.x >> 5) - w0;
+  if (wv < 0 || wv >= nw) return;
+  Real* const sw = scr + (size_t)wv * G::PER_WARP;
+  Real* const sPhi = sw + G::oPhi;
+  Real* const sU = sw + G::oU;
+  Real* const sPf = sw + G::oPf;
+  Real* const sDv = sw + G::oDv;
+  Real* const sZ = sw + G::oZ;
+  Real* const Y = sw + G::oY;   // Y, then PX
+  Real* const X = sw + G::oX;
+  const Real cA = (Real)coefA, st = (Real)sqrt_tau;
+  for (int m = wv; m < T; m += nw) {
+    {
+      const double* Phi = ar + L.Phi + (long long)m * NX * NX;
+      const double* U = ar + L.SigU + (long long)m * NX * NX;
+      const double* Pf = ar + L.Pf + (long long)m * NU * NU;
+      const double* Dv = ar + L.Dv + (long long)m * NE;
+      const double* Zp = ar + L.Zp + (long long)m * NE;
+      for (int q = lane; q < NX * NX; q += 32) { sPhi[q] = (Real)Phi[q]; sU[q] = (Real)U[q]; }
+      for (int q = lane; q < NU * NU; q += 32) sPf[q] = (Real)Pf[q];
+      for (int q = lane; q < NE; q += 32) { sDv[q] = (Real)Dv[q]; sZ[q] = (Real)Zp[q]; }
+    }
+    __syncwarp();
+    // Y = coefA Z' Φ
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+      const int e = lane + 32 * i;
+      if (e < NE) {
+        const int u = e / NX, c = e - u * NX;
+        Real acc = 0;
+#pragma unroll
+        for (int r = 0; r < NX; ++r) acc += sZ[u * NX + r] * sPhi[r * NX + c];
+        acc *= cA;
+        Y[e] = acc;
+      }
+    }
+    __syncwarp();
+    // X = (P_fᵀ Y) ⊙ D_v
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+      const int e = lane + 32 * i;
+      if (e < NE) {
+        const int u = e / NX, c = e - u * NX;
+        Real acc = 0;
+#pragma unroll
+        for (int v = 0; v < NU; ++v) acc += sPf[v * NU + u] * Y[v * NX + c];
+        X[e] = acc * sDv[e];
+      }
+    }
+    __syncwarp();
+    // PX = P_f X (into Y)
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+      const int e = lane + 32 * i;
+      if (e < NE) {
+        const int u = e / NX, c = e - u * NX;
+        Real acc = 0;
+#pragma unroll
+        for (int v = 0; v < NU; ++v) acc += sPf[u * NU + v] * X[v * NX + c];
+        Y[e] = acc;
+      }
+    }
+    __syncwarp();
+    // K = PX Uᵀ,  Gtᵀ = √τ PX Φᵀ
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+      const int e = lane + 32 * i;
+      if (e < NE) {
+        const int u = e / NX, c = e - u * NX;
+        Real k = 0, g = 0;
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+          const Real px = Y[u * NX + r];
+          k += px * sU[c * NX + r];
+          g += px * sPhi[c * NX + r];
+        }
+        Kout[(long long)m * NE + e] = (double)k;
+        gt_out[(long long)m * NE + e] = (double)(g * st);
+      }
+    }
+    __syncwarp();
+  }
+  if (wv == 0)
+    for (int q = lane; q < NE; q += 32) gt_out[(long long)T * NE + q] = 0.0;
 }
 
 // Block-2 (δû) LQ sweep with fixed factors (warp 0 only).  Linear terms q_t (t = 0..T, index t
@@ -463,7 +582,7 @@ struct B2Smem {
 // false if a copy did not arrive.
 template <int NX, int NU, typename Real>
 __device__ __noinline__ bool block2_sweep_and_gain(double* ar, const Arena& L, int T, const B2Smem<NX, NU, Real> b2,
-                                                   uint64_t* bars, uint32_t* phase, int* s_flag, Real* pv,
+                                                   uint64_t* bars, uint32_t* phase, int* s_flag, Real* gscr,
                                                    const double* gargs, double* Kout, double* gt_out) {
   constexpr int BW = pk_stride(NX, NU);
   constexpr int oM = NU * NU, oL = oM + NU * NX, oA = oL + NU * NX, oB = oA + NX * NX;
@@ -471,7 +590,6 @@ __device__ __noinline__ bool block2_sweep_and_gain(double* ar, const Arena& L, i
   const Real* pk = reinterpret_cast<const Real*>(ar + L.RicPk);
   const int nbs = b2.nbs;
   const int nblk = (T + nbs - 1) / nbs;
-  (void)pv;
   // one block of records [lo, hi] into ring half h (lane 0 of warp 0)
   auto issue = [&](int lo, int hi, int h) {
     const uint32_t bytes = (uint32_t)((hi - lo + 1) * BW * sizeof(Real));
@@ -504,7 +622,8 @@ __device__ __noinline__ bool block2_sweep_and_gain(double* ar, const Arena& L, i
   __syncthreads();
   bool ok = true;
   if (tid >= 32) {
-    gain_solve<NX, NU, Real>(ar, L, T, gargs[0], gargs[1], gargs[2], Kout, gt_out, 32, nthr - 32, 1);
+    gain_solve_warps<NX, NU, Real>(ar, L, T, gargs[0], gargs[1], Kout, gt_out, 1,
+                                   GainScratch<NX, NU, Real>::warps(nthr / 32 - 1), gscr);
   } else {
     // ---- backward: p_k = c_k + A_cl,kᵀ p_{k+1}; lane j < NX owns p_j ----
     Real p = (lane < NX) ? b2.qs[(size_t)T * NX + lane] : (Real)0;
@@ -921,7 +1040,6 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   // block-2 sweep areas in the chunk buffers (checked on the host to hold a ring of >= 1 step)
   B2Smem<NX, NU, Real> b2;
   b2.carve(reinterpret_cast<char*>(sm.buf[0].lam), 2 * FASmem<NX, NU, Real>::buf_bytes(sp.chunk, sp.max_rows), I.T);
-  Real* const b2pv = reinterpret_cast<Real*>(sm.vec);
 
   // ---- initialization (Algorithm 1): λ_p, λ_ν, k, p <- 0 (or a warm start of k, p̃, λ_p) ----
   for (long long e = tid; e < I.n_ent; e += NT) lam[I.ent0 + e] = (Real)0;
@@ -1108,9 +1226,9 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     // ---------------- (c) gain update and (b) Block 2, which are independent: the Riccati sweep runs
     // on warp 0 while the other warps solve for K^b (its Gtᵀ^b replaces the previous table) ----------------
     {
-      const double gargs[3] = {I.sqrt_tau, rho * I.sqrt_tau, 0.0};
+      const double gargs[2] = {I.sqrt_tau, rho * I.sqrt_tau};
       double* gt_new = ar + (gsel ? L.Gt0 : L.Gt1);
-      if (!block2_sweep_and_gain<NX, NU, Real>(ar, L, T, b2, bars, phase, s_flag, b2pv, gargs, ar + L.K1, gt_new)) {
+      if (!block2_sweep_and_gain<NX, NU, Real>(ar, L, T, b2, bars, phase, s_flag, sm.rowpart, gargs, ar + L.K1, gt_new)) {
         status = ST_TIMEOUT;
         goto done;
       }
