@@ -233,9 +233,11 @@ __device__ void issue_chunk(const Dev<Real>& D, const LinSlot<Real>& S, const In
   const uint32_t bm = (uint32_t)(nr * sizeof(RowMeta));
   const uint32_t bs = (uint32_t)(((so0 + nr + A - 1) & ~(A - 1)) * sizeof(Real));
   mbar_arrive_expect_tx(bar, 2 * bl + bbb + bm + bs);
-  bulk_g2s(bf.lam, D.lam + ck.e0, bl, bar);
-  bulk_g2s(bf.bhat, S.bhat + ck.e0, bl, bar);
-  bulk_g2s(bf.bb, S.bvec + ck.b0, bbb, bar);
+  // the row streams are read once per pass: first to leave L2
+  const uint64_t pol = l2_policy_evict_first();
+  bulk_g2s_hint(bf.lam, D.lam + ck.e0, bl, bar, pol);
+  bulk_g2s_hint(bf.bhat, S.bhat + ck.e0, bl, bar, pol);
+  bulk_g2s_hint(bf.bb, S.bvec + ck.b0, bbb, bar, pol);
   bulk_g2s(bf.meta, D.rmeta + I.row0 + ck.r0, bm, bar);
   bulk_g2s(bf.so, D.sr + (I.row0 + ck.r0 - so0), bs, bar);
 }
@@ -778,6 +780,24 @@ __device__ __forceinline__ void st_vec(Real* p, const Real (&v)[N]) {
   }
 }
 
+// Global store of N consecutive values with an L2 cache policy (the λ stream of the row pass is
+// written once per pass and marked first to evict).
+template <int N, typename Real>
+__device__ __forceinline__ void st_vec_stream(Real* p, const Real (&v)[N], uint64_t pol) {
+  if constexpr (N == 2 && sizeof(Real) == 4) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"((float)v[0]), "f"((float)v[1]), "l"(pol)
+                 : "memory");
+  } else if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p + i), "f"((float)v[i]), "l"(pol) : "memory");
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p + i), "d"((double)v[i]), "l"(pol) : "memory");
+  }
+}
+
 // Phase timer: thread 0 accumulates the SM cycles between consecutive marks (taken right after block
 // barriers) and adds them to the global counters at the end of the instance.
 struct PhaseTimer {
@@ -837,6 +857,7 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
 #pragma unroll
       for (int w = 0; w < W; ++w) z[k][u][w] = (Real)0;
   Real arp = 0, ard = 0;
+  const uint64_t spol = l2_policy_evict_first();
   // ---------------- row pass over state rows, chunk by chunk (bulk copies, double buffered) --------
   // Thread 0 waits for a chunk's copies before the block barrier that precedes its use: for chunk 0
   // here, for chunk ch+1 at the end of chunk ch, where that barrier also frees chunk ch's buffer.
@@ -909,7 +930,7 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
               yb[w] += l[w];     // b̂ + λ, kept for sub-pass 2
               l[w] = et;         // η̂, kept for sub-pass 2
             }
-            if (!first) st_vec<W, Real>(lam + cki.e0 + e, lg);
+            if (!first) st_vec_stream<W, Real>(lam + cki.e0 + e, lg, spol);
             if (block1) {
               st_vec<W, Real>(bf.lam + e, l);
               st_vec<W, Real>(bf.bhat + e, yb);
@@ -1127,8 +1148,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
         const long long e0 = D.rent[R];
         const Real sold = (Real)D.s[R];
         Real et[NX], lv[NX];
-        Real an = 0;
-        double lrp = 0, lrd = 0;
+        Real an = 0, lrp = 0, lrd = 0;   // per-row sums in the compute precision, like the state rows
 #pragma unroll
         for (int c = 0; c < NX; ++c) {
           const Real y = sg * (Real)gtc_arena[(long long)k * NU * NX + iu * NX + c];
@@ -1137,8 +1157,8 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
             const Real yo = sg * (Real)gto_arena[(long long)k * NU * NX + iu * NX + c];
             const Real nu = sold * (yo + l);
             const Real ln = l + y - nu;
-            lrp += (double)((y - nu) * (y - nu));
-            lrd += (double)((y - yo) * (y - yo));
+            lrp += (y - nu) * (y - nu);
+            lrd += (y - yo) * (y - yo);
             l = ln * lscale;
             lam[e0 + c] = l;
           }
@@ -1146,14 +1166,15 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
           et[c] = y + l;
           an += et[c] * et[c];
         }
-        prp += lrp; prd += lrd;
+        prp += (double)lrp; prd += (double)lrd;
         if (block1) {
-          double snew, ptn;
-          soc_case(D.p[R] + D.lamp[R], sqrt((double)an), snew, ptn);
-          D.s[R] = snew; D.ptn[R] = ptn;
+          // the cone in the compute precision (FP32 cones in mixed mode), as for the state rows
+          Real snew, ptn;
+          soc_case_r<Real>((Real)(D.p[R] + D.lamp[R]), sqrt(an), snew, ptn);
+          D.s[R] = (double)snew; D.ptn[R] = (double)ptn;
 #pragma unroll
           for (int c = 0; c < NX; ++c)
-            ar[L.Zp + (long long)k * NU * NX + iu * NX + c] += (double)(sg * ((Real)snew * et[c] - lv[c]));
+            ar[L.Zp + (long long)k * NU * NX + iu * NX + c] += (double)(sg * (snew * et[c] - lv[c]));
         }
       }
     }
