@@ -1137,44 +1137,92 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     __syncthreads();
     tm.mark(PH_ROWS);
     // ---------------- control rows (one block each; b = ±e_i, b̂ = 0) ----------------
+    // A group holds the rows of one (k, i), upper before lower bound, which update the same Z'
+    // elements; a thread takes whole groups.  For the common two-row group the loads of both rows
+    // are issued together, in few dependent rounds: each round trip costs a full memory latency while
+    // the row streams keep the memory system loaded.  Both paths update Z' and the residual sums row
+    // after row, in the same order.
     double prp = (double)arp, prd = (double)ard;
+    auto ctrl_row = [&](long long R, const int4 ri, long long e0, Real sold, Real tt, Real (&l)[NX], const Real (&gcv)[NX],
+                        const Real (&gov)[NX], Real& snew, Real (&et)[NX], Real (&lv)[NX]) {
+      const Real sg = (ri.y == ROW_UHI) ? (Real)1 : (Real)-1;
+      Real an = 0, lrp = 0, lrd = 0;   // per-row sums in the compute precision, like the state rows
+#pragma unroll
+      for (int c = 0; c < NX; ++c) {
+        const Real y = sg * gcv[c];
+        Real lc = l[c];
+        if (!first) {
+          const Real yo = sg * gov[c];
+          const Real nu = sold * (yo + lc);
+          const Real ln = lc + y - nu;
+          lrp += (y - nu) * (y - nu);
+          lrd += (y - yo) * (y - yo);
+          lc = ln * lscale;
+          lam[e0 + c] = lc;
+        }
+        lv[c] = lc;
+        et[c] = y + lc;
+        an += et[c] * et[c];
+      }
+      prp += (double)lrp; prd += (double)lrd;
+      if (block1) {
+        // the cone in the compute precision (FP32 cones in mixed mode), as for the state rows
+        Real ptn;
+        soc_case_r<Real>(tt, sqrt(an), snew, ptn);
+        D.s[R] = (double)snew; D.ptn[R] = (double)ptn;
+      }
+    };
     for (int g = tid; g < I.n_groups; g += NT) {
       const int2 gr = D.groups[I.grp0 + g];
-      for (int q = 0; q < gr.y; ++q) {
-        const long long R = gr.x + q;
-        const int4 ri = D.rinfo[R];
-        const int k = ri.x, iu = ri.z;
-        const Real sg = (ri.y == ROW_UHI) ? (Real)1 : (Real)-1;
-        const long long e0 = D.rent[R];
-        const Real sold = (Real)D.s[R];
-        Real et[NX], lv[NX];
-        Real an = 0, lrp = 0, lrd = 0;   // per-row sums in the compute precision, like the state rows
+      if (gr.y == 2) {
+        const long long RA = gr.x, RB = (long long)gr.x + 1;
+        const int4 riA = D.rinfo[RA], riB = D.rinfo[RB];
+        const long long eA = D.rent[RA], eB = D.rent[RB];
+        const Real sA = (Real)D.s[RA], sB = (Real)D.s[RB];
+        const Real tA = block1 ? (Real)(D.p[RA] + D.lamp[RA]) : (Real)0;
+        const Real tB = block1 ? (Real)(D.p[RB] + D.lamp[RB]) : (Real)0;
+        const long long gofs = (long long)riA.x * NU * NX + riA.z * NX;   // the group's (k, i)
+        Real gcv[NX], gov[NX], lA[NX], lB[NX];
 #pragma unroll
         for (int c = 0; c < NX; ++c) {
-          const Real y = sg * (Real)gtc_arena[(long long)k * NU * NX + iu * NX + c];
-          Real l = lam[e0 + c];
-          if (!first) {
-            const Real yo = sg * (Real)gto_arena[(long long)k * NU * NX + iu * NX + c];
-            const Real nu = sold * (yo + l);
-            const Real ln = l + y - nu;
-            lrp += (y - nu) * (y - nu);
-            lrd += (y - yo) * (y - yo);
-            l = ln * lscale;
-            lam[e0 + c] = l;
-          }
-          lv[c] = l;
-          et[c] = y + l;
-          an += et[c] * et[c];
+          gcv[c] = (Real)gtc_arena[gofs + c];
+          gov[c] = first ? (Real)0 : (Real)gto_arena[gofs + c];
+          lA[c] = lam[eA + c];
+          lB[c] = lam[eB + c];
         }
-        prp += (double)lrp; prd += (double)lrd;
+        Real snA = 1, snB = 1, etA[NX], etB[NX], lvA[NX], lvB[NX];
+        ctrl_row(RA, riA, eA, sA, tA, lA, gcv, gov, snA, etA, lvA);
+        ctrl_row(RB, riB, eB, sB, tB, lB, gcv, gov, snB, etB, lvB);
         if (block1) {
-          // the cone in the compute precision (FP32 cones in mixed mode), as for the state rows
-          Real snew, ptn;
-          soc_case_r<Real>((Real)(D.p[R] + D.lamp[R]), sqrt(an), snew, ptn);
-          D.s[R] = (double)snew; D.ptn[R] = (double)ptn;
+          const Real sgA = (riA.y == ROW_UHI) ? (Real)1 : (Real)-1, sgB = (riB.y == ROW_UHI) ? (Real)1 : (Real)-1;
 #pragma unroll
-          for (int c = 0; c < NX; ++c)
-            ar[L.Zp + (long long)k * NU * NX + iu * NX + c] += (double)(sg * (snew * et[c] - lv[c]));
+          for (int c = 0; c < NX; ++c) {
+            double z = ar[L.Zp + gofs + c];
+            z += (double)(sgA * (snA * etA[c] - lvA[c]));
+            z += (double)(sgB * (snB * etB[c] - lvB[c]));
+            ar[L.Zp + gofs + c] = z;
+          }
+        }
+      } else {
+        for (int q = 0; q < gr.y; ++q) {
+          const long long R = gr.x + q;
+          const int4 ri = D.rinfo[R];
+          const long long e0 = D.rent[R];
+          const long long gofs = (long long)ri.x * NU * NX + ri.z * NX;
+          Real gcv[NX], gov[NX], l[NX];
+#pragma unroll
+          for (int c = 0; c < NX; ++c) {
+            gcv[c] = (Real)gtc_arena[gofs + c];
+            gov[c] = first ? (Real)0 : (Real)gto_arena[gofs + c];
+            l[c] = lam[e0 + c];
+          }
+          Real sn = 1, et[NX], lv[NX];
+          ctrl_row(R, ri, e0, (Real)D.s[R], block1 ? (Real)(D.p[R] + D.lamp[R]) : (Real)0, l, gcv, gov, sn, et, lv);
+          if (block1) {
+            const Real sg = (ri.y == ROW_UHI) ? (Real)1 : (Real)-1;
+#pragma unroll
+            for (int c = 0; c < NX; ++c) ar[L.Zp + gofs + c] += (double)(sg * (sn * et[c] - lv[c]));
+          }
         }
       }
     }
