@@ -41,6 +41,9 @@ struct SolveParams {
 #ifndef NRTO_FA_NT_F32
 #define NRTO_FA_NT_F32 512
 #endif
+#ifndef NRTO_FA_EM
+#define NRTO_FA_EM 1
+#endif
 #ifndef NRTO_FA_RB
 #define NRTO_FA_RB 4
 #endif
@@ -61,6 +64,14 @@ struct FACfg {
   static constexpr int TPG_MAX = (NPAIR_MAX * NCG + 31) / 32 * 32;   // threads of one row group
   static constexpr int NWR_MAX = TPG_MAX / 32;           // warps of a row group (partial row norms)
   static constexpr int RB = NRTO_FA_RB;                  // rows per warp reduction in sub-pass 1
+  // Sub-pass 1 with a warp per row and lanes over the row's entries, the two gain tables in shared
+  // memory ([m][c][u], u padded to NUP), for small blocks (n_x·n_u ≤ 8: the unicycle).  Its rows are
+  // short and many per chunk, so warps stay balanced and the tables are small.  With n_x = 12 it
+  // measured 9% slower than the column-owned pass (62 KB of tables shrink the chunks, and a chunk's
+  // ~10 rows of 24..1932 entries leave warps idle), and 38% slower with rows split into segments.
+  static constexpr int NUP = NU <= 2 ? 2 : (NU <= 4 ? 4 : 8);
+  static constexpr bool EM = NRTO_FA_EM && NX * NU <= 8;
+  static constexpr int GT_COUNT = EM ? 2 * (TMAXC + 1) * NX * NUP : 0;   // values of the two tables
 };
 
 // Column ownership in the row pass for an instance of horizon T.  Rows at time t hold blocks
@@ -168,6 +179,7 @@ struct FASmem {
   Buf buf[2];
   Real* rowpart;   // [max_rows][NWR_MAX] warp partial norms; in block 2 the gain solve's per-warp scratch
   Real* snew;      // [max_rows]
+  Real* gts;       // the gain tables of an entry-major sub-pass 1 (FACfg::GT_COUNT values)
   double* red;     // block reductions
   double* vec;     // Riccati sweep vector
 
@@ -191,6 +203,7 @@ struct FASmem {
     size_t b = 2 * buf_bytes(chunk, max_rows);
     b += align16(rowpart_count(max_rows) * sizeof(Real));
     b += align16((size_t)max_rows * sizeof(Real));
+    b += align16((size_t)FACfg<NX, NU, Real>::GT_COUNT * sizeof(Real));
     b += (4 * FACfg<NX, NU, Real>::NW + 4 * 16) * sizeof(double);
     return b;
   }
@@ -210,6 +223,7 @@ struct FASmem {
     }
     rowpart = reinterpret_cast<Real*>(take(rowpart_count(max_rows) * sizeof(Real)));
     snew = reinterpret_cast<Real*>(take((size_t)max_rows * sizeof(Real)));
+    gts = reinterpret_cast<Real*>(take((size_t)FACfg<NX, NU, Real>::GT_COUNT * sizeof(Real)));
     red = reinterpret_cast<double*>(c);
     vec = red + 4 * FACfg<NX, NU, Real>::NW;
   }
@@ -858,6 +872,18 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
       for (int w = 0; w < W; ++w) z[k][u][w] = (Real)0;
   Real arp = 0, ard = 0;
   const uint64_t spol = l2_policy_evict_first();
+  constexpr int NUP = C::NUP;
+  const int TB = (T + 1) * NX * NUP;   // offset of the previous-gains table
+  if constexpr (C::EM) {
+    // Gtᵀ tables ([m][u][c] in the arena) into shared memory as [m][c][u], u padded to NUP
+    Real* const gts = sm.gts;
+    for (int q = tid; q < (T + 1) * NX * NUP; q += NT) {
+      const int u = q % NUP, mc = q / NUP, m = mc / NX, c = mc - m * NX;
+      const long long a = (long long)m * NU * NX + u * NX + c;
+      gts[q] = (u < NU) ? (Real)gtc[a] : (Real)0;
+      gts[TB + q] = (u < NU && !first) ? (Real)gto[a] : (Real)0;
+    }
+  }
   // ---------------- row pass over state rows, chunk by chunk (bulk copies, double buffered) --------
   // Thread 0 waits for a chunk's copies before the block barrier that precedes its use: for chunk 0
   // here, for chunk ch+1 at the end of chunk ch, where that barrier also frees chunk ch's buffer.
@@ -888,80 +914,145 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
     const ChunkInfo cki = chunks[ch];
     const int nr = cki.r1 - cki.r0;
     const Real* const so_s = bf.so + so_offset<NX, NU, Real>(I, cki);
-    // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms.  Row group `grp` takes
-    // rows grp, grp+NG, ...; a warp runs RB rows back to back and reduces their partial norms together
-    // (one transposing butterfly), so the rows' reduction latencies overlap.
-    for (int q0 = grp; q0 < nr; q0 += RB * NG) {
-      Real pnv[RB];
-#pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        const int q = q0 + r * NG;
-        pnv[r] = (Real)0;
-        if (q >= nr) continue;
+    if constexpr (C::EM) {
+      // sub-pass 1, entry-major: warp w takes rows w, w+NW, ...; lanes stride over the row's entries,
+      // whose (m, c) gains come from the shared tables.  The warp holds the row's whole norm, so its
+      // lane 0 projects the row at once.
+      const int warp = tid >> 5;
+      const Real* const gts = sm.gts;
+      for (int q = warp; q < nr; q += NT / 32) {
         const RowMeta rm = bf.meta[q];
+        const int len = (rm.t + 1) * NX;
         const Real so = so_s[q];
+        const long long R = row0 + rm.pad;
+        // t̂ = p + λ_p of this row, loaded now so that its latency overlaps the row
+        double tpre = 0.0;
+        if (block1 && lane == 0) tpre = parr[R] + lamparr[R];
         Real pn = 0;
+#pragma unroll 2
+        for (int p = lane; p < len; p += 32) {
+          const int m = p / NX, c = p - m * NX;
+          const int e = rm.off + p;
+          Real bv[NU], g[NUP];
+          ld_vec<NU, Real>(bf.bb + rm.boff + m * NU, bv);
+          ld_vec<NUP, Real>(gts + (m * NX + c) * NUP, g);
+          const Real yb = bf.bhat[e];
+          Real l = bf.lam[e];
+          Real y = yb;
 #pragma unroll
-        for (int k = 0; k < PAIRS; ++k) {
-          if (mk[k] <= rm.t) {
-            const int e = rm.off + mk[k] * NX + ck;
-            Real bv[NU], yb[W], l[W], lg[W];
-            ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
-            ld_vec<W, Real>(bf.bhat + e, yb);
-            ld_vec<W, Real>(bf.lam + e, l);
+          for (int u = 0; u < NU; ++u) y += g[u] * bv[u];
+          if (!first) {
+            Real go_[NUP];
+            ld_vec<NUP, Real>(gts + TB + (m * NX + c) * NUP, go_);
+            Real yo = yb;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-              Real y = yb[w];
-#pragma unroll
-              for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
-              if (!first) {
-                Real yo = yb[w];
-#pragma unroll
-                for (int u = 0; u < NU; ++u) yo += go[k][u][w] * bv[u];
-                const Real nu = so * (yo + l[w]);
-                const Real ln = l[w] + y - nu;
-                arp += (y - nu) * (y - nu);
-                ard += (y - yo) * (y - yo);
-                l[w] = ln * lscale;
-              }
-              const Real et = y + l[w];
-              pn += et * et;
-              lg[w] = l[w];
-              yb[w] += l[w];     // b̂ + λ, kept for sub-pass 2
-              l[w] = et;         // η̂, kept for sub-pass 2
-            }
-            if (!first) st_vec_stream<W, Real>(lam + cki.e0 + e, lg, spol);
-            if (block1) {
-              st_vec<W, Real>(bf.lam + e, l);
-              st_vec<W, Real>(bf.bhat + e, yb);
-            }
+            for (int u = 0; u < NU; ++u) yo += go_[u] * bv[u];
+            const Real nu = so * (yo + l);
+            const Real ln = l + y - nu;
+            arp += (y - nu) * (y - nu);
+            ard += (y - yo) * (y - yo);
+            l = ln * lscale;
+            const Real lg[1] = {l};
+            st_vec_stream<1, Real>(lam + cki.e0 + e, lg, spol);
+          }
+          const Real et = y + l;
+          pn += et * et;
+          if (block1) {
+            bf.lam[e] = et;         // η̂, kept for sub-pass 2
+            bf.bhat[e] = yb + l;    // b̂ + λ, kept for sub-pass 2
           }
         }
-        pnv[r] = pn;
+        if (block1) {
+          pn = warp_sum(pn);
+          if (lane == 0) {
+            // SOC projection (Supplementary Sec. II-C) with t̂ = p + λ_p, in the compute precision
+            Real snew, ptn;
+            soc_case_r<Real>((Real)tpre, sqrt(pn), snew, ptn);
+            snew_s[q] = snew;
+            sarr[R] = (double)snew;
+            sr[row0 + cki.r0 + q] = snew;
+            ptnarr[R] = (double)ptn;
+          }
+        }
       }
-      if (block1) {
-        // lanes [r·32/RB, (r+1)·32/RB) end with the warp's sum for row q0 + r·NG
-        const Real tot = warp_sum_rows<RB>(pnv, lane);
-        const int r = lane / (32 / RB);
-        const int q = q0 + r * NG;
-        if ((lane & (32 / RB - 1)) == 0 && q < nr) rowpart[q * NWR_MAX + gwarp] = tot;
+    } else {
+      // sub-pass 1: λ update of iteration b-1, η̂ of iteration b and row norms.  Row group `grp` takes
+      // rows grp, grp+NG, ...; a warp runs RB rows back to back and reduces their partial norms together
+      // (one transposing butterfly), so the rows' reduction latencies overlap.
+      for (int q0 = grp; q0 < nr; q0 += RB * NG) {
+        Real pnv[RB];
+  #pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const int q = q0 + r * NG;
+          pnv[r] = (Real)0;
+          if (q >= nr) continue;
+          const RowMeta rm = bf.meta[q];
+          const Real so = so_s[q];
+          Real pn = 0;
+  #pragma unroll
+          for (int k = 0; k < PAIRS; ++k) {
+            if (mk[k] <= rm.t) {
+              const int e = rm.off + mk[k] * NX + ck;
+              Real bv[NU], yb[W], l[W], lg[W];
+              ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
+              ld_vec<W, Real>(bf.bhat + e, yb);
+              ld_vec<W, Real>(bf.lam + e, l);
+  #pragma unroll
+              for (int w = 0; w < W; ++w) {
+                Real y = yb[w];
+  #pragma unroll
+                for (int u = 0; u < NU; ++u) y += gc[k][u][w] * bv[u];
+                if (!first) {
+                  Real yo = yb[w];
+  #pragma unroll
+                  for (int u = 0; u < NU; ++u) yo += go[k][u][w] * bv[u];
+                  const Real nu = so * (yo + l[w]);
+                  const Real ln = l[w] + y - nu;
+                  arp += (y - nu) * (y - nu);
+                  ard += (y - yo) * (y - yo);
+                  l[w] = ln * lscale;
+                }
+                const Real et = y + l[w];
+                pn += et * et;
+                lg[w] = l[w];
+                yb[w] += l[w];     // b̂ + λ, kept for sub-pass 2
+                l[w] = et;         // η̂, kept for sub-pass 2
+              }
+              if (!first) st_vec_stream<W, Real>(lam + cki.e0 + e, lg, spol);
+              if (block1) {
+                st_vec<W, Real>(bf.lam + e, l);
+                st_vec<W, Real>(bf.bhat + e, yb);
+              }
+            }
+          }
+          pnv[r] = pn;
+        }
+        if (block1) {
+          // lanes [r·32/RB, (r+1)·32/RB) end with the warp's sum for row q0 + r·NG
+          const Real tot = warp_sum_rows<RB>(pnv, lane);
+          const int r = lane / (32 / RB);
+          const int q = q0 + r * NG;
+          if ((lane & (32 / RB - 1)) == 0 && q < nr) rowpart[q * NWR_MAX + gwarp] = tot;
+        }
       }
     }
     __syncthreads();
     if (block1) {
-      // SOC projection per row (Supplementary Sec. II-C) with t̂ = p + λ_p
-      for (int q = tid; q < nr; q += NT) {
-        Real a2 = 0;
-        for (int w = 0; w < NWR; ++w) a2 += rowpart[q * NWR_MAX + w];
-        const long long R = row0 + bf.meta[q].pad;
-        Real snew, ptn;   // in the compute precision (FP32 cones in mixed mode)
-        soc_case_r<Real>((Real)(parr[R] + lamparr[R]), sqrt(a2), snew, ptn);
-        snew_s[q] = snew;
-        sarr[R] = (double)snew;
-        sr[row0 + cki.r0 + q] = snew;   // storage order: the next iteration's chunk copy brings it
-        ptnarr[R] = (double)ptn;
+      if constexpr (!C::EM) {
+        // SOC projection per row (Supplementary Sec. II-C) with t̂ = p + λ_p
+        for (int q = tid; q < nr; q += NT) {
+          Real a2 = 0;
+          for (int w = 0; w < NWR; ++w) a2 += rowpart[q * NWR_MAX + w];
+          const long long R = row0 + bf.meta[q].pad;
+          Real snew, ptn;   // in the compute precision (FP32 cones in mixed mode)
+          soc_case_r<Real>((Real)(parr[R] + lamparr[R]), sqrt(a2), snew, ptn);
+          snew_s[q] = snew;
+          sarr[R] = (double)snew;
+          sr[row0 + cki.r0 + q] = snew;   // storage order: the next iteration's chunk copy brings it
+          ptnarr[R] = (double)ptn;
+        }
+        __syncthreads();
       }
-      __syncthreads();
       // sub-pass 2: Z'_m[:, c] += b_{j,m} w_{j,m}[c], w = ν - b̂ - λ = s η̂ - (b̂ + λ), from the η̂ and
       // b̂ + λ that sub-pass 1 left in the chunk buffer (λ_ν itself was stored to global memory)
       for (int q = grp; q < nr; q += NG) {
