@@ -230,7 +230,52 @@ __global__ void __launch_bounds__(256) k_adjoint(Dev<Real> D, int slot_sel) {
 }
 
 // G_m = Σ_j b_{j,m} b_{j,m}ᵀ over state rows (from the stored, possibly rounded b) plus e_ie_iᵀ per
-// control bound at step m.  Block per instance, thread per (m, u1, u2).
+// control bound at step m.  Block per instance; a warp per block index m (gram_rows).
+template <int NU, typename Real>
+__device__ __forceinline__ void gram_rows(const Dev<Real>& D, const Inst& I, const Real* bv, double* sa, const SlotL& SL) {
+  // A warp per block index m; its lanes take rows lane, lane+32, ... with independent loads and keep
+  // the NU(NU+1)/2 distinct products in the compute precision, and the warp sums the lanes' partials
+  // in FP64.
+  constexpr int NP = NU * (NU + 1) / 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int m = warp; m < I.T; m += nw) {
+    Real acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = (Real)0;
+    // state rows with t > m start at local row m·rows_per_t (rows are ordered by t = 1..T)
+#pragma unroll 4
+    for (int r = m * I.rows_per_t + lane; r < I.n_sr; r += 32) {
+      const Real* b = bv + D.rbent[I.row0 + r] + (long long)m * NU;
+      Real bb[NU];
+#pragma unroll
+      for (int u = 0; u < NU; ++u) bb[u] = b[u];
+      int k = 0;
+#pragma unroll
+      for (int u1 = 0; u1 < NU; ++u1)
+#pragma unroll
+        for (int u2 = u1; u2 < NU; ++u2) acc[k++] += bb[u1] * bb[u2];
+    }
+    int k = 0;
+#pragma unroll
+    for (int u1 = 0; u1 < NU; ++u1)
+#pragma unroll
+      for (int u2 = u1; u2 < NU; ++u2, ++k) {
+        double v = warp_sum((double)acc[k]);
+        if (lane == 0) {
+          if (u1 == u2 && I.n_groups > 0) {
+            const int gpk = I.n_groups / I.T;   // control groups are ordered by step, gpk per step
+            for (int g = m * gpk; g < (m + 1) * gpk; ++g) {
+              const int2 gr = D.groups[I.grp0 + g];
+              if (D.rinfo[gr.x].z == u1) v += (double)gr.y;
+            }
+          }
+          sa[SL.Gm + (long long)m * NU * NU + u1 * NU + u2] = v;
+          sa[SL.Gm + (long long)m * NU * NU + u2 * NU + u1] = v;
+        }
+      }
+  }
+}
+
 template <typename Real>
 __global__ void k_gram(Dev<Real> D, int slot_sel) {
   const int i = blockIdx.x;
@@ -239,25 +284,9 @@ __global__ void k_gram(Dev<Real> D, int slot_sel) {
   const SlotL SL = slot_layout(I.nx, I.nu, I.T);
   double* sa = D.slot[slot].arena + I.slot0;
   const Real* bv = D.slot[slot].bvec;
-  const int nu = I.nu;
-  const int total = I.T * nu * nu;
-  for (int q = threadIdx.x; q < total; q += blockDim.x) {
-    const int m = q / (nu * nu), u1 = (q / nu) % nu, u2 = q % nu;
-    double acc = 0.0;
-    // state rows with t > m start at local row m·rows_per_t (rows are ordered by t = 1..T)
-    for (int r = m * I.rows_per_t; r < I.n_sr; ++r) {
-      const long long b0 = D.rbent[I.row0 + r] + (long long)m * nu;
-      acc += (double)bv[b0 + u1] * (double)bv[b0 + u2];
-    }
-    if (u1 == u2 && I.n_groups > 0) {
-      const int gpk = I.n_groups / I.T;   // control groups are ordered by step, gpk per step
-      for (int g = m * gpk; g < (m + 1) * gpk; ++g) {
-        const int2 gr = D.groups[I.grp0 + g];
-        if (D.rinfo[gr.x].z == u1) acc += (double)gr.y;
-      }
-    }
-    sa[SL.Gm + q] = acc;
-  }
+  if (I.kind == KIND_UNICYCLE) gram_rows<2, Real>(D, I, bv, sa, SL);
+  else if (I.kind == KIND_QUADCOPTER) gram_rows<4, Real>(D, I, bv, sa, SL);
+  else gram_rows<7, Real>(D, I, bv, sa, SL);
 }
 
 // Gain-solve factors for H_m = I⊗(2W + shift·I) + coef·τ Σ_m⊗G_m (W = R_KᵀR_K):
