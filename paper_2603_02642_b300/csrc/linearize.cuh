@@ -109,6 +109,24 @@ __global__ void k_rows(Dev<Real> D, int slot_sel) {
 // each thread keeps RB rows' v in registers, the step's Ψ_i, A_{i-1}, B_{i-1} are staged in shared
 // memory (double buffered, prefetched one step ahead) and shared by every row.  Arithmetic in the
 // compute precision.
+// Store N consecutive values of one row's block.  Blocks of n_x (or n_u) values start on a multiple
+// of n_x (n_u) inside a row, rows start on 4-element boundaries inside a chunk, and chunks on 4-element
+// boundaries of the array, so a block whose length is a multiple of 4 (2) is 16-byte (8-byte)
+// aligned for FP32 and is stored with vector stores.
+template <int N, typename Real>
+__device__ __forceinline__ void st_block(Real* p, const Real (&v)[N]) {
+  if constexpr (sizeof(Real) == 4 && N % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 4) *reinterpret_cast<float4*>(p + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  } else if constexpr (sizeof(Real) == 4 && N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) *reinterpret_cast<float2*>(p + i) = make_float2(v[i], v[i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = v[i];
+  }
+}
+
 template <int NX, int NU, int RB, typename Real>
 __device__ void adjoint_rows(const Dev<Real>& D, const Inst& I, const double* ar, const Arena& L, const double* sa,
                              const SlotL& SL, LinSlot<Real>& S, Real* smem) {
@@ -167,24 +185,32 @@ __device__ void adjoint_rows(const Dev<Real>& D, const Inst& I, const double* ar
         if (tr[b] == k) {
 #pragma unroll
           for (int c = 0; c < NX; ++c) v[b][c] = (Real)S.arow[I.arow0 + (long long)r * NX + c];
+          Real z[NU];
 #pragma unroll
-          for (int u = 0; u < NU; ++u) S.bvec[b0[b] + (long long)k * NU + u] = (Real)0;
+          for (int u = 0; u < NU; ++u) z[u] = (Real)0;
+          st_block<NU>(S.bvec + b0[b] + (long long)k * NU, z);
         }
+        {
+          Real h[NX];
 #pragma unroll
-        for (int c = 0; c < NX; ++c) {
-          Real acc = 0;
+          for (int c = 0; c < NX; ++c) {
+            Real acc = 0;
 #pragma unroll
-          for (int q = 0; q < NX; ++q) acc += sPsi[c * NX + q] * v[b][q];
-          S.bhat[e0[b] + (long long)k * NX + c] = sq * acc;
+            for (int q = 0; q < NX; ++q) acc += sPsi[c * NX + q] * v[b][q];
+            h[c] = sq * acc;
+          }
+          st_block<NX>(S.bhat + e0[b] + (long long)k * NX, h);
         }
         if (k >= 1) {
+          Real bk[NU];
 #pragma unroll
           for (int u = 0; u < NU; ++u) {
             Real acc = 0;
 #pragma unroll
             for (int q = 0; q < NX; ++q) acc += sB[q * NU + u] * v[b][q];
-            S.bvec[b0[b] + (long long)(k - 1) * NU + u] = acc;
+            bk[u] = acc;
           }
+          st_block<NU>(S.bvec + b0[b] + (long long)(k - 1) * NU, bk);
           Real vn[NX];
 #pragma unroll
           for (int c = 0; c < NX; ++c) {
