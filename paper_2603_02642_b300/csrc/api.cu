@@ -82,6 +82,32 @@ __global__ void k_scatter_uhat(double* slot_arena, const Inst* inst, const doubl
   for (int q = threadIdx.x; q < I.T * I.nu; q += blockDim.x) dst[q] = src[off[i] + q];
 }
 
+// Output gather: per instance (block), `cnt` values of a field at offset `off` inside its arena
+// (which = 0) or inside its current solver slot (which = 1) into out + out_off[i], so that the host
+// reads the batch's field with one copy.
+enum : int { GF_DU = 0, GF_K1 = 1, GF_UHAT = 2, GF_KACC = 3 };
+__global__ void k_gather_field(const Inst* inst, const int* is, const double* arena, const double* slot0,
+                               const double* slot1, int field, const long long* out_off, double* out, int n) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const Inst I = inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  const double* src = nullptr;
+  long long cnt = 0;
+  if (field == GF_UHAT) {
+    const double* sa = is[i * NIS + IS_SLOT] == 0 ? slot0 : slot1;
+    src = sa + I.slot0 + slot_layout(I.nx, I.nu, I.T).u_hat;
+    cnt = (long long)I.T * I.nu;
+  } else if (field == GF_DU) {
+    src = arena + I.arena0 + L.du;
+    cnt = (long long)I.T * I.nu;
+  } else {
+    src = arena + I.arena0 + (field == GF_K1 ? L.K1 : L.Kacc);
+    cnt = (long long)I.T * I.nu * I.nx;
+  }
+  for (long long q = threadIdx.x; q < cnt; q += blockDim.x) out[out_off[i] + q] = src[q];
+}
+
 template <typename Real>
 __global__ void k_candidate(Dev<Real> D) {
   const int i = blockIdx.x;
@@ -151,8 +177,8 @@ struct nrto_problem {
   KindLaunch kl[3];
   long long n_rows = 0, n_ent = 0, n_bent = 0, arena_total = 0, slot_total = 0, arow_total = 0;
   long long n_groups_total = 0, n_cb_total = 0;
-  std::vector<long long> stage_off, stage_len, uoff;
-  long long stage_total = 0, u_total = 0;
+  std::vector<long long> stage_off, stage_len, uoff, koff;
+  long long stage_total = 0, u_total = 0, k_total = 0;
   std::vector<void*> allocs;
   // When carve_base is set (nrto_solve_noalloc), device buffers are cut from that caller-owned area
   // instead of being allocated.
@@ -187,6 +213,8 @@ struct nrto_problem {
   long long* d_stage_off = nullptr;
   long long* d_stage_len = nullptr;
   long long* d_uoff = nullptr;
+  long long* d_koff = nullptr;     // per-instance offsets of T·n_u·n_x fields in a gathered output
+  double* d_gather = nullptr;      // output gather buffer (max(u_total, k_total) values)
   double* d_ustage = nullptr;
   bool linearized = false;
   bool warm_pending = false;
@@ -486,28 +514,18 @@ void choose_chunk(KindLaunch& kl) {
   if (need > 2 * bb) fail(NRTO_ERR_INVALID, "internal: chunk buffers too small for the block-2 sweep");
 }
 
-// per-instance arena/slot field copy (device → host) of cnt(I) doubles at off(I)
-void copy_arena_field(nrto_problem* P, int which /*0 arena, 1 current slot*/, long long (*off)(const Inst&),
-                      double* dst, long long (*cnt)(const Inst&)) {
-  std::vector<int> is(P->n * NIS);
-  CK(cudaMemcpyAsync(is.data(), P->d_is, sizeof(int) * is.size(), cudaMemcpyDeviceToHost, P->stream));
-  CK(cudaStreamSynchronize(P->stream));
-  long long o = 0;
-  for (int i = 0; i < P->n; ++i) {
-    const Inst& I = P->h_inst[i];
-    const double* base = which == 0 ? P->d_arena + I.arena0 : P->d_slot_arena[is[i * NIS + IS_SLOT]] + I.slot0;
-    CK(cudaMemcpyAsync(dst + o, base + off(I), sizeof(double) * cnt(I), cudaMemcpyDeviceToHost, P->stream));
-    o += cnt(I);
-  }
+// Per-instance field of the batch (device → host): one gather launch into a contiguous device
+// buffer, then one copy.
+void copy_arena_field(nrto_problem* P, int field, double* dst) {
+  const bool per_k = field == GF_K1 || field == GF_KACC;
+  const long long total = per_k ? P->k_total : P->u_total;
+  k_gather_field<<<P->n, 128, 0, P->stream>>>(P->d_inst, P->d_is, P->d_arena, P->d_slot_arena[0], P->d_slot_arena[1],
+                                              field, per_k ? P->d_koff : P->d_uoff, P->d_gather, P->n);
+  P->check_launch("k_gather_field");
+  if (total > 0) CK(cudaMemcpyAsync(dst, P->d_gather, sizeof(double) * total, cudaMemcpyDeviceToHost, P->stream));
   CK(cudaStreamSynchronize(P->stream));
 }
 
-long long off_du(const Inst& I) { return arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link).du; }
-long long off_k1(const Inst& I) { return arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link).K1; }
-long long off_kacc(const Inst& I) { return arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link).Kacc; }
-long long off_uhat(const Inst& I) { return slot_layout(I.nx, I.nu, I.T).u_hat; }
-long long cnt_u(const Inst& I) { return (long long)I.T * I.nu; }
-long long cnt_k(const Inst& I) { return (long long)I.T * I.nu * I.nx; }
 
 nrto_status handle(const std::exception& e) {
   if (auto ne = dynamic_cast<const NrtoError*>(&e)) {
@@ -559,8 +577,8 @@ nrto_status finish_statuses(nrto_problem* p, const nrto_solver_opts* o, nrto_soc
   std::vector<double> sc(p->n * NSC);
   CK(cudaMemcpyAsync(is.data(), p->d_is, sizeof(int) * is.size(), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaMemcpyAsync(sc.data(), p->d_sc, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
-  if (out->du) copy_arena_field(p, 0, off_du, out->du, cnt_u);
-  if (out->K) copy_arena_field(p, 0, off_k1, out->K, cnt_k);
+  if (out->du) copy_arena_field(p, GF_DU, out->du);
+  if (out->K) copy_arena_field(p, GF_K1, out->K);
   if (out->p) CK(cudaMemcpyAsync(out->p, p->d_p, sizeof(double) * p->n_rows, cudaMemcpyDeviceToHost, p->stream));
   if (out->ptilde) CK(cudaMemcpyAsync(out->ptilde, p->d_pt, sizeof(double) * p->n_rows, cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
@@ -874,6 +892,8 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
       stage += L.Psi;
       P->uoff.push_back(uo);
       uo += (long long)d.T * d.nu;
+      P->koff.push_back(P->k_total);
+      P->k_total += (long long)d.T * d.nu * d.nx;
       arena += L.total; slot += SL.total; arow += (long long)I.n_sr * d.nx;
       row += I.n_sr + I.n_cr; grp += ng;
       P->h_inst[i] = I;
@@ -923,6 +943,8 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
     P->d_stage_off = P->dalloc<long long>(n);
     P->d_stage_len = P->dalloc<long long>(n);
     P->d_uoff = P->dalloc<long long>(n);
+    P->d_koff = P->dalloc<long long>(n);
+    P->d_gather = P->dalloc<double>((size_t)std::max(P->u_total, P->k_total));
     P->d_ustage = P->dalloc<double>(uo);
     auto up = [&](void* dst, const void* src, size_t bytes) {
       if (bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, P->stream));
@@ -938,6 +960,7 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
     up(P->d_stage_off, P->stage_off.data(), sizeof(long long) * n);
     up(P->d_stage_len, P->stage_len.data(), sizeof(long long) * n);
     up(P->d_uoff, P->uoff.data(), sizeof(long long) * n);
+    up(P->d_koff, P->koff.data(), sizeof(long long) * n);
     upload_params(P, descs);
     if (precision == NRTO_PREC_FP64) {
       launch_setup<double>(P);
@@ -1100,8 +1123,8 @@ nrto_status nrto_solve(nrto_problem_t p, const nrto_solver_opts* o, int n_outer,
     for (int it = 0; it < n_outer; ++it) {
       if (f64) launch_outer_step<double>(p, *o); else launch_outer_step<float>(p, *o);
     }
-    if (u_bar) copy_arena_field(p, 1, off_uhat, u_bar, cnt_u);
-    if (K) copy_arena_field(p, 0, off_kacc, K, cnt_k);
+    if (u_bar) copy_arena_field(p, GF_UHAT, u_bar);
+    if (K) copy_arena_field(p, GF_KACC, K);
     if (merit) {
       std::vector<double> sc(p->n * NSC);
       CK(cudaMemcpyAsync(sc.data(), p->d_sc, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));

@@ -24,14 +24,19 @@ _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
 
 
+# nrto_problem_desc.  The `const double*` members are declared as void pointers (same size and
+# alignment) so that the binding can store array addresses as plain integers.
+_vp = C.c_void_p
+
+
 class ProblemDesc(C.Structure):
     _fields_ = [("dyn", C.c_int), ("nx", C.c_int), ("nu", C.c_int), ("T", C.c_int), ("dt", C.c_double),
-                ("dyn_params", _dp), ("n_dyn_params", C.c_int),
-                ("x0", _dp), ("x_goal", _dp), ("u_init", _dp), ("u_ref", _dp), ("Sigma", _dp),
-                ("tau", C.c_double), ("Qx", _dp), ("Ru", _dp), ("RK", _dp),
-                ("n_obs", C.c_int), ("obs_dim", C.c_int), ("obs_center", _dp), ("obs_radius", _dp),
-                ("n_link", C.c_int), ("link_spheres", _dp),
-                ("u_lo", _dp), ("u_hi", _dp), ("x_lo", _dp), ("x_hi", _dp)]
+                ("dyn_params", _vp), ("n_dyn_params", C.c_int),
+                ("x0", _vp), ("x_goal", _vp), ("u_init", _vp), ("u_ref", _vp), ("Sigma", _vp),
+                ("tau", C.c_double), ("Qx", _vp), ("Ru", _vp), ("RK", _vp),
+                ("n_obs", C.c_int), ("obs_dim", C.c_int), ("obs_center", _vp), ("obs_radius", _vp),
+                ("n_link", C.c_int), ("link_spheres", _vp),
+                ("u_lo", _vp), ("u_hi", _vp), ("x_lo", _vp), ("x_hi", _vp)]
 
 
 class SolverOpts(C.Structure):
@@ -160,25 +165,28 @@ class Options:
                           self.stall_every, self.stall_ratio, self.warm_fallback)
 
 
+_ZERO1 = np.zeros(1)
+_ZERO5 = np.zeros(5)
+
+
 def _desc(inst, keep):
-    def arr(a):
-        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    def adr(a):
+        # address of a C-contiguous float64 copy (the array itself when it already is one)
+        if not (type(a) is np.ndarray and a.dtype == np.float64 and a.flags.c_contiguous):
+            a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
         keep.append(a)
-        return a
+        return a.ctypes.data
     is_arm = inst.kind == 2
     return ProblemDesc(
-        dyn=inst.kind, nx=inst.nx, nu=inst.nu, T=inst.T, dt=inst.dt,
-        dyn_params=_ptr(arr(inst.dyn_params if inst.dyn_params.size else np.zeros(1))),
-        n_dyn_params=int(inst.dyn_params.size),
-        x0=_ptr(arr(inst.x0)), x_goal=_ptr(arr(inst.x_goal)), u_init=_ptr(arr(inst.u_init)),
-        u_ref=_ptr(arr(inst.u_ref)), Sigma=_ptr(arr(inst.Sigma)), tau=inst.tau,
-        Qx=_ptr(arr(inst.Qx)), Ru=_ptr(arr(inst.Ru)), RK=_ptr(arr(inst.RK)),
-        n_obs=inst.n_obs, obs_dim=inst.obs_dim,
-        obs_center=_ptr(arr(inst.obs_center if inst.n_obs else np.zeros(1))),
-        obs_radius=_ptr(arr(inst.obs_radius if inst.n_obs else np.zeros(1))),
-        n_link=int(inst.link_spheres.shape[0]) if is_arm else 0,
-        link_spheres=_ptr(arr(inst.link_spheres if is_arm and inst.link_spheres.size else np.zeros(5))),
-        u_lo=_ptr(arr(inst.u_lo)), u_hi=_ptr(arr(inst.u_hi)), x_lo=_ptr(arr(inst.x_lo)), x_hi=_ptr(arr(inst.x_hi)))
+        inst.kind, inst.nx, inst.nu, inst.T, inst.dt,
+        adr(inst.dyn_params if inst.dyn_params.size else _ZERO1), int(inst.dyn_params.size),
+        adr(inst.x0), adr(inst.x_goal), adr(inst.u_init), adr(inst.u_ref), adr(inst.Sigma),
+        inst.tau, adr(inst.Qx), adr(inst.Ru), adr(inst.RK),
+        inst.n_obs, inst.obs_dim,
+        adr(inst.obs_center if inst.n_obs else _ZERO1), adr(inst.obs_radius if inst.n_obs else _ZERO1),
+        int(inst.link_spheres.shape[0]) if is_arm else 0,
+        adr(inst.link_spheres if is_arm and inst.link_spheres.size else _ZERO5),
+        adr(inst.u_lo), adr(inst.u_hi), adr(inst.x_lo), adr(inst.x_hi))
 
 
 class Problem:
