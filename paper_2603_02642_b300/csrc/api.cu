@@ -8,7 +8,9 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <exception>
 #include <mutex>
+#include <thread>
 #include <numeric>
 #include <stdexcept>
 #include <string>
@@ -536,15 +538,47 @@ nrto_status handle(const std::exception& e) {
   return NRTO_ERR_INVALID;
 }
 
+// Runs f(i) for i in [0, n) on up to hardware_concurrency host threads.  A failure of instance i is
+// kept, and the failure of the lowest index is rethrown after all threads finish, so the reported
+// error does not depend on scheduling.
+template <typename F>
+void parallel_instances(int n, F f) {
+  const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), (n + 63) / 64));
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::exception_ptr> err(nt);
+  std::vector<int> err_at(nt, n);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t]() {
+      for (int i = t; i < n; i += nt) {
+        try {
+          f(i);
+        } catch (...) {
+          err[t] = std::current_exception();
+          err_at[t] = i;
+          return;
+        }
+      }
+    });
+  for (auto& x : th) x.join();
+  int first = -1;
+  for (int t = 0; t < nt; ++t)
+    if (err[t] && (first < 0 || err_at[t] < err_at[first])) first = t;
+  if (first >= 0) std::rethrow_exception(err[first]);
+}
+
 void upload_params(nrto_problem* P, const nrto_problem_desc* descs) {
   std::vector<double> stage(P->stage_total, 0.0);
   std::vector<double> ust(P->u_total, 0.0);
-  for (int i = 0; i < P->n; ++i) {
+  parallel_instances(P->n, [&](int i) {
     const Inst& I = P->h_inst[i];
     const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
     pack_params(descs[i], L, stage.data() + P->stage_off[i]);
     std::memcpy(ust.data() + P->uoff[i], descs[i].u_init, sizeof(double) * I.T * I.nu);
-  }
+  });
   CK(cudaMemcpyAsync(P->d_stage, stage.data(), sizeof(double) * stage.size(), cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_ustage, ust.data(), sizeof(double) * ust.size(), cudaMemcpyHostToDevice, P->stream));
   k_scatter<<<P->n, 256, 0, P->stream>>>(P->d_arena, P->d_inst, P->d_stage, P->d_stage_off, P->d_stage_len, P->n);
@@ -1012,7 +1046,7 @@ nrto_status nrto_problem_info(nrto_problem_t p, int i, nrto_instance_info* info)
 nrto_status nrto_problem_update(nrto_problem_t p, const nrto_problem_desc* descs, int n) {
   try {
     if (!p || !descs || n != p->n) fail(NRTO_ERR_INVALID, "update needs the same number of instances");
-    for (int i = 0; i < n; ++i) {
+    parallel_instances(n, [&](int i) {
       validate(descs[i], i);
       const Inst& I = p->h_inst[i];
       if (descs[i].dyn != I.kind || descs[i].T != I.T || descs[i].n_obs != I.n_obs || descs[i].n_link != I.n_link)
@@ -1022,7 +1056,7 @@ nrto_status nrto_problem_update(nrto_problem_t p, const nrto_problem_desc* descs
       build_rows(descs[i], sr, cr, rpt);
       if ((int)sr.size() != I.n_sr || (int)cr.size() != I.n_cr) fail(NRTO_ERR_INVALID, "row structure differs from create");
       if (descs[i].tau != I.tau || descs[i].dt != I.dt) fail(NRTO_ERR_INVALID, "dt/tau differ from create");
-    }
+    });
     upload_params(p, descs);
     if (p->prec == NRTO_PREC_FP64) launch_setup<double>(p); else launch_setup<float>(p);
     p->linearized = false;
