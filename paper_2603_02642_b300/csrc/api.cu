@@ -217,6 +217,11 @@ struct nrto_problem {
   long long* d_uoff = nullptr;
   long long* d_koff = nullptr;     // per-instance offsets of T·n_u·n_x fields in a gathered output
   double* d_gather = nullptr;      // output gather buffer (max(u_total, k_total) values)
+  // Pinned host staging of the per-instance parameters and initial controls, kept across updates
+  // (zero-filled once; every update rewrites the same positions).  Not used by nrto_solve_noalloc,
+  // which allocates nothing and stages through temporary host vectors.
+  double* h_stage = nullptr;
+  double* h_ustage = nullptr;
   double* d_ustage = nullptr;
   bool linearized = false;
   bool warm_pending = false;
@@ -246,6 +251,8 @@ struct nrto_problem {
   ~nrto_problem() {
     for (auto& ev : prof_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
     for (void* a : allocs) cudaFree(a);
+    if (h_stage) cudaFreeHost(h_stage);
+    if (h_ustage) cudaFreeHost(h_ustage);
   }
   template <typename Real>
   Dev<Real> dev() const {
@@ -372,6 +379,7 @@ void pack_params(const nrto_problem_desc& d, const Arena& L, double* dst) {
   put(L.Qx, d.Qx, d.nx); put(L.Ru, d.Ru, d.nu); put(L.RK, d.RK, d.nu);
   put(L.ulo, d.u_lo, d.nu); put(L.uhi, d.u_hi, d.nu); put(L.xlo, d.x_lo, d.nx); put(L.xhi, d.x_hi, d.nx);
   if (d.n_dyn_params > 0) put(L.dyn, d.dyn_params, d.n_dyn_params);
+  for (int i = d.n_dyn_params; i < MAX_DYN; ++i) dst[L.dyn + i] = 0.0;   // the staging is reused across updates
   for (int o = 0; o < d.n_obs; ++o) {
     for (int k = 0; k < 3; ++k) dst[L.obs + 4 * o + k] = (k < d.obs_dim) ? d.obs_center[o * d.obs_dim + k] : 0.0;
     dst[L.obs + 4 * o + 3] = d.obs_radius[o];
@@ -571,23 +579,38 @@ void parallel_instances(int n, F f) {
 }
 
 void upload_params(nrto_problem* P, const nrto_problem_desc* descs) {
-  std::vector<double> stage(P->stage_total, 0.0);
-  std::vector<double> ust(P->u_total, 0.0);
+  std::vector<double> sv, uv;
+  if (!P->carve_base && !P->h_stage) {
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&P->h_stage), sizeof(double) * std::max<long long>(P->stage_total, 1),
+                     cudaHostAllocDefault));
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&P->h_ustage), sizeof(double) * std::max<long long>(P->u_total, 1),
+                     cudaHostAllocDefault));
+    std::memset(P->h_stage, 0, sizeof(double) * P->stage_total);
+    std::memset(P->h_ustage, 0, sizeof(double) * P->u_total);
+  }
+  double* stage = P->h_stage;
+  double* ust = P->h_ustage;
+  if (!stage) {
+    sv.assign(P->stage_total, 0.0);
+    uv.assign(P->u_total, 0.0);
+    stage = sv.data();
+    ust = uv.data();
+  }
   parallel_instances(P->n, [&](int i) {
     const Inst& I = P->h_inst[i];
     const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
-    pack_params(descs[i], L, stage.data() + P->stage_off[i]);
-    std::memcpy(ust.data() + P->uoff[i], descs[i].u_init, sizeof(double) * I.T * I.nu);
+    pack_params(descs[i], L, stage + P->stage_off[i]);
+    std::memcpy(ust + P->uoff[i], descs[i].u_init, sizeof(double) * I.T * I.nu);
   });
-  CK(cudaMemcpyAsync(P->d_stage, stage.data(), sizeof(double) * stage.size(), cudaMemcpyHostToDevice, P->stream));
-  CK(cudaMemcpyAsync(P->d_ustage, ust.data(), sizeof(double) * ust.size(), cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->d_stage, stage, sizeof(double) * P->stage_total, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->d_ustage, ust, sizeof(double) * P->u_total, cudaMemcpyHostToDevice, P->stream));
   k_scatter<<<P->n, 256, 0, P->stream>>>(P->d_arena, P->d_inst, P->d_stage, P->d_stage_off, P->d_stage_len, P->n);
   P->check_launch("k_scatter");
   for (int s = 0; s < 2; ++s) {
     k_scatter_uhat<<<P->n, 128, 0, P->stream>>>(P->d_slot_arena[s], P->d_inst, P->d_ustage, P->d_uoff, P->n);
     P->check_launch("k_scatter_uhat");
   }
-  CK(cudaStreamSynchronize(P->stream));   // host staging vectors go out of scope
+  CK(cudaStreamSynchronize(P->stream));   // the staging is reused (or goes out of scope) after this
 }
 
 void check_opts(const nrto_solver_opts* o) {
