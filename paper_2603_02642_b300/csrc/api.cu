@@ -348,6 +348,15 @@ void validate(const nrto_problem_desc& d, int idx) {
 }
 
 // rows of one instance in the shared row order
+// Row counts of build_rows without building the rows.
+void count_rows(const nrto_problem_desc& d, long long& n_sr, long long& n_cr) {
+  long long per_t = (long long)d.n_obs * (d.dyn == KIND_ARM ? d.n_link : 1), per_k = 0;
+  for (int i = 0; i < d.nx; ++i) per_t += (std::isfinite(d.x_hi[i]) ? 1 : 0) + (std::isfinite(d.x_lo[i]) ? 1 : 0);
+  for (int i = 0; i < d.nu; ++i) per_k += (std::isfinite(d.u_hi[i]) ? 1 : 0) + (std::isfinite(d.u_lo[i]) ? 1 : 0);
+  n_sr = per_t * d.T;
+  n_cr = per_k * d.T;
+}
+
 void build_rows(const nrto_problem_desc& d, std::vector<int4>& srows, std::vector<int4>& crows, int& rows_per_t) {
   srows.clear();
   crows.clear();
@@ -1074,10 +1083,9 @@ nrto_status nrto_problem_update(nrto_problem_t p, const nrto_problem_desc* descs
       const Inst& I = p->h_inst[i];
       if (descs[i].dyn != I.kind || descs[i].T != I.T || descs[i].n_obs != I.n_obs || descs[i].n_link != I.n_link)
         fail(NRTO_ERR_INVALID, "instance " + std::to_string(i) + ": structure differs from create");
-      std::vector<int4> sr, cr;
-      int rpt = 0;
-      build_rows(descs[i], sr, cr, rpt);
-      if ((int)sr.size() != I.n_sr || (int)cr.size() != I.n_cr) fail(NRTO_ERR_INVALID, "row structure differs from create");
+      long long nsr = 0, ncr = 0;
+      count_rows(descs[i], nsr, ncr);
+      if (nsr != I.n_sr || ncr != I.n_cr) fail(NRTO_ERR_INVALID, "row structure differs from create");
       if (descs[i].tau != I.tau || descs[i].dt != I.dt) fail(NRTO_ERR_INVALID, "dt/tau differ from create");
     });
     upload_params(p, descs);
