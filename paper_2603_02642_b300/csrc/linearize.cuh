@@ -474,10 +474,143 @@ __device__ __noinline__ void riccati_factor_warp(const Dev<Real>& D, int i, doub
 }
 
 // One warp per instance (block per instance, blockDim = 32).
+// C (m×n) = α·op(A)·op(B) (+ C), compile-time shapes, each element summed over j in order (the
+// same order as wmm).
+template <int M, int N, int K, bool TA, bool TB, int LDA, int LDB>
+__device__ __forceinline__ void wmm_c(double* C, const double* A, const double* B, double alpha, bool accumulate) {
+  for (int q = threadIdx.x & 31; q < M * N; q += 32) {
+    const int r = q / N, c = q % N;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const double av = TA ? A[j * LDA + r] : A[r * LDA + j];
+      const double bv = TB ? B[c * LDB + j] : B[j * LDB + c];
+      acc += av * bv;
+    }
+    C[r * N + c] = accumulate ? C[r * N + c] + alpha * acc : alpha * acc;
+  }
+  __syncwarp();
+}
+
+// riccati_factor_warp with compile-time (n_x, n_u) and A_k, B_k staged in shared memory once per step;
+// the same operations in the same order, so the factors are identical.  Used by k_riccati_factor,
+// which has shared memory to spare; the solver kernels keep riccati_factor_warp and its smaller
+// scratch for their in-kernel refactorization.
+constexpr int RIC_SCRATCH_STAGED = RIC_SCRATCH + 196 + 98;
+template <int nx, int nu, typename Real>
+__device__ void riccati_factor_staged(const Dev<Real>& D, int i, double rho, double* scr) {
+  const Inst I = D.inst[i];
+  const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+  const SlotL SL = slot_layout(I.nx, I.nu, I.T);
+  double* ar = D.arena + I.arena0;
+  const int sl = D.is[i * NIS + IS_SLOT];
+  const double* sa = D.slot[sl].arena + I.slot0;
+  const double* arow = D.slot[sl].arow;
+  const int lane = threadIdx.x & 31;
+  double* P = scr;
+  double* PA = P + 196;
+  double* PB = PA + 196;
+  double* Huu = PB + 98;
+  double* Hux = Huu + 49;
+  double* Nm = Hux + 98;
+  double* Lm = Nm + 49;
+  double* Q = Lm + 98;
+  double* tmp = Q + 196;
+  double* sA = tmp + 196;
+  double* sB = sA + 196;
+  auto build_Q = [&](int t) {
+    for (int q = lane; q < nx * nx; q += 32) {
+      int r = q / nx, c = q % nx;
+      double v = (r == c) ? (2.0 * ar[L.Qx + r] + rho) : 0.0;
+      for (int s = 0; s < I.rows_per_t; ++s) {
+        long long rr = (long long)(t - 1) * I.rows_per_t + s;
+        v += 0.5 * rho * arow[I.arow0 + rr * nx + r] * arow[I.arow0 + rr * nx + c];
+      }
+      Q[q] = v;
+    }
+    __syncwarp();
+  };
+  build_Q(I.T);
+  for (int q = lane; q < nx * nx; q += 32) P[q] = Q[q];
+  __syncwarp();
+  for (int k = I.T - 1; k >= 0; --k) {
+    const double* Ak = sa + SL.A + (long long)k * nx * nx;
+    const double* Bk = sa + SL.B + (long long)k * nx * nu;
+    for (int q = lane; q < nx * nx; q += 32) sA[q] = Ak[q];
+    for (int q = lane; q < nx * nu; q += 32) sB[q] = Bk[q];
+    __syncwarp();
+    wmm_c<nx, nx, nx, false, false, nx, nx>(PA, P, sA, 1.0, false);
+    wmm_c<nx, nu, nx, false, false, nx, nu>(PB, P, sB, 1.0, false);
+    wmm_c<nu, nu, nx, true, false, nu, nu>(Huu, sB, PB, 1.0, false);
+    wmm_c<nu, nx, nx, true, false, nu, nx>(Hux, sB, PA, 1.0, false);
+    if (lane == 0) {
+      for (int u = 0; u < nu; ++u) Huu[u * nu + u] += 2.0 * ar[L.Ru + u];
+      if (I.n_groups > 0) {
+        const int gpk = I.n_groups / I.T;
+        for (int g = k * gpk; g < (k + 1) * gpk; ++g) {
+          const int2 gr = D.groups[I.grp0 + g];
+          const int iu = D.rinfo[gr.x].z;
+          Huu[iu * nu + iu] += 0.5 * rho * gr.y;
+        }
+      }
+      double C[nu * nu];
+      for (int q = 0; q < nu * nu; ++q) C[q] = Huu[q];
+      chol_inplace(C, nu);
+      for (int col = 0; col < nu; ++col) {
+        double y[nu];
+        for (int r = 0; r < nu; ++r) {
+          double v = (r == col) ? 1.0 : 0.0;
+          for (int s = 0; s < r; ++s) v -= C[r * nu + s] * y[s];
+          y[r] = v / C[r * nu + r];
+        }
+        for (int r = nu - 1; r >= 0; --r) {
+          double v = y[r];
+          for (int s = r + 1; s < nu; ++s) v -= C[s * nu + r] * y[s];
+          y[r] = v / C[r * nu + r];
+        }
+        for (int r = 0; r < nu; ++r) Nm[r * nu + col] = y[r];
+      }
+    }
+    __syncwarp();
+    wmm_c<nu, nx, nu, false, false, nu, nx>(Lm, Nm, Hux, -1.0, false);
+    double* gL = ar + L.RicL + (long long)k * nu * nx;
+    double* gAcl = ar + L.RicAcl + (long long)k * nx * nx;
+    double* gN = ar + L.RicN + (long long)k * nu * nu;
+    double* gM = ar + L.RicM + (long long)k * nu * nx;
+    for (int q = lane; q < nu * nx; q += 32) gL[q] = Lm[q];
+    for (int q = lane; q < nu * nu; q += 32) gN[q] = Nm[q];
+    wmm_c<nu, nx, nu, false, true, nu, nu>(gM, Nm, sB, 1.0, false);
+    for (int q = lane; q < nx * nx; q += 32) gAcl[q] = sA[q];
+    __syncwarp();
+    wmm_c<nx, nx, nu, false, false, nu, nx>(gAcl, sB, Lm, 1.0, true);
+    {
+      Real* pk = reinterpret_cast<Real*>(ar + L.RicPk) + (long long)k * pk_stride(nx, nu);
+      const int oM = nu * nu, oL = oM + nu * nx, oA = oL + nu * nx, oB = oA + nx * nx;
+      for (int q = lane; q < nu * nu; q += 32) pk[q] = (Real)Nm[q];
+      for (int q = lane; q < nu * nx; q += 32) { pk[oM + q] = (Real)gM[q]; pk[oL + q] = (Real)Lm[q]; pk[oB + q] = (Real)sB[q]; }
+      for (int q = lane; q < nx * nx; q += 32) pk[oA + q] = (Real)gAcl[q];
+      __syncwarp();
+    }
+    if (k >= 1) {
+      build_Q(k);
+      wmm_c<nx, nx, nx, true, false, nx, nx>(tmp, sA, PA, 1.0, false);
+      wmm_c<nx, nx, nu, true, false, nx, nx>(tmp, Hux, Lm, 1.0, true);
+      for (int q = lane; q < nx * nx; q += 32) {
+        int r = q / nx, c = q % nx;
+        P[q] = Q[q] + 0.5 * (tmp[r * nx + c] + tmp[c * nx + r]);
+      }
+      __syncwarp();
+    }
+  }
+}
+
 template <typename Real>
 __global__ void k_riccati_factor(Dev<Real> D, double rho) {
-  __shared__ double scr[RIC_SCRATCH];
-  riccati_factor_warp<Real>(D, blockIdx.x, rho, scr);
+  __shared__ double scr[RIC_SCRATCH_STAGED];
+  const int kind = D.inst[blockIdx.x].kind;
+  if (kind == KIND_UNICYCLE) riccati_factor_staged<3, 2, Real>(D, blockIdx.x, rho, scr);
+  else if (kind == KIND_QUADCOPTER) riccati_factor_staged<12, 4, Real>(D, blockIdx.x, rho, scr);
+  else riccati_factor_staged<14, 7, Real>(D, blockIdx.x, rho, scr);
 }
 
 // Dv_m[u][c] = 1/(1 + coef τ γ_u λ_c) for a new penalty (the eigen factors do not depend on it).
