@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -47,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned-warm-start study")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the raw nvidia-smi clock samples (default: a temporary directory)")
     return ap.parse_args()
 
 
@@ -314,7 +317,8 @@ def main():
     for _ in range(args.warmup):
         prob.solve(opts, args.n_outer, fetch=False)
     barrier()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    clk_dir = args.clocks_dir or tempfile.gettempdir()
+    clk_path = os.path.join(clk_dir, f"nrto_clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     clk = clocks_start(clk_path)
     time.sleep(0.5)
