@@ -437,7 +437,7 @@ struct nrto_mlp {
       ep.M = B; ep.N = dims[l + 1]; ep.bias = theta + boff[l]; ep.err = d_err;
       if (l < L - 1) {
         ep.out_f32 = Z[l + 1]; ep.ld_f32 = dims[l + 1]; ep.out_bf16 = H[l + 1]; ep.ld_bf16 = dims[l + 1];
-        gemm<128, EPI_BIAS_GELU>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
+        gemm<64, EPI_BIAS_GELU>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
       } else {
         ep.out_f32 = Y; ep.ld_f32 = dims[L];
         gemm<256, EPI_BIAS>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
