@@ -471,7 +471,7 @@ struct nrto_mlp {
         // dZ_l = (dZ_{l+1} · W_l) ⊙ gelu'(Z_l)
         EpiArgs eb{};
         eb.M = B; eb.N = din; eb.out_bf16 = dZ[l]; eb.ld_bf16 = din; eb.zin = Z[l]; eb.ld_zin = din; eb.err = d_err;
-        gemm<128, EPI_GELU_BWD>(dZ[l + 1], dout, Wkn[l], dout, B, din, dout, eb);
+        gemm<64, EPI_GELU_BWD>(dZ[l + 1], dout, Wkn[l], dout, B, din, dout, eb);
         ++launches;
       }
     }
