@@ -463,7 +463,7 @@ struct nrto_mlp {
       MK(cudaGetLastError());
       EpiArgs ew{};
       ew.M = dout; ew.N = din; ew.out_f32 = grad + woff[l]; ew.ld_f32 = din; ew.err = d_err;
-      gemm<256, EPI_F32>(tA, B, tB, B, dout, din, B, ew);
+      gemm<64, EPI_F32>(tA, B, tB, B, dout, din, B, ew);
       k_colsum_bf16<<<(dout + 255) / 256, 256, 0, stream>>>(dZ[l + 1], B, dout, dout, grad + boff[l]);
       MK(cudaGetLastError());
       launches += 4;
