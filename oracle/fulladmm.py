@@ -132,9 +132,10 @@ def block2_solve(inst, lin, rho, mats, pt, lam_p, w, lam_w, e, lam_e):
 
 
 def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None,
-            n_iter: int | None = None) -> FullADMMState:
-    """Run Algorithm 1 for up to n_iter (default opts.max_iter) iterations."""
-    rho = opts.rho
+            n_iter: int | None = None, rho0: float | None = None) -> FullADMMState:
+    """Run Algorithm 1 for up to n_iter (default opts.max_iter) iterations, starting from `state`
+    (default: the zero initialization) with penalty rho0 (default opts.rho)."""
+    rho = opts.rho if rho0 is None else rho0
     s = zero_state(lin) if state is None else state
     H = P.gain_hessian_blocks(lin, inst, coef=rho)
     mats = block2_matrices(inst, lin, rho)
@@ -211,3 +212,45 @@ def solve_warm_with_fallback(inst, lin, opts: FullADMMOptions, K0, pt0, lam_p0):
     c = iterate(inst, lin, opts, zero_state(lin))
     c.iters = s.iters + c.iters
     return c, True
+
+
+def carry_state(lin, prev: FullADMMState, opts: FullADMMOptions, shifted: bool):
+    """Start of the next inner solve from the state the previous one ended in (the library's
+    inner-state carry across successive-linearization steps; the paper re-initializes each inner
+    solve).  Carried: k_v (K), p, p̃ and the scaled duals λ_p, λ_ν, λ_w, λ_e, with the penalty
+    they are scaled for.  δû, δx and e are measured from the nominal: `shifted` means the nominal
+    moved to û + δû (an accepted outer step), so in the new coordinates the previous solution is
+    δû = 0 and they restart at zero; otherwise (same nominal, e.g. a rejected step that only
+    shrinks the trust radius) they are carried too.  The solver state at the end of a solve is
+    the one at the start of its next iteration, so a residual-balancing update scheduled there
+    (same rule as in `iterate`, with the residuals of the iteration before last) is applied first.
+    Any state is a valid ADMM start, so the fixed point is the same as the cold solve's.
+    Returns (state, rho)."""
+    rho = prev.rho
+    f = 1.0
+    it = prev.iters + 1
+    A = opts.adapt_every
+    # A solve that ran to its iteration cap has no next iteration; one that stopped at its
+    # tolerance or on the stall rule stopped before the iteration cap.
+    if (A > 0 and (prev.converged or prev.stalled) and it >= 3 and it > A and (it - 1) % A == 0):
+        rp2, rd2 = prev.history[it - 3]
+        rho_new = rho
+        if rp2 > opts.adapt_mu * rd2:
+            rho_new = min(rho * opts.adapt_tau, opts.rho_max)
+        elif rd2 > opts.adapt_mu * rp2:
+            rho_new = max(rho / opts.adapt_tau, opts.rho_min)
+        f = rho / rho_new
+        rho = rho_new
+    s = zero_state(lin)
+    s.K = prev.K.copy()
+    s.p = prev.p.copy()
+    s.pt = prev.pt.copy()
+    s.lam_p = prev.lam_p * f
+    s.lam_nu = prev.lam_nu * f
+    s.lam_w = prev.lam_w * f
+    s.lam_e = prev.lam_e * f
+    if not shifted:
+        s.du = prev.du.copy()
+        s.dx = prev.dx.copy()
+        s.e = prev.e.copy()
+    return s, rho

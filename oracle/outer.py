@@ -28,6 +28,9 @@ class OuterOptions:
     r_min: float = 1e-3
     w_p: float = 10.0
     solver: str = "fulladmm"          # or "dr"
+    # FullADMM only: start every inner solve after the first from the state the previous inner
+    # solve ended in (fulladmm.carry_state); the paper re-initializes each inner solve.
+    carry: bool = False
 
 
 def cost(inst, lin, K):
@@ -38,8 +41,14 @@ def cost(inst, lin, K):
     return float(np.sum(ud * ud * inst.Ru[None, :]) + np.sum(xd * xd * inst.Qx[None, :]) + np.sum(RK * RK))
 
 
+def robust_violation(lin, K):
+    """Per-row robust constraint of Problem 2 at δû = 0: g_j(x̂) + ‖Â_j k_v + b̂_j‖ (≤ 0 when the
+    constraint holds for every disturbance of the ellipsoid, to first order around x̂)."""
+    return lin.g0 + np.sqrt(np.sum((P.Ahat_apply(lin, K) + lin.bhat) ** 2, axis=(1, 2)))
+
+
 def merit(inst, lin, K, w_p):
-    viol = lin.g0 + np.sqrt(np.sum((P.Ahat_apply(lin, K) + lin.bhat) ** 2, axis=(1, 2)))
+    viol = robust_violation(lin, K)
     return cost(inst, lin, K) + w_p * float(np.sum(np.maximum(viol, 0.0)))
 
 
@@ -52,6 +61,8 @@ class OuterResult:
     inner_iters: list = field(default_factory=list)
     inner_converged: list = field(default_factory=list)
     radii: list = field(default_factory=list)
+    max_violation: float = np.inf      # max_j of robust_violation at the accepted iterate
+    accepted_inner_converged: bool = False   # the inner solve of the last accepted step converged
 
 
 def solve(inst, opts: OuterOptions, admm: fulladmm.FullADMMOptions | None = None,
@@ -64,11 +75,19 @@ def solve(inst, opts: OuterOptions, admm: fulladmm.FullADMMOptions | None = None
     phi = merit(inst, lin, K, opts.w_p)
     r = opts.r0
     res = OuterResult(u_bar=u_hat, K=K, phi=phi)
+    res.max_violation = float(np.max(robust_violation(lin, K))) if lin.g0.size else -np.inf
+    prev = None
+    moved = False          # the nominal changed since the previous inner solve
     for _ in range(opts.n_outer):
         res.radii.append(r)
         if opts.solver == "fulladmm":
             a = fulladmm.FullADMMOptions(**{**admm.__dict__, "r_trust": r})
-            s = fulladmm.iterate(inst, lin, a)
+            if opts.carry and prev is not None and np.isfinite(prev.r_p) and np.isfinite(prev.r_d):
+                st0, rho0 = fulladmm.carry_state(lin, prev, a, shifted=moved)
+                s = fulladmm.iterate(inst, lin, a, st0, rho0=rho0)
+            else:
+                s = fulladmm.iterate(inst, lin, a)
+            prev = s
             du, K_c, n_it, conv = s.du, s.K, s.iters, s.converged
         else:
             o = dr.DROptions(**{**dropts.__dict__, "r_trust": r})
@@ -81,9 +100,13 @@ def solve(inst, opts: OuterOptions, admm: fulladmm.FullADMMOptions | None = None
         phi_c = merit(inst, lin_c, K_c, opts.w_p)
         if phi_c < phi:
             u_hat, K, lin, phi = u_c, K_c, lin_c, phi_c
+            res.max_violation = float(np.max(robust_violation(lin, K))) if lin.g0.size else -np.inf
+            res.accepted_inner_converged = bool(conv)
             r = min(1.5 * r, opts.r0)
             res.accepted.append(True)
+            moved = True
         else:
+            moved = False
             r = max(0.8 * r, opts.r_min)
             res.accepted.append(False)
     res.u_bar, res.K, res.phi = u_hat, K, phi

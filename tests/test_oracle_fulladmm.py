@@ -208,3 +208,70 @@ def test_warm_start_fallback_runs_the_cold_solve():
     ref = F.iterate(feas, linf, of)
     s2, fell2 = F.solve_warm_with_fallback(feas, linf, of, ref.K, ref.pt, ref.lam_p)
     assert not fell2 and s2.converged and np.allclose(s2.du, ref.du, atol=1e-5)
+
+
+def test_carried_start_reaches_the_interior_point_solution_of_the_next_linearization():
+    """The inner-state carry starts the next inner solve from the previous one's final state.  Any
+    ADMM start converges to the same fixed point, so after an accepted step (new nominal û + δû,
+    new linearization) the carried solve must reach the interior-point solution of the new
+    Problem 2, like a cold solve."""
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    o = F.FullADMMOptions(rho=10.0, r_trust=0.5, eps_p=1e-9, eps_d=1e-9, max_iter=30000)
+    s1 = F.iterate(inst, lin, o)
+    assert s1.converged
+    # half of the step: a new nominal whose every row is still strictly feasible at δû = 0 (the
+    # barrier solver needs a strictly feasible start), so the new solution is interior-pinned
+    lin2 = P.linearize(inst, inst.u_init + 0.5 * s1.du)
+    assert np.max(lin2.g0 + np.linalg.norm(lin2.bhat.reshape(lin2.g0.shape[0], -1), axis=1)) < -1e-3
+    du_ip, K_ip = problem2_ip(inst, lin2, r=0.4)
+    o2 = F.FullADMMOptions(rho=10.0, r_trust=0.4, eps_p=1e-9, eps_d=1e-9, max_iter=30000)
+    st, rho0 = F.carry_state(lin2, s1, o2, shifted=True)
+    assert rho0 == 10.0
+    assert np.array_equal(st.K, s1.K) and np.array_equal(st.lam_nu, s1.lam_nu)
+    assert not st.du.any() and not st.dx.any() and not st.e.any()
+    s2 = F.iterate(inst, lin2, o2, st, rho0=rho0)
+    assert s2.converged
+    assert np.allclose(s2.du, du_ip, atol=2e-6) and np.allclose(s2.K, K_ip, atol=2e-6)
+
+
+def test_carry_into_the_same_problem_is_immediately_converged():
+    """Carrying a converged state into the same linearization and trust radius (a rejected step
+    whose radius did not change) leaves nothing to do: the first iteration already meets the
+    tolerances.  A dropped or mis-scaled dual would restart the transient instead."""
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    o = F.FullADMMOptions(rho=10.0, r_trust=0.5, eps_p=1e-7, eps_d=1e-7, max_iter=30000)
+    s1 = F.iterate(inst, lin, o)
+    assert s1.converged and s1.iters > 20
+    st, rho0 = F.carry_state(lin, s1, o, shifted=False)
+    s2 = F.iterate(inst, lin, o, st, rho0=rho0)
+    assert s2.converged and s2.iters <= 2
+    assert np.allclose(s2.du, s1.du, atol=1e-6) and np.allclose(s2.K, s1.K, atol=1e-6)
+
+
+def test_carry_applies_the_pending_penalty_update_and_keeps_unscaled_duals():
+    """With residual balancing, the state at the end of a solve is the one at the start of its next
+    iteration, where a scheduled penalty change rescales the scaled duals (λ ← λ ρ_old / ρ_new).
+    The unscaled duals ρλ are unchanged by that rescale, and the carried solve still reaches the
+    interior-point solution."""
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    found = None
+    for eps in (1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7):
+        o = F.FullADMMOptions(rho=100.0, r_trust=0.5, eps_p=eps, eps_d=eps, max_iter=30000, adapt_every=1,
+                              adapt_mu=1.5)
+        s1 = F.iterate(inst, lin, o)
+        st, rho0 = F.carry_state(lin, s1, o, shifted=False)
+        if s1.converged and rho0 != s1.rho:
+            found = (o, s1, st, rho0)
+            break
+    assert found is not None, "no tolerance ended on an iteration with a pending penalty change"
+    o, s1, st, rho0 = found
+    assert np.allclose(rho0 * st.lam_nu, s1.rho * s1.lam_nu, rtol=1e-14, atol=0)
+    assert np.allclose(rho0 * st.lam_p, s1.rho * s1.lam_p, rtol=1e-14, atol=0)
+    du_ip, K_ip = problem2_ip(inst, lin, r=0.5)
+    o2 = F.FullADMMOptions(rho=100.0, r_trust=0.5, eps_p=1e-9, eps_d=1e-9, max_iter=30000, adapt_every=25)
+    s2 = F.iterate(inst, lin, o2, st, rho0=rho0)
+    assert s2.converged
+    assert np.allclose(s2.du, du_ip, atol=2e-6) and np.allclose(s2.K, K_ip, atol=2e-6)

@@ -28,3 +28,22 @@ def test_accepted_steps_decrease_merit_and_radius_schedule():
         assert np.isclose(r, expect)
     lin0 = P.linearize(inst, inst.u_init)
     assert res.phi <= O.merit(inst, lin0, np.zeros((inst.T, inst.nu, inst.nx)), 10.0)
+
+
+def test_carry_changes_the_path_not_the_outer_iterates():
+    """With every inner solve converged tightly, each outer step's candidate is the unique
+    (δû, k_v) solution of its Problem 2 whatever the inner start, so the carried and the
+    re-initialized outer loops accept the same steps and end at the same (ū, K); the carried
+    one needs fewer inner iterations after the first step."""
+    inst = tiny_unicycle()
+    a = F.FullADMMOptions(rho=10.0, eps_p=1e-10, eps_d=1e-10, max_iter=40000)
+    cold = O.solve(inst, O.OuterOptions(n_outer=4), a)
+    warm = O.solve(inst, O.OuterOptions(n_outer=4, carry=True), a)
+    assert cold.accepted == warm.accepted
+    assert all(cold.inner_converged) and all(warm.inner_converged)
+    assert np.allclose(cold.u_bar, warm.u_bar, atol=1e-7) and np.allclose(cold.K, warm.K, atol=1e-7)
+    assert warm.inner_iters[0] == cold.inner_iters[0]
+    assert sum(warm.inner_iters[1:]) < sum(cold.inner_iters[1:])
+    lin = P.linearize(inst, warm.u_bar)
+    assert np.isclose(warm.max_violation, np.max(O.robust_violation(lin, warm.K)))
+    assert warm.accepted_inner_converged
