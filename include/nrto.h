@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define NRTO_ABI_VERSION 1
+#define NRTO_ABI_VERSION 2
 
 typedef enum {
   NRTO_OK = 0,
@@ -40,7 +40,8 @@ typedef enum {
   NRTO_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed                  */
   NRTO_ERR_NOT_CONVERGED = 3,  /* some instance stopped at its iteration cap                  */
   NRTO_ERR_NUMERIC = 4,        /* non-finite input, or a non-finite residual in some instance */
-  NRTO_ERR_TIMEOUT = 5,        /* reserved                                                    */
+  NRTO_ERR_TIMEOUT = 5,        /* a bounded device wait gave up (nrto_mlp_train_step); solver
+                                  instances that time out report per-instance status 4 instead */
   NRTO_ERR_STATE = 6           /* call order violated (e.g. solve before linearize)           */
 } nrto_status;
 
@@ -99,6 +100,21 @@ typedef struct {
    * rule, rerun the instance from the cold initialization of Algorithm 1 with the full iteration
    * budget (reported iterations count both runs; NRTO_F_STATS flags it).  0 disables it. */
   int warm_fallback;
+  /* FullADMM inner-state carry (the library's warm start across successive-linearization steps;
+   * the paper re-initializes every inner solve, Algorithm 1): 1 starts each inner solve after the
+   * first from the state the previous FullADMM inner solve of the problem ended in — K, p, p̃, the
+   * scaled duals λ_p, λ_ν, λ_w, λ_e and the penalty they are scaled for; δû, δx and e as well
+   * unless the nominal moved to û + δû since (an accepted outer step), in which case they restart
+   * at zero, the previous solution's coordinates in the new linearization.  The first inner solve
+   * after nrto_problem_create, nrto_problem_update, nrto_linearize with a new nominal or the reset
+   * of nrto_solve starts cold, and so does one after a non-finite or timed-out solve.  A pending
+   * learned warm start (nrto_set_warm_start*) takes precedence.  NRTO-DR ignores it.  0 disables. */
+  int carry;
+  /* nrto_solve only: iteration cap of the inner solve of its last outer step (0: max_inner), so that
+   * the inner solves during the successive linearization can stay inexact (the paper runs 40 FullADMM
+   * iterations per outer step, Supplementary Tables VI-VIII) while the subproblem of the returned step
+   * is solved to the tolerances. */
+  int max_inner_final;
 } nrto_solver_opts;
 
 /* Per-instance sizes, for sizing output buffers. */
@@ -174,6 +190,22 @@ nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, con
 /* Warm start for the next inner solve only: K (Σ T*nu*nx), p̃ and λ_p (Σ n_rows each); λ_ν = 0. */
 nrto_status nrto_set_warm_start(nrto_problem_t p, const double* K, const double* ptilde,
                                 const double* lambda_p);
+
+/* Per-instance solve statistics of the whole batch in one call: out (host, n × width doubles,
+ * width >= NRTO_NSTAT), row i = instance i:
+ *  0 inner iterations since the last nrto_solve reset     1 iterations of the last inner solve
+ *  2 status of the last inner solve (nrto_socp_out.status codes)
+ *  3 accepted outer steps                                  4 final ρ of the last inner solve
+ *  5 NRTO-DR iterations summed over its ADMM iterations    6 1 if the last solve fell back to cold
+ *  7 status of the inner solve that produced the accepted iterate (0: no step accepted yet)
+ *  8 merit φ of the accepted iterate                       9 cost J of the accepted iterate
+ * 10 max_j g_j(x̄) + ‖Â_j k + b̂_j‖ of the accepted iterate: the largest robust-constraint value of
+ *    Problem 2 at δû = 0, linearized at the accepted nominal x̄ (≤ 0: every robust constraint holds
+ *    for all disturbances of the ellipsoid, to first order about x̄; -INFINITY without rows)
+ * 11 trust radius                                         12, 13 full r_p, r_d of the last inner solve
+ * Synchronizes the problem's stream. */
+#define NRTO_NSTAT 14
+nrto_status nrto_get_stats(nrto_problem_t p, double* out, int width);
 
 /* Named internal arrays of one instance, converted to float64 (checkpointing and testing).
  * field: one of NRTO_F_*; count must equal the field's size for that instance. */

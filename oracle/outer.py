@@ -31,6 +31,10 @@ class OuterOptions:
     # FullADMM only: start every inner solve after the first from the state the previous inner
     # solve ended in (fulladmm.carry_state); the paper re-initializes each inner solve.
     carry: bool = False
+    # FullADMM only: iteration cap of the last outer step's inner solve (0: the same cap as the
+    # others), so that the inner solves during the successive linearization can stay inexact (the
+    # paper's 40 iterations) while the returned step's subproblem is solved to tolerance.
+    max_inner_final: int = 0
 
 
 def cost(inst, lin, K):
@@ -78,10 +82,12 @@ def solve(inst, opts: OuterOptions, admm: fulladmm.FullADMMOptions | None = None
     res.max_violation = float(np.max(robust_violation(lin, K))) if lin.g0.size else -np.inf
     prev = None
     moved = False          # the nominal changed since the previous inner solve
-    for _ in range(opts.n_outer):
+    for step in range(opts.n_outer):
         res.radii.append(r)
         if opts.solver == "fulladmm":
             a = fulladmm.FullADMMOptions(**{**admm.__dict__, "r_trust": r})
+            if opts.max_inner_final > 0 and step == opts.n_outer - 1:
+                a.max_iter = opts.max_inner_final
             if opts.carry and prev is not None and np.isfinite(prev.r_p) and np.isfinite(prev.r_d):
                 st0, rho0 = fulladmm.carry_state(lin, prev, a, shifted=moved)
                 s = fulladmm.iterate(inst, lin, a, st0, rho0=rho0)

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libnrto.so")
-SOURCES = ["api.cu", "mlp.cu"]
+SOURCES = ["api.cu", "mlp.cu", "solver_uni.cu", "solver_quad.cu", "solver_arm.cu"]
 FLAGS = ["-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-lineinfo",
          "-gencode", "arch=compute_103a,code=sm_103a", "--expt-relaxed-constexpr"]
 
@@ -28,18 +28,36 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/api.cu (solver kernels) and csrc/mlp.cu (warm-start network) into libnrto.so if stale."""
+    """Compile the sources (host API and outer-loop kernels, warm-start network, one solver-kernel
+    unit per dynamics kind) into libnrto.so if stale; the units compile in parallel processes."""
     if not force and not _stale():
         return OUT
-    cmd = ["nvcc", *FLAGS, "-o", OUT + ".tmp", *[os.path.join(CSRC, s) for s in SOURCES]]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    compile_flags = [f for f in FLAGS if f != "-shared"]
+    procs = []
+    for src in SOURCES:
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
+        cmd = ["nvcc", *compile_flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append((src, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
+    failed = False
+    for src, obj, pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            failed = True
+            sys.stderr.write(f"--- {src}\n{out}{err}")
+        elif verbose:
+            sys.stderr.write(f"--- {src}\n{err}")
+    if failed:
+        raise RuntimeError("nvcc failed building libnrto.so")
+    link = ["nvcc", "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", OUT + ".tmp",
+            *[obj for _, obj, _ in procs]]
+    r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libnrto.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
+        raise RuntimeError("nvcc failed linking libnrto.so")
     os.replace(OUT + ".tmp", OUT)
     return OUT
 

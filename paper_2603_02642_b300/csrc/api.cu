@@ -19,7 +19,7 @@
 
 #include "../../include/nrto.h"
 #include "fulladmm.cuh"
-#include "dr.cuh"
+#include "solver_kernels.h"
 
 using namespace nrto;
 
@@ -135,9 +135,13 @@ __global__ void k_accept(Dev<Real> D, double r0, double r_min) {
     acc = sc[SC_PHI_CAND] < sc[SC_PHI] ? 1 : 0;
     D.is[i * NIS + IS_ACCEPT] = acc;
     D.is[i * NIS + IS_NACC] += acc;
+    D.is[i * NIS + IS_MOVED] = acc;
     if (acc) {
       D.is[i * NIS + IS_SLOT] = 1 - D.is[i * NIS + IS_SLOT];
+      D.is[i * NIS + IS_ACCST] = D.is[i * NIS + IS_STATUS];
       sc[SC_PHI] = sc[SC_PHI_CAND];
+      sc[SC_VIOL] = sc[SC_VIOLC];
+      sc[SC_COST_ACC] = sc[SC_COST];
       sc[SC_RTRUST] = fmin(1.5 * sc[SC_RTRUST], r0);
     } else {
       sc[SC_RTRUST] = fmax(0.8 * sc[SC_RTRUST], r_min);
@@ -158,6 +162,8 @@ __global__ void k_reset_outer(Dev<Real> D, double r0) {
     D.is[i * NIS + IS_SLOT] = 0;
     D.is[i * NIS + IS_CUMITERS] = 0;
     D.is[i * NIS + IS_NACC] = 0;
+    D.is[i * NIS + IS_ACCST] = 0;
+    D.is[i * NIS + IS_MOVED] = 0;
     D.sc[(long long)i * NSC + SC_RTRUST] = r0;
   }
   for (int q = threadIdx.x; q < I.T * I.nu * I.nx; q += blockDim.x) ar[L.Kacc + q] = 0.0;
@@ -225,6 +231,9 @@ struct nrto_problem {
   double* d_ustage = nullptr;
   bool linearized = false;
   bool warm_pending = false;
+  // A FullADMM inner solve ran since the last reset, so its final state can start the next one
+  // (nrto_solver_opts.carry).
+  bool carry_ok = false;
   long long launches = 0;
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;   // around each solver-kernel launch
@@ -417,15 +426,17 @@ void launch_linearize(nrto_problem* P, int slot_sel) {
   P->check_launch("k_gram");
 }
 
+// One persistent launch of a solver kernel (FullADMM or NRTO-DR) for the instances of one kind:
+// as many CTAs as fit on the GPU, at most one per instance; CTAs take instances from the queue.
 template <int NX, int NU, typename Real>
-void launch_fa_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
-  auto kern = k_fulladmm<NX, NU, Real>;
-  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kl.smem));
+void launch_solver_kind(nrto_problem* P, int solver, const KindLaunch& kl, SolveParams sp) {
+  using SK = SolverKernel<NX, NU, Real>;
+  const char* name = solver == SOLVER_KERNEL_FULLADMM ? "k_fulladmm" : "k_dr";
   int dev = 0, nsm = 0, per_sm = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FACfg<NX, NU, Real>::NT, kl.smem));
-  if (per_sm < 1) fail(NRTO_ERR_CUDA, "solver kernel does not fit on an SM");
+  CK(SK::configure(solver, kl.smem, &per_sm));
+  if (per_sm < 1) fail(NRTO_ERR_CUDA, std::string(name) + " does not fit on an SM");
   const int grid = std::min(kl.count, nsm * per_sm);
   sp.chunk = kl.chunk; sp.max_rows = kl.max_rows; sp.tmax = kl.tmax; sp.n_order = kl.count;
   sp.order0 = kl.order0; sp.queue_idx = kl.kind;
@@ -435,13 +446,19 @@ void launch_fa_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, P->stream));
   }
-  kern<<<grid, FACfg<NX, NU, Real>::NT, kl.smem, P->stream>>>(P->dev<Real>(), sp);
-  P->check_launch("k_fulladmm");
+  const cudaError_t le = SK::launch(solver, grid, kl.smem, P->stream, P->dev<Real>(), sp);
+  ++P->launches;
+  if (le != cudaSuccess) fail(NRTO_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(le));
   if (P->profiling) {
     CK(cudaEventRecord(e1, P->stream));
     P->prof_events.push_back({e0, e1});
     P->prof_launches++;
   }
+}
+
+template <int NX, int NU, typename Real>
+void launch_fa_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
+  launch_solver_kind<NX, NU, Real>(P, SOLVER_KERNEL_FULLADMM, kl, sp);
 }
 
 template <typename Real>
@@ -450,7 +467,8 @@ void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
   SolveParams sp{};
   sp.rho = o.rho; sp.eps_p = o.eps_p; sp.eps_d = o.eps_d;
   sp.alpha = o.alpha; sp.r_chi = o.r_chi; sp.sigma = o.sigma; sp.eps_dr = o.eps_dr;
-  sp.max_iter = o.max_inner; sp.check = o.check; sp.warm = P->warm_pending ? 1 : 0; sp.max_dr = o.max_dr;
+  sp.max_iter = o.max_inner; sp.check = o.check; sp.max_dr = o.max_dr;
+  sp.warm = P->warm_pending ? 1 : ((o.carry && P->carry_ok && o.solver == NRTO_SOLVER_FULLADMM) ? 2 : 0);
   sp.adapt_every = o.adapt_every; sp.stall_every = o.stall_every;
   sp.adapt_mu = o.adapt_mu; sp.adapt_tau = o.adapt_tau; sp.rho_min = o.rho_min; sp.rho_max = o.rho_max;
   sp.stall_ratio = o.stall_ratio;
@@ -469,8 +487,10 @@ void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
       else if (k == KIND_QUADCOPTER) launch_fa_kind<12, 4, Real>(P, kl, sp);
       else launch_fa_kind<14, 7, Real>(P, kl, sp);
     }
+    P->carry_ok = true;
   } else {
     launch_dr<Real>(P, o, sp);
+    P->carry_ok = false;
   }
 }
 
@@ -631,6 +651,8 @@ void check_opts(const nrto_solver_opts* o) {
   if (o->adapt_every > 0 && !(o->adapt_mu > 1 && o->adapt_tau > 1 && o->rho_min > 0 && o->rho_max >= o->rho_min))
     fail(NRTO_ERR_INVALID, "residual balancing needs mu > 1, tau > 1, 0 < rho_min <= rho_max");
   if (o->stall_every > 0 && !(o->stall_ratio > 0 && o->stall_ratio < 1)) fail(NRTO_ERR_INVALID, "stall_ratio must be in (0,1)");
+  if (o->carry != 0 && o->carry != 1) fail(NRTO_ERR_INVALID, "carry must be 0 or 1");
+  if (o->max_inner_final < 0 || o->max_inner_final > 1000000) fail(NRTO_ERR_INVALID, "max_inner_final out of range");
   if (o->solver == NRTO_SOLVER_DR) {
     if (!(o->alpha > 0 && o->alpha < 2)) fail(NRTO_ERR_INVALID, "alpha must be in (0,2)");
     if (!(o->r_chi > 0) || !(o->sigma > 0)) fail(NRTO_ERR_INVALID, "r_chi and sigma must be positive");
@@ -1091,6 +1113,7 @@ nrto_status nrto_problem_update(nrto_problem_t p, const nrto_problem_desc* descs
     upload_params(p, descs);
     if (p->prec == NRTO_PREC_FP64) launch_setup<double>(p); else launch_setup<float>(p);
     p->linearized = false;
+    p->carry_ok = false;
     return NRTO_OK;
   } catch (const std::exception& e) {
     return handle(e);
@@ -1112,6 +1135,7 @@ nrto_status nrto_linearize(nrto_problem_t p, const double* u_hat) {
                            sizeof(double) * I.T * I.nu, cudaMemcpyHostToDevice, p->stream));
       }
       CK(cudaStreamSynchronize(p->stream));
+      p->carry_ok = false;   // a new nominal from the caller: the next inner solve starts cold
     }
     if (p->prec == NRTO_PREC_FP64) launch_linearize<double>(p, -1); else launch_linearize<float>(p, -1);
     p->linearized = true;
@@ -1180,13 +1204,17 @@ nrto_status nrto_solve(nrto_problem_t p, const nrto_solver_opts* o, int n_outer,
     if (f64) k_reset_outer<double><<<p->n, 128, 0, p->stream>>>(p->dev<double>(), o->r0);
     else k_reset_outer<float><<<p->n, 128, 0, p->stream>>>(p->dev<float>(), o->r0);
     p->check_launch("k_reset_outer");
+    p->carry_ok = false;
     k_scatter_uhat<<<p->n, 128, 0, p->stream>>>(p->d_slot_arena[0], p->d_inst, p->d_ustage, p->d_uoff, p->n);
     p->check_launch("k_scatter_uhat");
     if (f64) { launch_linearize<double>(p, -1); launch_merit_current<double>(p, o->w_p); }
     else { launch_linearize<float>(p, -1); launch_merit_current<float>(p, o->w_p); }
     p->linearized = true;
+    nrto_solver_opts last = *o;
+    if (o->max_inner_final > 0) last.max_inner = o->max_inner_final;
     for (int it = 0; it < n_outer; ++it) {
-      if (f64) launch_outer_step<double>(p, *o); else launch_outer_step<float>(p, *o);
+      const nrto_solver_opts& oi = (it == n_outer - 1) ? last : *o;
+      if (f64) launch_outer_step<double>(p, oi); else launch_outer_step<float>(p, oi);
     }
     if (u_bar) copy_arena_field(p, GF_UHAT, u_bar);
     if (K) copy_arena_field(p, GF_KACC, K);
@@ -1253,6 +1281,31 @@ nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, con
     p->check_launch("k_scatter_warm");
     CK(cudaStreamSynchronize(p->stream));   // the network's output buffer may be reused after return
     p->warm_pending = true;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_get_stats(nrto_problem_t p, double* out, int width) {
+  try {
+    if (!p || !out) fail(NRTO_ERR_INVALID, "null argument");
+    if (width < NRTO_NSTAT) fail(NRTO_ERR_INVALID, "width must be >= NRTO_NSTAT");
+    std::vector<int> is(p->n * NIS);
+    std::vector<double> sc(p->n * NSC);
+    CK(cudaMemcpyAsync(is.data(), p->d_is, sizeof(int) * is.size(), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(sc.data(), p->d_sc, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    for (int i = 0; i < p->n; ++i) {
+      const int* a = is.data() + (size_t)i * NIS;
+      const double* c = sc.data() + (size_t)i * NSC;
+      double* o = out + (size_t)i * width;
+      o[0] = a[IS_CUMITERS]; o[1] = a[IS_ITERS]; o[2] = a[IS_STATUS]; o[3] = a[IS_NACC];
+      o[4] = c[SC_RHO]; o[5] = a[IS_DRITERS]; o[6] = a[IS_FALLBACK]; o[7] = a[IS_ACCST];
+      o[8] = c[SC_PHI]; o[9] = c[SC_COST_ACC]; o[10] = c[SC_VIOL]; o[11] = c[SC_RTRUST];
+      o[12] = c[SC_RP]; o[13] = c[SC_RD];
+      for (int k = NRTO_NSTAT; k < width; ++k) o[k] = 0.0;
+    }
     return NRTO_OK;
   } catch (const std::exception& e) {
     return handle(e);
@@ -1368,29 +1421,7 @@ extern "C" nrto_status nrto_solve_noalloc(const nrto_problem_desc* descs, int n,
 
 template <int NX, int NU, typename Real>
 void launch_dr_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
-  auto kern = k_dr<NX, NU, Real>;
-  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kl.smem));
-  int dev = 0, nsm = 0, per_sm = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FACfg<NX, NU, Real>::NT, kl.smem));
-  if (per_sm < 1) fail(NRTO_ERR_CUDA, "DR kernel does not fit on an SM");
-  const int grid = std::min(kl.count, nsm * per_sm);
-  sp.chunk = kl.chunk; sp.max_rows = kl.max_rows; sp.tmax = kl.tmax; sp.n_order = kl.count;
-  sp.order0 = kl.order0; sp.queue_idx = kl.kind;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (P->profiling) {
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventRecord(e0, P->stream));
-  }
-  kern<<<grid, FACfg<NX, NU, Real>::NT, kl.smem, P->stream>>>(P->dev<Real>(), sp);
-  P->check_launch("k_dr");
-  if (P->profiling) {
-    CK(cudaEventRecord(e1, P->stream));
-    P->prof_events.push_back({e0, e1});
-    P->prof_launches++;
-  }
+  launch_solver_kind<NX, NU, Real>(P, SOLVER_KERNEL_DR, kl, sp);
 }
 
 // NRTO-DR: gain-solve factors for (Q_v + r_χ I + σ Σ Â_jᵀÂ_j), then one persistent launch per kind.

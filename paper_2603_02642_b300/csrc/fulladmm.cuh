@@ -1153,18 +1153,43 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   B2Smem<NX, NU, Real> b2;
   b2.carve(reinterpret_cast<char*>(sm.buf[0].lam), 2 * FASmem<NX, NU, Real>::buf_bytes(sp.chunk, sp.max_rows), I.T);
 
-  // ---- initialization (Algorithm 1): λ_p, λ_ν, k, p <- 0 (or a warm start of k, p̃, λ_p) ----
-  for (long long e = tid; e < I.n_ent; e += NT) lam[I.ent0 + e] = (Real)0;
+  // ---- initialization (Algorithm 1): λ_p, λ_ν, k, p <- 0.  winit 1: a learned warm start of k, p̃,
+  // λ_p (p = p̃).  winit 2 (inner-state carry): the previous inner solve's final state is kept — k,
+  // p, p̃, λ_p, λ_ν, λ_w, λ_e and the penalty they are scaled for; δû, δx, e and ℓ too unless the
+  // nominal moved to û + δû since (then the previous solution is δû = 0 in the new coordinates).
+  // A previous solve that ended on a non-finite residual or a copy timeout is not carried. ----
+  const int prev_st = isr[IS_STATUS];
+  const bool carry = sp.warm == 2 && (prev_st == ST_CONVERGED || prev_st == ST_MAXITER || prev_st == ST_STALLED);
+  const int winit = carry ? 2 : (sp.warm == 1 ? 1 : 0);
+  const bool keep_dx = carry && isr[IS_MOVED] == 0;
+  if (winit != 2)
+    for (long long e = tid; e < I.n_ent; e += NT) lam[I.ent0 + e] = (Real)0;
   for (int r = tid; r < n_rows; r += NT) {
     const long long R = I.row0 + r;
-    if (!sp.warm) { D.p[R] = 0.0; D.pt[R] = 0.0; D.lamp[R] = 0.0; }
-    else { D.p[R] = D.pt[R]; }
-    D.w[R] = 0.0; D.lamw[R] = 0.0; D.s[R] = 1.0; D.sr[R] = (Real)1; D.ell[R] = 0.0;
+    if (winit == 0) { D.p[R] = 0.0; D.pt[R] = 0.0; D.lamp[R] = 0.0; }
+    else if (winit == 1) { D.p[R] = D.pt[R]; }
+    if (winit != 2) D.lamw[R] = 0.0;
+    if (!keep_dx) D.ell[R] = 0.0;
+    D.w[R] = 0.0; D.s[R] = 1.0; D.sr[R] = (Real)1;
   }
-  for (int q = tid; q < T * NU; q += NT) ar[L.du + q] = 0.0;
-  for (int q = tid; q < (T + 1) * NX; q += NT) { ar[L.dx + q] = 0.0; ar[L.e + q] = 0.0; ar[L.lam_e + q] = 0.0; }
-  if (!sp.warm)
+  if (!keep_dx) {
+    for (int q = tid; q < T * NU; q += NT) ar[L.du + q] = 0.0;
+    for (int q = tid; q < (T + 1) * NX; q += NT) { ar[L.dx + q] = 0.0; ar[L.e + q] = 0.0; }
+  }
+  if (winit != 2)
+    for (int q = tid; q < (T + 1) * NX; q += NT) ar[L.lam_e + q] = 0.0;
+  if (winit == 0)
     for (int q = tid; q < T * NU * NX; q += NT) ar[L.K1 + q] = 0.0;
+  if (winit == 2) {
+    // start at the penalty the carried duals are scaled for (block 2 and the gain divisors follow it)
+    rho = sc[SC_RHOD];
+    rho_done = rho;
+    if (rho != sp.rho) {
+      gain_divisors<Real>(D, inst, rho);
+      __syncthreads();
+      if (warp == 0) riccati_factor_warp<Real>(D, inst, rho, ric_scr);
+    }
+  }
   __syncthreads();
   // Gtᵀ of the initial gains into Gt1 ("current"); Gt0 is the "previous" table
   for (int q = tid; q < (T + 1) * NU * NX; q += NT) {
@@ -1442,7 +1467,9 @@ done:
     sc[SC_RP] = r_p; sc[SC_RD] = r_d;
     sc[SC_RPP] = sqrt(sc[SC_SCAL_RPP]); sc[SC_RDP] = rho_done * sqrt(sc[SC_SCAL_RDP]);
     sc[SC_RHO] = rho_done;
+    sc[SC_RHOD] = rho;
     isr[IS_STATUS] = status; isr[IS_ITERS] = iters; isr[IS_CUMITERS] += iters;
+    isr[IS_MOVED] = 0;
   }
   tm.flush(D.phase_cycles);
   __syncthreads();
@@ -1481,8 +1508,9 @@ __global__ void __launch_bounds__(FACfg<NX, NU, Real>::NT, FACfg<NX, NU, Real>::
       __syncthreads();
       if (threadIdx.x == 0) isr[IS_FALLBACK] = 1;
       {
-        // residual balancing may have refactored block 2 and the gain divisors for another ρ
-        if (sp.adapt_every > 0) {
+        // residual balancing or a carried penalty may have refactored block 2 and the gain
+        // divisors for another ρ
+        if (sp.adapt_every > 0 || sp.warm == 2) {
           gain_divisors<Real>(D, inst, sp.rho);
           __syncthreads();
           if ((threadIdx.x >> 5) == 0) riccati_factor_warp<Real>(D, inst, sp.rho, ric_scr);

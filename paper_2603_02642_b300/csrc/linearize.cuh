@@ -655,7 +655,7 @@ __global__ void k_gain_to_gt(Dev<Real> D, int kbuf, int gtbuf) {
 // the compute precision, sums in FP64.
 template <int NX, int NU, typename Real>
 __device__ void merit_rows(const Dev<Real>& D, const Inst& I, const double* Gt, const LinSlot<Real>& S,
-                           Real* gts, double& vio) {
+                           Real* gts, double& vio, double& vmax) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q = threadIdx.x; q < (I.T + 1) * NU * NX; q += blockDim.x) gts[q] = (Real)Gt[q];
   __syncthreads();
@@ -680,7 +680,11 @@ __device__ void merit_rows(const Dev<Real>& D, const Inst& I, const double* Gt, 
       }
     }
     n2 = warp_sum(n2);
-    if (lane == 0) vio += fmax(0.0, S.g0[R] + sqrt((double)n2));
+    if (lane == 0) {
+      const double v = S.g0[R] + sqrt((double)n2);
+      vio += fmax(0.0, v);
+      vmax = fmax(vmax, v);
+    }
   }
 }
 
@@ -700,6 +704,7 @@ __global__ void k_merit(Dev<Real> D, int slot_sel, int kbuf, int gtbuf, double w
   const double* K = ar + kbuf_off(L, kbuf);
   __shared__ double red[4 * 32];
   double cst = 0.0, vio = 0.0, z0 = 0.0, z1 = 0.0;
+  double vmax = -INFINITY;   // no rows: every robust constraint holds trivially
   for (int q = threadIdx.x; q < I.T * nu; q += blockDim.x) {
     double d = sa[SL.u_hat + q] - ar[L.uref + q % nu];
     cst += ar[L.Ru + q % nu] * d * d;
@@ -713,13 +718,20 @@ __global__ void k_merit(Dev<Real> D, int slot_sel, int kbuf, int gtbuf, double w
     cst += kv * kv;
   }
   Real* gts = reinterpret_cast<Real*>(merit_smem);
-  if (I.kind == KIND_UNICYCLE) merit_rows<3, 2, Real>(D, I, Gt, S, gts, vio);
-  else if (I.kind == KIND_QUADCOPTER) merit_rows<12, 4, Real>(D, I, Gt, S, gts, vio);
-  else merit_rows<14, 7, Real>(D, I, Gt, S, gts, vio);
+  if (I.kind == KIND_UNICYCLE) merit_rows<3, 2, Real>(D, I, Gt, S, gts, vio, vmax);
+  else if (I.kind == KIND_QUADCOPTER) merit_rows<12, 4, Real>(D, I, Gt, S, gts, vio, vmax);
+  else merit_rows<14, 7, Real>(D, I, Gt, S, gts, vio, vmax);
   block_sum4(cst, vio, z0, z1, red);
+  vmax = block_max(vmax, red);
   if (threadIdx.x == 0) {
     D.sc[i * NSC + out_idx] = cst + w_p * vio;
     D.sc[i * NSC + SC_COST] = cst;
+    if (out_idx == SC_PHI) {
+      D.sc[i * NSC + SC_VIOL] = vmax;
+      D.sc[i * NSC + SC_COST_ACC] = cst;
+    } else {
+      D.sc[i * NSC + SC_VIOLC] = vmax;
+    }
   }
 }
 

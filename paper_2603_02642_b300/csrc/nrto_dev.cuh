@@ -119,9 +119,14 @@ NRTO_HD SlotL slot_layout(int nx, int nu, int T) {
 }
 
 // Per-instance scalar record (double) and integer record.
+// SC_RHOD: the penalty the stored scaled duals are scaled for (the start penalty of a carried inner
+// solve); SC_VIOL / SC_VIOLC: max_j g_j(x̄) + ‖Â_j k + b̂_j‖ of the accepted / candidate iterate.
 enum : int { SC_RTRUST = 0, SC_RP, SC_RD, SC_RPP, SC_RDP, SC_SCAL_RP, SC_SCAL_RD, SC_SCAL_RPP, SC_SCAL_RDP,
-             SC_PHI, SC_PHI_CAND, SC_COST, SC_RHO, SC_RDR, NSC = 16 };
-enum : int { IS_STATUS = 0, IS_ITERS, IS_SLOT, IS_ACCEPT, IS_DRITERS, IS_CUMITERS, IS_NACC, IS_FALLBACK, NIS = 8 };
+             SC_PHI, SC_PHI_CAND, SC_COST, SC_RHO, SC_RDR, SC_RHOD, SC_VIOL, SC_VIOLC, SC_COST_ACC, NSC = 20 };
+// IS_ACCST: status of the inner solve whose candidate became the accepted iterate (0: none yet);
+// IS_MOVED: the nominal moved to û + δû since the last inner solve (an accepted outer step).
+enum : int { IS_STATUS = 0, IS_ITERS, IS_SLOT, IS_ACCEPT, IS_DRITERS, IS_CUMITERS, IS_NACC, IS_FALLBACK, IS_ACCST,
+             IS_MOVED, NIS = 10 };
 
 template <typename Real>
 struct LinSlot {
@@ -179,6 +184,20 @@ __device__ inline void block_sum4(double& a, double& b, double& c, double& d, do
   a = b = c = d = 0.0;
   for (int i = 0; i < nw; ++i) { a += red[4 * i]; b += red[4 * i + 1]; c += red[4 * i + 2]; d += red[4 * i + 3]; }
   __syncthreads();
+}
+
+// Block-wide maximum of one double (same scratch as block_sum4); all threads get the result.
+__device__ inline double block_max(double a, double* red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+  __syncthreads();
+  if (lane == 0) red[wid] = a;
+  __syncthreads();
+  a = red[0];
+  for (int i = 1; i < nw; ++i) a = fmax(a, red[i]);
+  __syncthreads();
+  return a;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("NRTO_LIB", os.path.join(HERE, "libnrto.so"))
 
 PREC_FP64, PREC_MIXED = 0, 1
+NSTAT = 14   # NRTO_NSTAT
 SOLVER_DR, SOLVER_FULLADMM = 0, 1
 
 (F_XHAT, F_UHAT, F_A, F_B, F_G0, F_BHAT, F_BVEC, F_LAMNU, F_K, F_DU, F_P, F_PT, F_LAMP, F_GM, F_KACC,
@@ -46,7 +47,8 @@ class SolverOpts(C.Structure):
                 ("r0", C.c_double), ("r_min", C.c_double), ("w_p", C.c_double),
                 ("adapt_every", C.c_int), ("adapt_mu", C.c_double), ("adapt_tau", C.c_double),
                 ("rho_min", C.c_double), ("rho_max", C.c_double),
-                ("stall_every", C.c_int), ("stall_ratio", C.c_double), ("warm_fallback", C.c_int)]
+                ("stall_every", C.c_int), ("stall_ratio", C.c_double), ("warm_fallback", C.c_int),
+                ("carry", C.c_int), ("max_inner_final", C.c_int)]
 
 
 class InstanceInfo(C.Structure):
@@ -104,6 +106,8 @@ def load():
     lib.nrto_mlp_profile.restype = C.c_int
     lib.nrto_mlp_kernel_launches.argtypes = [P]
     lib.nrto_mlp_kernel_launches.restype = C.c_longlong
+    lib.nrto_get_stats.argtypes = [P, _dp, C.c_int]
+    lib.nrto_get_stats.restype = C.c_int
     lib.nrto_kernel_launches.argtypes = [P]
     lib.nrto_kernel_launches.restype = C.c_longlong
     lib.nrto_last_error.restype = C.c_char_p
@@ -157,12 +161,15 @@ class Options:
     stall_every: int = 0
     stall_ratio: float = 0.9
     warm_fallback: int = 0
+    carry: int = 0
+    max_inner_final: int = 0
 
     def c(self) -> SolverOpts:
         return SolverOpts(self.solver, self.rho, self.alpha, self.r_chi, self.sigma, self.eps_p, self.eps_d,
                           self.eps_dr, self.max_inner, self.max_dr, self.check, self.r0, self.r_min, self.w_p,
                           self.adapt_every, self.adapt_mu, self.adapt_tau, self.rho_min, self.rho_max,
-                          self.stall_every, self.stall_ratio, self.warm_fallback)
+                          self.stall_every, self.stall_ratio, self.warm_fallback, self.carry,
+                          self.max_inner_final)
 
 
 _ZERO1 = np.zeros(1)
@@ -333,6 +340,15 @@ class Problem:
 
     def kernel_launches(self):
         return int(load().nrto_kernel_launches(self._h))
+
+    STATS = ["cum_iters", "iters", "status", "n_accepted", "rho", "dr_iters", "fallback", "accepted_status",
+             "merit", "cost", "max_violation", "trust_radius", "r_p", "r_d"]
+
+    def stats(self):
+        """Per-instance statistics of the batch (nrto_get_stats): a dict of arrays named by STATS."""
+        out = np.zeros((self.n, NSTAT))
+        _check(load().nrto_get_stats(self._h, _ptr(out), NSTAT))
+        return {k: out[:, i] for i, k in enumerate(self.STATS)}
 
 
 def solve_noalloc(instances, opts: Options, n_outer=10, precision=PREC_FP64, stream=None):

@@ -47,3 +47,11 @@ def test_carry_changes_the_path_not_the_outer_iterates():
     lin = P.linearize(inst, warm.u_bar)
     assert np.isclose(warm.max_violation, np.max(O.robust_violation(lin, warm.K)))
     assert warm.accepted_inner_converged
+
+
+def test_final_step_cap_applies_to_the_last_inner_solve_only():
+    inst = tiny_unicycle()
+    a = F.FullADMMOptions(rho=10.0, max_iter=5)
+    res = O.solve(inst, O.OuterOptions(n_outer=3, carry=True, max_inner_final=3000), a)
+    assert res.inner_iters[:2] == [5, 5]
+    assert res.inner_iters[2] > 5 and res.inner_converged[2]
