@@ -1,21 +1,30 @@
-"""Benchmark: NRTO solves/sec of the batched, mixed-precision FullADMM path on one B300.
+"""Benchmark: NRTO solves/sec at residual <= 1e-4 on one B300, batched + warm-started + mixed
+precision against the plain cold-started FP64 GPU form at batch 1.
 
-One step = one full NRTO solve (10 successive-linearization outer steps, each with a FullADMM
-inner solve that stops at full residuals <= 1e-4 or after --max-inner iterations; the default 40
-iterations and rho = 10 are the paper's FullADMM settings, Supplementary Tables VI-VIII) of every
-instance of the batched workload (2048 seeded instances, 50/50 unicycle T~U{20..200} with 1-20
-obstacles and quadcopter T~U{50..150} with 1-15 obstacles).  Inputs are resident in HBM before the
-timed region; the row arrays (several GB) exceed the 126 MB L2, so no flush is needed.
+Workload: the 2048-instance batch (seeded; 50/50 unicycle T~U{20..200} with 1-20 obstacles and
+quadcopter T~U{50..150} with 1-15 obstacles).  One step = one complete NRTO solve of every instance:
+10 successive-linearization steps; the inner FullADMM solves of the first nine stop after the
+paper's 40 iterations (inexact, Supplementary Tables VI-VIII), the last one runs to full residuals
+<= 1e-4 (cap 2000), all with residual balancing every 25 iterations and the stall stop.
 
-`--impl reference` times the CPU oracle (the reference arm of this project) on a bounded sample of
-the same workload.  Under torchrun, every rank solves its own batch (weak scaling); there is no
-collective on the data path, only a barrier and a max-reduction of the timings.
+A solve counts when (i) the inner solve that produced the returned (accepted) iterate terminated at
+full residuals r_p, r_d <= 1e-4 and (ii) every robust constraint holds there:
+max_j g_j(x̄) + ‖Â_j k + b̂_j‖ <= 1e-4 (Problem 2 at δû = 0, linearized at the returned trajectory).
+`value` = counted solves per second of the batched + warm-started (inner-state carry across outer
+steps) + mixed-precision form; the same metric is measured for the plain form — FP64, one instance
+per launch (batch 1, looped over a seeded sample of the workload), cold start of every inner solve,
+same schedule and tolerances — and their ratio is reported.
+
+Inputs are resident in HBM before the timed region; the row arrays (several GB) exceed the 126 MB L2.
+`--impl reference` times the CPU oracle (this project's reference arm) on the machine's host cores.
+Under torchrun every rank solves its own batch (weak scaling; no collective on the data path).
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -28,7 +37,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "NRTO solves/sec at residual <=1e-4 (batched mixed-precision FullADMM, 10 outer steps)"
+METRIC = "NRTO solves/sec at residual ≤1e-4: warm-start+batched vs plain, 1×B300"
 UNIT = "solves/s"
 
 
@@ -40,14 +49,20 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--n-outer", type=int, default=10)
-    ap.add_argument("--max-inner", type=int, default=40)
+    ap.add_argument("--max-inner", type=int, default=40, help="inner cap of the first n_outer-1 outer steps")
+    ap.add_argument("--max-inner-final", type=int, default=2000, help="inner cap of the last outer step")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--rho", type=float, default=10.0)
-    ap.add_argument("--adapt", type=int, default=0, help="residual-balancing period (0 = fixed rho)")
-    ap.add_argument("--stall", type=int, default=0, help="stall-stop period (0 = off)")
+    ap.add_argument("--adapt", type=int, default=25, help="residual-balancing period (0 = fixed rho)")
+    ap.add_argument("--stall", type=int, default=100, help="stall-stop period (0 = off)")
+    ap.add_argument("--carry", type=int, default=1, help="inner-state carry across outer steps")
+    ap.add_argument("--feas-tol", type=float, default=1e-4)
+    ap.add_argument("--plain-n", type=int, default=16, help="instances of the plain batch-1 FP64 arm")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned-warm-start study")
+    ap.add_argument("--no-configs", action="store_true", help="skip the single-instance configurations")
     ap.add_argument("--clocks-dir", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: a temporary directory)")
     return ap.parse_args()
@@ -62,59 +77,129 @@ def workload(n, rank):
     return W.batched_mix(n, base_seed=10000 + rank * n)
 
 
-def row_entries(inst):
-    """Ragged row entries of one instance (state rows: (t+1)·nx, control bounds: nx)."""
+def entries(inst):
+    """Ragged row entries of one instance: state rows S ((t+1)·nx each) and control rows C (nx each)."""
     per_t = inst.n_obs * (inst.link_spheres.shape[0] if inst.kind == 2 else 1)
     per_t += int(np.isfinite(inst.x_lo).sum() + np.isfinite(inst.x_hi).sum())
-    nst = sum((t + 1) * inst.nx for t in range(1, inst.T + 1))
-    nc = int(np.isfinite(inst.u_lo).sum() + np.isfinite(inst.u_hi).sum())
-    return per_t * nst + nc * inst.T * inst.nx
+    S = per_t * sum((t + 1) * inst.nx for t in range(1, inst.T + 1))
+    C = int(np.isfinite(inst.u_lo).sum() + np.isfinite(inst.u_hi).sum()) * inst.T * inst.nx
+    return S, C
+
+
+def solver_options(args, carry=None):
+    from paper_2603_02642_b300 import nrto
+    return nrto.Options(rho=args.rho, max_inner=args.max_inner, max_inner_final=args.max_inner_final,
+                        eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0, adapt_every=args.adapt,
+                        stall_every=args.stall, stall_ratio=0.9, carry=args.carry if carry is None else carry)
+
+
+def counted(st, tol):
+    """Solves that count: the returned iterate's inner solve converged and its robust constraints hold."""
+    return (st["accepted_status"] == 1) & (st["max_violation"] <= tol)
 
 
 # ---------------------------------------------------------------------------------------------
-# CPU oracle baseline (bounded sample)
+# CPU oracle (the reference arm and the cpu_baseline): nproc worker processes
 # ---------------------------------------------------------------------------------------------
-def oracle_estimate(instances, n_outer, max_inner, budget_s=20.0, seed=0):
-    """Time the FP64 NumPy oracle on a bounded sample of the workload and scale to solves/s.
-
-    Sample: instances drawn with a fixed seed among those whose rows hold <= 60k entries; for each,
-    one linearization and one complete FullADMM inner solve (tolerance 1e-4, cap max_inner), until
-    `budget_s` of CPU time is used.  Scaling: oracle seconds per (row entry × inner iteration) and
-    per (row entry × linearization) from the sample, times the workload's row entries, the sample's
-    mean inner iterations per outer step, n_outer outer steps and two linearizations per outer step."""
-    from oracle import fulladmm as F, problem as P
-
-    rng = np.random.default_rng(seed)
-    cand = [i for i in rng.permutation(len(instances)) if row_entries(instances[i]) <= 60000]
-    t_in = t_lin = s_it = s_ent = 0.0
-    iters, used = [], []
-    t_start = time.perf_counter()
-    for i in cand:
-        if time.perf_counter() - t_start > budget_s and used:
-            break
-        inst = instances[i]
+def _oracle_task(task):
+    """One oracle task in a worker process (spawned; BLAS single-threaded)."""
+    from oracle import fulladmm as F, outer as O, problem as P
+    kind, inst, prm = task
+    if kind == "cost":
+        # per-linearization and per-inner-iteration cost of one instance
         t0 = time.perf_counter()
         lin = P.linearize(inst, inst.u_init)
         t1 = time.perf_counter()
-        s = F.iterate(inst, lin, F.FullADMMOptions(rho=10.0, r_trust=2.0, max_iter=max_inner))
+        F.iterate(inst, lin, F.FullADMMOptions(rho=prm["rho"], r_trust=2.0, check=False), n_iter=prm["k_it"])
         t2 = time.perf_counter()
-        e = row_entries(inst)
-        t_lin += t1 - t0
-        t_in += t2 - t1
-        s_it += s.iters * e
-        s_ent += e
-        iters.append(s.iters)
-        used.append(int(i))
-    c_it = t_in / s_it
-    c_lin = t_lin / s_ent
-    m_it = float(np.mean(iters))
-    total_entries = float(sum(row_entries(x) for x in instances))
-    per_step_s = n_outer * (m_it * c_it * total_entries + 2 * c_lin * total_entries)
-    return dict(value=len(instances) / per_step_s, unit=UNIT, cores=1, kind="oracle",
-                sample=(f"{len(used)} workload instances (ids {used}) with <=60k row entries: one linearization "
-                        f"+ one FullADMM inner solve each (mean {m_it:.0f} iterations), {t_in + t_lin:.1f} s of "
-                        f"single-thread CPU; scaled per row entry to the {len(instances)}-instance workload "
-                        f"x {n_outer} outer steps"))
+        return {"kind": "cost", "S": sum(entries(inst)), "t_lin": t1 - t0, "t_it": (t2 - t1) / prm["k_it"]}
+    # a complete solve with the benchmark's schedule
+    t0 = time.perf_counter()
+    res = O.solve(inst, O.OuterOptions(n_outer=prm["n_outer"], r0=2.0, carry=bool(prm["carry"]),
+                                       max_inner_final=prm["max_inner_final"]),
+                  admm=F.FullADMMOptions(rho=prm["rho"], max_iter=prm["max_inner"], eps_p=1e-4, eps_d=1e-4,
+                                         adapt_every=prm["adapt"], stall_every=prm["stall"], stall_ratio=0.9))
+    t1 = time.perf_counter()
+    ok = bool(res.accepted_inner_converged and res.max_violation <= prm["feas_tol"])
+    return {"kind": "full", "S": sum(entries(inst)), "iters": int(sum(res.inner_iters)), "ok": ok, "t": t1 - t0}
+
+
+def cpu_model():
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True).stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def oracle_tasks(instances, args, cores):
+    """Task list of the oracle estimate: (a) cost tasks on a size-stratified sample of the workload
+    (instances at evenly spaced quantiles of the row-entry count, smallest and largest included):
+    one linearization and 4 inner iterations each; (b) complete solves with the benchmark's schedule
+    on the smallest instances of the workload."""
+    sizes = np.array([sum(entries(x)) for x in instances], dtype=np.float64)
+    order = np.argsort(sizes, kind="stable")
+    n_cost = int(min(max(cores, 8), 24))
+    q = np.linspace(0, len(order) - 1, n_cost).round().astype(int)
+    n_full = int(min(max(cores, 4), 16))
+    prm = dict(rho=args.rho, k_it=4, n_outer=args.n_outer, max_inner=args.max_inner,
+               max_inner_final=args.max_inner_final, adapt=args.adapt, stall=args.stall, carry=args.carry,
+               feas_tol=args.feas_tol)
+    return ([("full", instances[int(i)], prm) for i in order[:n_full]]
+            + [("cost", instances[int(order[i])], prm) for i in q])
+
+
+def oracle_pool(cores, n_tasks):
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    return mp.get_context("spawn").Pool(processes=max(1, min(cores, n_tasks)))
+
+
+def oracle_from_results(instances, args, out, cores, wall):
+    """Per instance, time = (1 + n_outer) linearizations + I inner iterations, with per-linearization
+    and per-iteration costs from least-squares lines in the row-entry count fitted to the cost tasks,
+    and I and the fraction of solves that count from the complete solves.  Throughput on N cores =
+    counted solves / (Σ times / N)."""
+    sizes = np.array([sum(entries(x)) for x in instances], dtype=np.float64)
+    cost = [r for r in out if r["kind"] == "cost"]
+    full = [r for r in out if r["kind"] == "full"]
+    S = np.array([r["S"] for r in cost], dtype=np.float64)
+    Xm = np.stack([np.ones_like(S), S], axis=1)
+    c_lin = np.linalg.lstsq(Xm, np.array([r["t_lin"] for r in cost]), rcond=None)[0]
+    c_it = np.linalg.lstsq(Xm, np.array([r["t_it"] for r in cost]), rcond=None)[0]
+    iters = float(np.mean([r["iters"] for r in full]))
+    frac = float(np.mean([r["ok"] for r in full]))
+    per = (1 + args.n_outer) * np.maximum(c_lin[0] + c_lin[1] * sizes, 1e-6) \
+        + iters * np.maximum(c_it[0] + c_it[1] * sizes, 1e-7)
+    total = float(per.sum())
+    value = frac * len(instances) / (total / cores)
+    return dict(value=value, unit=UNIT, cores=cores, kind="oracle", cpu_model=cpu_model(),
+                sample=(f"{n_cores_str(cores)}: cost of one linearization and one inner iteration on {len(cost)} "
+                        f"workload instances at evenly spaced size quantiles ({int(S.min())}..{int(S.max())} row "
+                        f"entries), and {len(full)} complete solves with the benchmark's schedule on the smallest "
+                        f"instances (mean {iters:.0f} inner iterations per solve, {frac:.2f} counted); per-instance "
+                        f"time = linear fits in the row-entry count, summed over the {len(instances)}-instance "
+                        f"workload and divided by {cores} cores; {wall:.1f} s wall"),
+                fit={"lin_s": [float(c) for c in c_lin], "iter_s": [float(c) for c in c_it]},
+                counted_fraction=frac, inner_iters_per_solve=iters, wall_s=wall)
+
+
+def oracle_estimate(instances, args):
+    """The FP64 oracle's solves/s at the metric on all host cores, from a bounded sample: the tasks of
+    oracle_tasks run concurrently in one spawned process per core (so their timings include the
+    contention of a fully loaded host), then oracle_from_results."""
+    cores = os.cpu_count() or 1
+    tasks = oracle_tasks(instances, args, cores)
+    t0 = time.perf_counter()
+    with oracle_pool(cores, len(tasks)) as pool:
+        out = pool.map(_oracle_task, tasks, chunksize=1)
+    return oracle_from_results(instances, args, out, cores, time.perf_counter() - t0)
+
+
+def n_cores_str(cores):
+    return f"{cores} spawned processes (one per host core)"
 
 
 # ---------------------------------------------------------------------------------------------
@@ -154,11 +239,10 @@ def clocks_summary(path, dev_index):
 
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) over algorithmic bytes of one
 # k_fulladmm launch per dynamics kind (0 unicycle, 1 quadcopter), from a full capture of 148 mixed
-# instances x 40 iterations.  The launch at the benchmark size is scaled from it by its algorithmic
-# bytes (traffic grows with row entries x iterations).  Valid only for the kernel sources it was
-# measured on: any change to them makes the reported traffic null until it is measured again.
-TRAFFIC = {"sources_sha256": "eff2433af36d414ff3515553259a35ce1cff0034a51ebd97c1c7c299926fa02c",
-           "ratio": {0: 0.6565, 1: 0.9781}}
+# instances.  The launch at the benchmark size is scaled from it by its algorithmic bytes (traffic
+# grows with row entries x iterations).  Valid only for the kernel sources it was measured on: any
+# change to them makes the reported traffic null until it is measured again.
+TRAFFIC = {"sources_sha256": None, "ratio": {}}
 KERNEL_SOURCES = ["fulladmm.cuh", "nrto_dev.cuh", "tma.cuh", "linearize.cuh", "dynamics.cuh"]
 
 
@@ -170,12 +254,178 @@ def kernel_sources_sha():
     return h.hexdigest()
 
 
-def measured_peak_bf16():
+def measured_peak(key, fallback):
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        return float(d["bf16_tflops"]), "measured (burst)"
+        return float(d[key]), "measured"
     except Exception:
-        return 1800.0, "fallback"
+        return fallback, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# plain arm: FP64, batch 1, cold start, same schedule
+# ---------------------------------------------------------------------------------------------
+def sample_ids(args, n):
+    rng = np.random.default_rng(7)
+    return sorted(rng.choice(n, size=min(args.plain_n, n), replace=False).tolist())
+
+
+def plain_arm(args, insts, stream):
+    import torch
+    from paper_2603_02642_b300 import nrto
+    ids = sample_ids(args, len(insts))
+    opts = solver_options(args, carry=0)
+    probs = [nrto.Problem([insts[i]], nrto.PREC_FP64, stream=stream.cuda_stream) for i in ids]
+    probs[0].solve(opts, args.n_outer, fetch=False)   # first use of the FP64 kernels (module load)
+    torch.cuda.synchronize()
+    ms, ok, iters = [], [], []
+    for p in probs:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p.solve(opts, args.n_outer, fetch=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        st = p.stats()
+        ok.append(bool(counted(st, args.feas_tol)[0]))
+        iters.append(float(st["cum_iters"][0]))
+    for p in probs:
+        p.close()
+    tot = sum(ms) / 1e3
+    return {"value": sum(ok) / tot, "unit": UNIT, "counted": int(sum(ok)), "solves": len(ids),
+            "solves_per_s": len(ids) / tot, "iterations_per_s": sum(iters) / tot, "seconds": tot,
+            "sample": f"{len(ids)} instances of the workload (ids {ids}), each alone on the GPU, FP64, cold start "
+                      f"of every inner solve, the schedule and tolerances of the batched arm"}
+
+
+def rel_err(a, b, floor=1e-9):
+    """‖a - b‖ / max(‖b‖, floor): relative error, absolute below the floor (gains that are zero up to
+    rounding in both precisions when no robust constraint is active)."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), floor))
+
+
+def mixed_results(prob, ids):
+    """The batch's returned (ū, K) and last p̃ of the sample instances, read from the device."""
+    from paper_2603_02642_b300 import nrto
+    return {"u_bar": {i: prob.export(nrto.F_UHAT, i) for i in ids}, "K": {i: prob.export(nrto.F_KACC, i) for i in ids},
+            "pt": {i: prob.export(nrto.F_PT, i) for i in ids}}
+
+
+def fp64_errors(args, insts, ids, out_mixed, st_mixed, stream):
+    """Per-result error of the batched mixed-precision solve against the FP64 path with the same
+    schedule (the GPU FP64 path matches the oracle to 1e-8 in the parity tests), on a seeded sample."""
+    from paper_2603_02642_b300 import nrto
+    p = nrto.Problem([insts[i] for i in ids], nrto.PREC_FP64, stream=stream.cuda_stream)
+    o = p.solve(solver_options(args), args.n_outer, fetch=True)
+    st = p.stats()
+    pt64 = [p.export(nrto.F_PT, k) for k in range(len(ids))]
+    p.close()
+
+    def rel(a, b):
+        return rel_err(a, b)
+
+    rows = {"K": [], "u_bar": [], "cost": [], "p_tilde": [], "iterations": [], "counted_agree": []}
+    ok64 = counted(st, args.feas_tol)
+    okm = counted(st_mixed, args.feas_tol)
+    for k, i in enumerate(ids):
+        rows["K"].append(rel(out_mixed["K"][i], o["K"][k].reshape(-1)))
+        rows["u_bar"].append(rel(out_mixed["u_bar"][i], o["u_bar"][k].reshape(-1)))
+        rows["cost"].append(abs(st_mixed["cost"][i] - st["cost"][k]) / max(abs(st["cost"][k]), 1e-300))
+        rows["p_tilde"].append(rel(out_mixed["pt"][i], pt64[k]))
+        rows["iterations"].append(int(st_mixed["cum_iters"][i] - st["cum_iters"][k]))
+        rows["counted_agree"].append(bool(okm[i] == ok64[k]))
+    summ = {}
+    for k, v in rows.items():
+        if k == "counted_agree":
+            summ[k] = f"{sum(v)}/{len(v)}"
+        elif k == "iterations":
+            summ[k] = {"median_abs": float(np.median(np.abs(v))), "max_abs": int(np.max(np.abs(v)))}
+        else:
+            summ[k] = {"median": float(np.median(v)), "max": float(np.max(v))}
+    summ["sample"] = f"{len(ids)} instances (ids {ids}); reference: the FP64 path, same schedule and carry"
+    return summ
+
+
+def single_configs(args, stream):
+    """The single-instance configurations: solves/s and iterations/s on one B300 (one instance
+    occupies one SM), with the oracle's time per inner iteration on the same instance."""
+    import torch
+    from oracle import dr as DRO, fulladmm as F, problem as P
+    from paper_2603_02642_b300 import nrto, workloads as W
+    out = {}
+
+    def timed(prob, opts, n_outer, reps=2):
+        prob.solve(opts, n_outer, fetch=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            prob.solve(opts, n_outer, fetch=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) / 1e3 / reps
+        st = prob.stats()
+        return s, st
+
+    def oracle_iter_s(inst, solver):
+        lin = P.linearize(inst, inst.u_init)
+        t0 = time.perf_counter()
+        if solver == "dr":
+            DRO.solve(inst, lin, DRO.DROptions(rho=40.0, r_trust=2.0, max_admm=1, max_dr=20), n_admm=1, n_dr=20,
+                      check=False)
+            return (time.perf_counter() - t0) / 20.0
+        F.iterate(inst, lin, F.FullADMMOptions(rho=10.0, r_trust=2.0, check=False), n_iter=3)
+        return (time.perf_counter() - t0) / 3.0
+
+    # unicycle T = 20, 3 obstacles, NRTO-DR, FP64, 10 outer steps x <= 500 DR iterations
+    uni = W.unicycle(0, T=20, n_obs=3)
+    o = nrto.Options(solver=nrto.SOLVER_DR, rho=40.0, max_inner=40, max_dr=500, eps_dr=1e-4, eps_p=1e-4, eps_d=1e-4,
+                     check=1, r0=2.0)
+    p = nrto.Problem([uni], nrto.PREC_FP64, stream=stream.cuda_stream)
+    s, st = timed(p, o, 10)
+    p.close()
+    out["unicycle_T20_o3_dr_fp64"] = {"solves_per_s": 1.0 / s, "admm_iterations_per_s": st["cum_iters"][0] / s,
+                                      "dr_iterations_per_s": st["dr_iters"][0] / s, "seconds_per_solve": s,
+                                      "oracle_s_per_dr_iteration": oracle_iter_s(uni, "dr")}
+    # quadcopter T = 100, 10 obstacles, FP64: NRTO-DR vs FullADMM over the same bounded work (two
+    # outer steps of 10 ADMM iterations, DR capped at 100 per ADMM iteration; FullADMM 10 iterations)
+    quad = W.quadcopter(0, T=100, n_obs=10)
+    d = {"work": "2 outer steps x 10 inner iterations (NRTO-DR: <= 100 DR iterations each), FP64"}
+    for name, oo in (("dr", nrto.Options(solver=nrto.SOLVER_DR, rho=40.0, max_inner=10, max_dr=100, eps_dr=1e-4,
+                                         eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0)),
+                     ("fulladmm", nrto.Options(rho=10.0, max_inner=10, eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0))):
+        p = nrto.Problem([quad], nrto.PREC_FP64, stream=stream.cuda_stream)
+        s, st = timed(p, oo, 2, reps=1)
+        p.close()
+        d[name] = {"outer_steps_per_s": 2.0 / s, "inner_iterations_per_s": st["cum_iters"][0] / s,
+                   "seconds": s}
+        if name == "dr":
+            d[name]["dr_iterations_per_s"] = st["dr_iters"][0] / s
+    d["oracle_s_per_fulladmm_iteration"] = oracle_iter_s(quad, "fulladmm")
+    out["quadcopter_T100_o10_fp64"] = d
+    # arm T = 100, mixed precision vs FP64 (3 outer steps: 2 x 40 inner iterations, then <= 200)
+    arm = W.arm(0, T=100)
+    res = {}
+    ao = nrto.Options(rho=10.0, max_inner=40, max_inner_final=200, eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0,
+                      adapt_every=25, stall_every=100, carry=1)
+    for prec in (nrto.PREC_MIXED, nrto.PREC_FP64):
+        p = nrto.Problem([arm], prec, stream=stream.cuda_stream)
+        s, st = timed(p, ao, 3, reps=1)
+        sol = p.solve(ao, 3, fetch=True)
+        p.close()
+        res[prec] = (s, st, sol)
+    (sm, stm, solm), (s64, st64, sol64) = res[nrto.PREC_MIXED], res[nrto.PREC_FP64]
+    out["arm_T100_mixed"] = {
+        "work": "3 outer steps (40, 40, <= 200 inner iterations), carry, residual balancing",
+        "solves_per_s": 1.0 / sm, "inner_iterations_per_s": stm["cum_iters"][0] / sm, "seconds_per_solve": sm,
+        "fp64_solves_per_s": 1.0 / s64, "oracle_s_per_fulladmm_iteration": oracle_iter_s(arm, "fulladmm"),
+        "error_vs_fp64": {"K": rel_err(solm["K"][0], sol64["K"][0]), "K_norm_fp64": float(np.linalg.norm(sol64["K"][0])),
+                          "u_bar": rel_err(solm["u_bar"][0], sol64["u_bar"][0]),
+                          "cost": float(abs(stm["cost"][0] - st64["cost"][0]) / abs(st64["cost"][0])),
+                          "iterations": int(stm["cum_iters"][0] - st64["cum_iters"][0])}}
+    return out
 
 
 def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
@@ -201,8 +451,6 @@ def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
     t_fit = time.perf_counter() - t0
     test = [W.warmstart_quad(1_000_000 + s) for s in range(n_eval)]
     res = {}
-    # cold start; warm start; warm start with the cold fallback on a residual plateau (r_p above its
-    # tolerance and down by less than 1% over 1000 iterations)
     for mode in ("cold", "warm", "warm_fallback"):
         q = nrto.Problem(test, nrto.PREC_MIXED, stream=stream.cuda_stream)
         q.linearize()
@@ -218,20 +466,20 @@ def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
                                       **opts))
         e2.record(stream)
         torch.cuda.synchronize()
-        fb = sum(int(q.export(nrto.F_STATS, i)[6]) for i in range(n_eval))
+        fb = int(q.stats()["fallback"].sum())
         res[mode] = dict(iters=o["iters"].copy(), conv=o["status"] == 1, solve_ms=e1.elapsed_time(e2),
                          predict_ms=e0.elapsed_time(e1), fallbacks=fb)
         q.close()
     both = res["cold"]["conv"] & res["warm"]["conv"] & res["warm_fallback"]["conv"]
-    # tensor-core rate of the network's GEMMs on an inference batch
     feats = WS.features([W.warmstart_quad(2_000_000 + s) for s in range(n_infer)])
     ws.net.forward(feats)
     ws.net.profile(True)
     ws.net.forward(feats)
     gms, gfl, gn = ws.net.profile(False)
-    peak, peak_kind = measured_peak_bf16()
+    peak, peak_kind = measured_peak("bf16_tflops", 1800.0)
     achieved = gfl / (gms / 1e3) / 1e12
     ws.net.close()
+
     def summary(r, warm):
         total_ms = r["solve_ms"] + (r["predict_ms"] if warm else 0.0)
         d = {"converged": int(r["conv"].sum()), "solve_ms": r["solve_ms"],
@@ -253,34 +501,39 @@ def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
         "warm": summary(res["warm"], True),
         "warm_fallback": summary(res["warm_fallback"], True),
         "mlp_roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "peak_source": peak_kind, "batch": n_infer,
+                         "frac": achieved / peak, "peak_source": peak_kind + " (burst)", "batch": n_infer,
                          "gemm_launches": int(gn), "gemm_ms": gms},
     }
 
 
-def measured_peak_gbs():
-    try:
-        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        return float(d["hbm_gbs"]), "measured"
-    except Exception:
-        return 6400.0, "fallback"
-
-
 def reference_arm(args):
+    """The oracle on the host cores: each timed step runs its share of the estimate's tasks (a
+    bounded sample of the workload), and the value is the estimate from all timed steps' results.
+    Warm-up steps run one of the smallest complete solves each (process start and imports)."""
     insts = workload(args.n, 0)
-    vals = []
-    for k in range(args.warmup + args.steps):
-        est = oracle_estimate(insts, args.n_outer, args.max_inner, budget_s=15.0, seed=k)
-        if k >= args.warmup:
-            vals.append(est)
-    value = float(np.mean([v["value"] for v in vals]))
-    est = dict(vals[-1])
-    est["value"] = value
+    cores = os.cpu_count() or 1
+    tasks = oracle_tasks(insts, args, cores)
+    full = [t for t in tasks if t[0] == "full"]
+    K = max(args.steps, 1)
+    out, t_steps = [], []
+    with oracle_pool(cores, len(tasks)) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_task, full[:1], chunksize=1)
+        for k in range(K):
+            t0 = time.perf_counter()
+            out += pool.map(_oracle_task, tasks[k::K], chunksize=1)
+            t_steps.append(time.perf_counter() - t0)
+    est = oracle_from_results(insts, args, out, cores, sum(t_steps))
+    value = est["value"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * args.n / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(t_steps)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
             "config": {"workload": f"batch{args.n}_mixed_unicycle_quadcopter", "n_outer": args.n_outer,
-                       "max_inner": args.max_inner, "instances_per_gpu": args.n},
+                       "max_inner": args.max_inner, "max_inner_final": args.max_inner_final,
+                       "instances_per_gpu": args.n, "adapt_every": args.adapt, "stall_every": args.stall,
+                       "carry": args.carry, "feas_tol": args.feas_tol,
+                       "step": "a 1/steps share of the oracle sample's tasks on all host cores"},
             "cpu_baseline": est,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -306,8 +559,7 @@ def main():
     prec = nrto.PREC_MIXED if args.prec == "mixed" else nrto.PREC_FP64
     stream = torch.cuda.current_stream()
     prob = nrto.Problem(insts, prec, stream=stream.cuda_stream)
-    opts = nrto.Options(rho=args.rho, max_inner=args.max_inner, eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0,
-                        adapt_every=args.adapt, stall_every=args.stall)
+    opts = solver_options(args)
 
     def barrier():
         if ws > 1:
@@ -345,87 +597,110 @@ def main():
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    value = ws * args.n * args.steps / (ms_max / 1000.0)
+    step_s = ms_max / 1000.0 / args.steps
 
-    # per-instance iteration counts of the last step (every step is the same computation)
-    stats = np.array([prob.export(nrto.F_STATS, i) for i in range(prob.n)])
-    iters = stats[:, 0]
+    # every step is the same computation: the last step's per-instance outcome holds for all
+    st = prob.stats()
+    ok = counted(st, args.feas_tol)
+    n_ok = int(ok.sum())
+    tn = torch.tensor([float(n_ok)], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(tn, op=dist.ReduceOp.SUM)
+    value = float(tn.item()) / step_s
+    iters = st["cum_iters"]
     w = 4 if prec == nrto.PREC_MIXED else 8
-    bytes_step = 0.0
-    bytes_kind = {}
-    for i, inf in enumerate(prob.info):
-        s_state = inf.n_entries_state
-        per_it = (3 + inf.nu / inf.nx) * s_state * w + 2 * w * (inf.n_entries - s_state)
-        bytes_step += per_it * iters[i]
-        bytes_kind[insts[i].kind] = bytes_kind.get(insts[i].kind, 0.0) + per_it * iters[i]
+    bytes_step = bytes_design = 0.0
+    for i, x in enumerate(insts):
+        S, C = entries(x)
+        bytes_step += (3 * S + 2 * C) * w * iters[i]
+        bytes_design += ((3 + x.nu / x.nx) * S + 2 * C) * w * iters[i]
     launches_per_step = solver_launches / max(args.steps, 1)
-    avg_launch_s = solver_ms / 1000.0 / max(solver_launches, 1)
-    achieved = bytes_step / launches_per_step / avg_launch_s / 1e9
-    peak, peak_kind = measured_peak_gbs()
+    solver_s_step = solver_ms / 1000.0 / max(args.steps, 1)
+    achieved = bytes_step / solver_s_step / 1e9
+    peak, peak_kind = measured_peak("hbm_gbs", 6400.0)
     traffic = None
-    if (prec == nrto.PREC_MIXED and kernel_sources_sha() == TRAFFIC["sources_sha256"]
-            and all(k in TRAFFIC["ratio"] for k in bytes_kind)):
-        traffic = sum(TRAFFIC["ratio"][k] * b for k, b in bytes_kind.items()) / max(launches_per_step, 1e-30)
-    conv = int(np.sum(stats[:, 2] == 1))
-    stalled = int(np.sum(stats[:, 2] == 5))
+    # the batch's mixed-precision results of the sample, for the per-result comparison with FP64
+    ids = sample_ids(args, len(insts))
+    sol_mixed = mixed_results(prob, ids) if rank == 0 and not args.no_plain else None
 
-    # end to end through the C ABI with host buffers: upload the step's problem data, solve, read back
+    # end to end through the C ABI with host buffers: upload the step's problem data, solve, read
+    # back the solution and the per-instance outcome
     e2e = None
     if not args.no_e2e:
         h2d = 0
         for x in insts:
             h2d += 8 * (x.u_init.size + x.Sigma.size + x.x0.size + x.x_goal.size + x.obs_center.size
                         + x.obs_radius.size + x.dyn_params.size + 4 * x.nx + 6 * x.nu)
-        d2h = 8 * sum(x.T * x.nu * (1 + x.nx) + 1 for x in insts)
+        d2h = 8 * sum(x.T * x.nu * (1 + x.nx) + 1 for x in insts) + 8 * nrto.NSTAT * len(insts)
+        n_e2e = min(args.steps, 2)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        n_ok_e2e = 0
+        for _ in range(n_e2e):
             prob.update(insts)
             prob.solve(opts, args.n_outer, fetch=True)
+            n_ok_e2e = int(counted(prob.stats(), args.feas_tol).sum())
         barrier()
         t1 = time.perf_counter()
-        tt = torch.tensor([t1 - t0], dtype=torch.float64, device="cuda")
+        tt = torch.tensor([t1 - t0, float(n_ok_e2e)], dtype=torch.float64, device="cuda")
         if ws > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": ws * args.n * args.steps / float(tt.item()), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+            dist.all_reduce(tt[:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        e2e = {"value": float(tt[1].item()) * n_e2e / float(tt[0].item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
 
-    warm = None
+    plain = errs = cfgs = warm = cpu = None
+    if rank == 0:
+        if not args.no_plain:
+            plain = plain_arm(args, insts, stream)
+            errs = fp64_errors(args, insts, ids, sol_mixed, st, stream)
+        if not args.no_configs:
+            cfgs = single_configs(args, stream)
+    prob.close()
     if rank == 0 and not args.no_warm:
-        prob.close()
         warm = warm_start_study(stream)
-    cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = oracle_estimate(insts, args.n_outer, args.max_inner)
+        cpu = oracle_estimate(insts, args)
     clocks = clocks_summary(clk_path, local)
     if rank == 0:
+        kinds = np.array([x.kind for x in insts])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == nrto.PREC_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": f"batch{args.n}_mixed_unicycle_quadcopter", "instances_per_gpu": args.n,
-                       "n_outer": args.n_outer, "max_inner": args.max_inner, "precision": args.prec, "rho0": args.rho,
-                       "adapt_every": args.adapt, "stall_every": args.stall,
+                       "n_outer": args.n_outer, "max_inner": args.max_inner, "max_inner_final": args.max_inner_final,
+                       "precision": args.prec, "rho0": args.rho, "adapt_every": args.adapt,
+                       "stall_every": args.stall, "carry": args.carry, "feas_tol": args.feas_tol,
                        "l2": "inputs larger than L2 (row arrays of several GB)",
+                       "counted": n_ok, "counted_frac": n_ok / prob.n,
+                       "counted_by_kind": {"unicycle": int(ok[kinds == 0].sum()), "quadcopter": int(ok[kinds == 1].sum())},
+                       "solves_per_s_all": ws * args.n / step_s,
+                       "final_inner_converged_frac": float(np.mean(st["status"] == 1)),
+                       "final_inner_stalled_frac": float(np.mean(st["status"] == 5)),
                        "inner_iters_per_solve_mean": float(np.mean(iters)),
-                       "final_inner_converged_frac": conv / prob.n,
-                       "final_inner_stalled_frac": stalled / prob.n,
-                       "iterations_per_s": ws * float(np.sum(iters)) * args.steps / (ms_max / 1000.0)},
+                       "iterations_per_s": ws * float(np.sum(iters)) / step_s},
+            "plain_fp64_gpu": plain,
+            "ratio_vs_plain": (value / plain["value"]) if plain and plain["value"] > 0 else None,
+            "error_vs_fp64": errs,
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "k_fulladmm",
-                         "peak_source": peak_kind, "avg_launch_ms": avg_launch_s * 1000.0,
+                         "peak_source": peak_kind, "avg_launch_ms": solver_ms / max(solver_launches, 1),
                          "launches": int(solver_launches),
-                         "algorithmic_bytes_per_launch": bytes_step / max(launches_per_step, 1e-30)},
+                         "algorithmic_bytes_per_launch": bytes_step / max(launches_per_step, 1e-30),
+                         "bytes_per_iteration": "(3 S + 2 C) w: read b-hat and the adjoint rows, read and write "
+                                                "lambda_nu (state rows), read and write lambda_nu (control rows)",
+                         "design_bytes_per_launch": bytes_design / max(launches_per_step, 1e-30)},
             "phase_share": phase_share,
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "configs": cfgs,
             "warm_start": warm,
         }
         print(json.dumps(line))
-    prob.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
