@@ -19,8 +19,8 @@ Subproblem 2 (step (4b), defined in prior work): the exact minimizer of
 Q_û(δû) + λᵀ(p - p̃) + ρ/2‖p - p̃‖² s.t. g_j + b_jᵀδû + p_j ≤ 0, ‖F_u δû‖ ≤ r.  With
 v = p̃ - λ/ρ, p_j = min(v_j, -g_j - b_jᵀδû), which leaves a strongly convex squared-hinge
 objective in δû; it is minimized by semismooth Newton (active-set Newton steps with an
-Armijo backtracking safeguard) and the trust region is enforced by a multiplier μ ≥ 0
-found by bisection on ‖F̃ δû(μ)‖ = r.
+Armijo backtracking safeguard) and the trust region is enforced by a multiplier μ ≥ 0, the
+root of ‖F̃ δû(μ)‖² = r² found by bracketing (growth by 4) and Illinois regula falsi.
 Dual update (4c) uses the current iterates: λ ← λ + ρ(p - p̃).
 """
 from __future__ import annotations
@@ -147,22 +147,44 @@ def sub2_solve(inst, lin, rho, pt, lam, r_trust):
     def solve_mu(mu, x0):
         return _ssn(inst, lin, rho, v, H0 + mu * FtF, c, Bm, x0)
 
+    def phi(y):
+        """‖F̃ δû‖² - r²: decreasing in μ; the multiplier μ > 0 is its root."""
+        return float(np.sum((Ft @ y) ** 2)) - r_trust * r_trust
+
     x = solve_mu(0.0, np.zeros(T * nu))
     mu = 0.0
-    if np.linalg.norm(Ft @ x) > r_trust:
+    if phi(x) > 0.0:
+        # bracket [lo, hi] with phi(lo) > 0 >= phi(hi), growing hi by 4
         lo, hi = 0.0, 1.0
+        fa = phi(x)
         xh = solve_mu(hi, x)
-        while np.linalg.norm(Ft @ xh) > r_trust:
-            lo, hi = hi, hi * 4.0
+        fb = phi(xh)
+        while fb > 0.0:
+            lo, fa = hi, fb
+            hi *= 4.0
             xh = solve_mu(hi, xh)
+            fb = phi(xh)
+        # Illinois regula falsi on phi (a bracketing secant: the endpoint kept twice in a row has
+        # its phi halved), each point solved from the feasible end's solution; the feasible end is
+        # returned once the bracket is 1e-14 relative
+        side = 0
         for _ in range(200):
-            mid = 0.5 * (lo + hi)
-            xm = solve_mu(mid, xh)
-            if np.linalg.norm(Ft @ xm) > r_trust:
-                lo = mid
+            mc = hi - fb * (hi - lo) / (fb - fa)
+            if not (lo < mc < hi):
+                mc = 0.5 * (lo + hi)
+            xc = solve_mu(mc, xh)
+            fc = phi(xc)
+            if fc > 0.0:
+                lo, fa = mc, fc
+                if side == -1:
+                    fb *= 0.5
+                side = -1
             else:
-                hi, xh = mid, xm
-            if hi - lo <= 1e-14 * hi:
+                hi, fb, xh = mc, fc, xc
+                if side == 1:
+                    fa *= 0.5
+                side = 1
+            if hi - lo <= 1e-14 * hi or fc == 0.0:
                 break
         mu, x = hi, xh
     du = x.reshape(T, nu)

@@ -26,6 +26,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from . import dr
 from . import problem as P
 from . import soc
 
@@ -254,3 +255,44 @@ def carry_state(lin, prev: FullADMMState, opts: FullADMMOptions, shifted: bool):
         s.dx = prev.dx.copy()
         s.e = prev.e.copy()
     return s, rho
+
+
+def iterate_as_written(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None,
+                       n_iter: int | None = None) -> FullADMMState:
+    """Algorithm 1 with block 2a as the paper states it (Sec. IV): (δû, p) is the exact minimizer of
+    Q_û(δû) + ρ/2‖p - p̃ + λ_p‖² subject to the linearized robust constraints
+    g_j(x̂) + b_jᵀδû + p_j ≤ 0 and the trust region ‖F_u δû‖ ≤ r, with no slack variables.  That QP
+    is NRTO-DR's subproblem 2 with v = p̃ - λ_p (scaled dual), solved exactly by dr.sub2_solve.
+    Block 1 and the k_v update are those of `iterate`; duals λ_p, λ_ν only.  Residuals: every
+    coupling, r_p = ‖(p - p̃, Â_jk + b̂_j - ν_j)‖, and the block-2 change mapped through them,
+    r_d = ρ‖(Δp, Δ(Â_jk + b̂_j))‖; the paper's r_p, r_d are kept alongside.  The lifted form of
+    `iterate` has the same Problem (12) fixed point."""
+    rho = opts.rho
+    s = zero_state(lin) if state is None else state
+    H = P.gain_hessian_blocks(lin, inst, coef=rho)
+    L = opts.max_iter if n_iter is None else n_iter
+    Y_prev = P.Ahat_apply(lin, s.K) + lin.bhat
+    for it in range(1, L + 1):
+        Y = Y_prev
+        # Block 1: per-row SOC projection of (Â_j k + b̂_j + λ_ν,j, p_j + λ_p,j).
+        pt_new, nu = soc.project_rows(s.p + s.lam_p, Y + s.lam_nu)
+        # Block 2b, direct form.
+        K_new = P.gain_solve(H, rho * P.Ahat_T_apply(lin, nu - lin.bhat - s.lam_nu))
+        # Block 2a: the constrained (δû, p) QP (λ_p is scaled: the unscaled dual is ρ λ_p).
+        du, dx, p, _ = dr.sub2_solve(inst, lin, rho, pt_new, rho * s.lam_p, opts.r_trust)
+        Y_new = P.Ahat_apply(lin, K_new) + lin.bhat
+        lam_p = s.lam_p + (p - pt_new)
+        lam_nu = s.lam_nu + (Y_new - nu)
+        r_p = np.sqrt(np.sum((p - pt_new) ** 2) + np.sum((Y_new - nu) ** 2))
+        r_d = rho * np.sqrt(np.sum((p - s.p) ** 2) + np.sum((Y_new - Y) ** 2))
+        r_p_paper = float(np.linalg.norm(p - pt_new))
+        r_d_paper = float(rho * np.linalg.norm(pt_new - s.pt))
+        s = FullADMMState(K=K_new, du=du, dx=dx, p=p, pt=pt_new, lam_p=lam_p, lam_nu=lam_nu,
+                          w=s.w, lam_w=s.lam_w, e=s.e, lam_e=s.lam_e, nu=nu, iters=s.iters + 1,
+                          r_p=float(r_p), r_d=float(r_d), r_p_paper=r_p_paper, r_d_paper=r_d_paper,
+                          rho=rho, history=s.history + [(float(r_p), float(r_d))])
+        Y_prev = Y_new
+        if opts.check and r_p <= opts.eps_p and r_d <= opts.eps_d:
+            s.converged = True
+            break
+    return s

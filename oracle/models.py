@@ -48,13 +48,47 @@ def quad_xdot(x, u, prm):
     return np.concatenate([v, vdot, angdot, omdot])
 
 
-def f_arm(x, u, dt):
-    """Double-integrator joint model: q̇_{k+1} = q̇_k + u dt, q_{k+1} = q_k + q̇_{k+1} dt
-    (the Franka model's forward-Euler update of Supplementary Sec. IV-A with unit inertia,
-    no damping and no clipping)."""
+def _clip(z, lo, hi):
+    """Element-wise clip that extends to complex arguments by comparing real parts: a clamped
+    component takes the (real) bound, so its complex-step derivative is zero; inside the bounds
+    (bounds included) the component passes through with derivative one."""
+    out = np.array(z, copy=True)
+    below = np.real(z) < lo
+    above = np.real(z) > hi
+    out[below] = lo[below]
+    out[above] = hi[above]
+    return out
+
+
+def f_arm(x, u, dt, damping=None, inertia=None, clip=False, lo=None, hi=None):
+    """Franka joint-space model (Supplementary Sec. IV-A, "Franka Manipulator Model"):
+    q̈_i = (τ_i - d_i q̇_i) / I_i; forward Euler with post-update clamping,
+    q̇_{k+1} = clip(q̇_k + q̈_k dt, -q̇_max, q̇_max), q_{k+1} = clip(q_k + q̇_{k+1} dt, q_min, q_max),
+    the limits being the state bounds lo, hi.  Without damping, inertia or clipping (the defaults)
+    this is the double integrator q̇_{k+1} = q̇_k + u dt, q_{k+1} = q_k + q̇_{k+1} dt."""
     q, dq = x[:7], x[7:]
-    dq1 = dq + u * dt
-    return np.concatenate([q + dq1 * dt, dq1])
+    d = np.zeros(7) if damping is None else damping
+    inr = np.ones(7) if inertia is None else inertia
+    dq1 = dq + (u - d * dq) / inr * dt
+    if clip:
+        dq1 = _clip(dq1, lo[7:], hi[7:])
+    q1 = q + dq1 * dt
+    if clip:
+        q1 = _clip(q1, lo[:7], hi[:7])
+    return np.concatenate([q1, dq1])
+
+
+# Parameter layout of the arm model (flat dyn_params): the DH table (a_i, d_i, α_i) × 7, then, when
+# present, damping d (7), inertia I (7) and the clipping flag (1).
+ARM_DH, ARM_DAMP, ARM_INERT, ARM_CLIP, ARM_NPRM = 0, 21, 28, 35, 36
+
+
+def arm_params(inst):
+    """(damping, inertia, clip) of an arm instance; the 21-value table is the double integrator."""
+    prm = inst.dyn_params
+    if prm.size >= ARM_NPRM:
+        return prm[ARM_DAMP:ARM_DAMP + 7], prm[ARM_INERT:ARM_INERT + 7], bool(prm[ARM_CLIP] != 0.0)
+    return np.zeros(7), np.ones(7), False
 
 
 def step(inst, x, u):
@@ -64,7 +98,8 @@ def step(inst, x, u):
     if inst.kind == KIND_QUADCOPTER:
         return x + inst.dt * quad_xdot(x, u, inst.dyn_params)
     if inst.kind == KIND_ARM:
-        return f_arm(x, u, inst.dt)
+        d, inr, clip = arm_params(inst)
+        return f_arm(x, u, inst.dt, d, inr, clip, inst.x_lo, inst.x_hi)
     raise ValueError(inst.kind)
 
 
@@ -106,7 +141,7 @@ def dh_transform(theta, d, a, alpha):
 
 def arm_link_sphere_centres(inst, q):
     """World positions of the link spheres: frame_l = Π_{i≤l} DH_i(q_i), centre = frame_l·[offset;1]."""
-    dh = inst.dyn_params.reshape(7, 3)
+    dh = inst.dyn_params[:21].reshape(7, 3)
     frames = []
     Tcur = np.eye(4) + 0 * q[0]
     for i in range(7):

@@ -13,8 +13,9 @@ disturbance-feedback policy u_k = ū_k + K_k d_{k-1}, robust state constraints g
 robust control constraints h ≤ 0.
 
 Dynamics models (Supplementary Sec. IV-A): unicycle (3,2), quadcopter (12,4); the 7-DoF arm
-is a double integrator with random-DH forward kinematics (a synthetic stand-in for the
-Franka model, whose collision spheres are not available).
+as a double integrator with random-DH forward kinematics (`arm`), and the paper's Franka model
+(`franka`: damping, unit inertia, clamped joint limits, torque bounds, the Panda's published
+kinematics with this library's collision spheres).
 
 Draw order is fixed per generator and documented inline; `numpy.random.default_rng(seed)`.
 """
@@ -198,6 +199,73 @@ def arm(seed: int, T: int = 100, n_link: int = 8, n_static: int = 6, dt: float =
         x_hi=np.concatenate([ARM_Q_MAX, ARM_DQ_MAX]), seed=seed)
 
 
+# Franka Emika Panda kinematics: the manufacturer's published modified (Craig) DH table, rows
+# (a_{i-1}, d_i, α_{i-1}) for joints 1..7 and the flange: (0, .333, 0), (0, 0, -π/2), (0, .316, π/2),
+# (.0825, 0, π/2), (-.0825, .384, -π/2), (0, 0, π/2), (.088, 0, π/2), flange (0, .107, 0).  Since
+# Rot_x and Trans_x commute, that chain equals a standard-DH chain whose joint i takes d_i and the
+# (a, α) of the next row, with the flange offset as joint 7's d: the rows below, (a_i, d_i, α_i).
+FRANKA_DH = np.array([
+    [0.0, 0.333, -math.pi / 2],
+    [0.0, 0.0, math.pi / 2],
+    [0.0825, 0.316, math.pi / 2],
+    [-0.0825, 0.0, -math.pi / 2],
+    [0.0, 0.384, math.pi / 2],
+    [0.088, 0.0, math.pi / 2],
+    [0.0, 0.107, 0.0],
+])
+# Model parameters (Supplementary Table "Dynamics dimensions and model parameters").
+FRANKA_TAU_MAX = np.array([87.0, 87.0, 87.0, 87.0, 12.0, 12.0, 12.0])
+FRANKA_DAMPING = np.full(7, 0.5)
+FRANKA_INERTIA = np.ones(7)
+# Collision spheres of this library (the paper's come from a simulator and are not given): link
+# index of the standard-DH frame, offset in that frame, radius; at q = 0 they sit on the shoulder
+# (0, 0, .333), the upper-arm axis (0, 0, .491), the elbow (.0825, 0, .649) and (0, 0, .649), the
+# forearm axis (0, 0, .841), the wrist (0, 0, 1.033), (.088, 0, 1.033) and the hand (.088, 0, .876).
+FRANKA_SPHERES = np.array([
+    [1, 0.0, 0.0, 0.0, 0.09],
+    [2, 0.0, 0.0, 0.158, 0.08],
+    [3, 0.0, 0.0, 0.0, 0.08],
+    [4, 0.0, 0.0, 0.0, 0.07],
+    [4, 0.0, 0.0, 0.192, 0.07],
+    [5, 0.0, 0.0, 0.0, 0.07],
+    [6, 0.0, 0.0, 0.0, 0.06],
+    [7, 0.0, 0.0, 0.05, 0.07],
+])
+FRANKA_Q_READY = np.array([0.0, -math.pi / 4, 0.0, -3 * math.pi / 4, 0.0, math.pi / 2, math.pi / 4])
+
+
+def franka(seed: int, T: int = 100, n_static: int = 6, dt: float = 0.02) -> Instance:
+    """The paper's Franka model: x = [q, q̇] (14), u = τ (7); q̈ = (τ - d q̇)/I with d = 0.5, I = 1,
+    forward Euler with the joint position and velocity limits clamped after each step, torque bounds
+    |τ_i| ≤ τ_max,i as robust control constraints, the limits also as robust state constraints; the
+    Panda's published kinematics with this library's link spheres against static spheres.
+    Draws, in order: static sphere centre (3) and radius per sphere (centres at |y| in [.35, .7]
+    beside the arm, x in [.1, .6], z in [.1, .8]); q0 (7) and q_goal (7) within ±0.4 rad of the
+    ready pose, inside 80% of the joint range."""
+    rng = np.random.default_rng(seed)
+    centers = np.zeros((n_static, 3))
+    radii = np.zeros(n_static)
+    for o in range(n_static):
+        side = 1.0 if rng.uniform() < 0.5 else -1.0
+        centers[o] = [rng.uniform(0.1, 0.6), side * rng.uniform(0.35, 0.7), rng.uniform(0.1, 0.8)]
+        radii[o] = rng.uniform(0.05, 0.12)
+    mid = 0.5 * (ARM_Q_MIN + ARM_Q_MAX)
+    half = 0.5 * (ARM_Q_MAX - ARM_Q_MIN) * 0.8
+    q0 = np.clip(FRANKA_Q_READY + rng.uniform(-0.4, 0.4, size=7), mid - half, mid + half)
+    qg = np.clip(FRANKA_Q_READY + rng.uniform(-0.4, 0.4, size=7), mid - half, mid + half)
+    prm = np.concatenate([FRANKA_DH.reshape(-1), FRANKA_DAMPING, FRANKA_INERTIA, [1.0]])
+    return Instance(
+        kind=KIND_ARM, nx=14, nu=7, T=T, dt=dt, dyn_params=prm,
+        x0=np.concatenate([q0, np.zeros(7)]), x_goal=np.concatenate([qg, np.zeros(7)]),
+        u_init=np.zeros((T, 7)), u_ref=np.zeros(7),
+        Sigma=_diag_blocks(T, 1e-4 * np.ones(14)), tau=1.0,
+        Qx=np.ones(14), Ru=0.1 * np.ones(7), RK=math.sqrt(0.1) * np.ones(7),
+        obs_dim=3, obs_center=centers, obs_radius=radii, link_spheres=FRANKA_SPHERES.copy(),
+        u_lo=-FRANKA_TAU_MAX, u_hi=FRANKA_TAU_MAX.copy(),
+        x_lo=np.concatenate([ARM_Q_MIN, -ARM_DQ_MAX]),
+        x_hi=np.concatenate([ARM_Q_MAX, ARM_DQ_MAX]), seed=seed)
+
+
 def batched_mix(n: int = 2048, base_seed: int = 10000) -> list[Instance]:
     """Mixed batch: kind ~ Bernoulli(0.5) per instance (seed base_seed+i).
     Unicycle: T~U{20..200}, n_obs~U{1..20}, x0~U[-.5,.5]²×{0}, goal~(5,5)+U[-.5,.5]²,
@@ -245,6 +313,8 @@ def config(name: str, seed: int = 0):
         return quadcopter(seed)
     if name == "arm_T100":
         return arm(seed)
+    if name == "franka_T100":
+        return franka(seed)
     if name == "batch2048":
         return batched_mix(2048)
     raise KeyError(name)

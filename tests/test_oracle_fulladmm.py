@@ -275,3 +275,44 @@ def test_carry_applies_the_pending_penalty_update_and_keeps_unscaled_duals():
     s2 = F.iterate(inst, lin, o2, st, rho0=rho0)
     assert s2.converged
     assert np.allclose(s2.du, du_ip, atol=2e-6) and np.allclose(s2.K, K_ip, atol=2e-6)
+
+
+def test_as_written_block2_reaches_the_interior_point_solution():
+    """The as-written block 2a (exact constrained (δû, p) QP every iteration, no slacks) converges to
+    the interior-point solution of Problem 2, as the lifted split does: both are ADMM splittings of
+    the same problem, and their iteration counts differ."""
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    du_ip, K_ip = problem2_ip(inst, lin, r=0.5)
+    o = F.FullADMMOptions(rho=10.0, r_trust=0.5, eps_p=1e-9, eps_d=1e-9, max_iter=30000)
+    aw = F.iterate_as_written(inst, lin, o)
+    lifted = F.iterate(inst, lin, o)
+    assert aw.converged and lifted.converged
+    assert np.allclose(aw.du, du_ip, atol=2e-6) and np.allclose(aw.K, K_ip, atol=2e-6)
+    assert aw.iters != lifted.iters
+    # every iterate of the as-written form satisfies the linearized constraints and the trust region
+    # exactly (block 2a is feasible by construction): g + bᵀδû + p ≤ 0 and ‖F_u δû‖ ≤ r
+    assert np.max(lin.g0 + P.ell(lin, aw.du) + aw.p) <= 1e-10
+    assert np.linalg.norm(aw.dx[1:]) <= 0.5 * (1 + 1e-12)
+
+
+def test_as_written_block2_is_the_dr_subproblem_2_minimizer():
+    """One as-written iteration from a given state: its (δû, p) is the KKT point of the block-2a QP,
+    checked independently: p = min(p̃ - λ_p, -g - bᵀδû), and the gradient of the squared-hinge
+    objective in δû vanishes (trust region inactive at this radius)."""
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    o = F.FullADMMOptions(rho=7.0, r_trust=100.0, check=False)
+    s0 = F.iterate(inst, lin, o, n_iter=3)
+    s1 = F.iterate_as_written(inst, lin, o, s0, n_iter=1)
+    v = s1.pt - s0.lam_p
+    assert np.allclose(s1.p, np.minimum(v, -lin.g0 - P.ell(lin, s1.du)), atol=1e-12)
+    t = lambda a: torch.tensor(a, dtype=torch.float64)
+    du_t = t(s1.du).requires_grad_(True)
+    dxv = (t(lin.Fu) @ du_t.reshape(-1)).reshape(inst.T + 1, inst.nx)
+    ub = t(lin.u_hat) + du_t - t(inst.u_ref)
+    xb = t(lin.x_hat[1:]) + dxv[1:] - t(inst.x_goal)
+    z = t(v + lin.g0) + torch.einsum("jku,ku->j", t(lin.bvec), du_t)
+    f = torch.sum(ub * ub * t(inst.Ru)) + torch.sum(xb * xb * t(inst.Qx)) + 0.5 * 7.0 * torch.sum(torch.clamp(z, min=0) ** 2)
+    g, = torch.autograd.grad(f, [du_t])
+    assert g.abs().max().item() < 1e-9

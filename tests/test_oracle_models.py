@@ -104,3 +104,72 @@ def test_row_order_and_counts():
     assert [r[0] for r in st] == sorted(r[0] for r in st)
     arm = W.arm(0, T=100)
     assert len(models.state_rows(arm)) == 7600 and len(models.control_rows(arm)) == 0
+
+
+def _modified_dh_flange(q):
+    """Independent forward kinematics of the Panda from the manufacturer's modified (Craig) DH table:
+    T = Π_i Rot_x(α_{i-1}) Trans_x(a_{i-1}) Rot_z(q_i) Trans_z(d_i), then the flange Trans_z(0.107)."""
+    rows = [(0.0, 0.333, 0.0), (0.0, 0.0, -math.pi / 2), (0.0, 0.316, math.pi / 2), (0.0825, 0.0, math.pi / 2),
+            (-0.0825, 0.384, -math.pi / 2), (0.0, 0.0, math.pi / 2), (0.088, 0.0, math.pi / 2)]
+
+    def rx(a):
+        c, s = math.cos(a), math.sin(a)
+        return np.array([[1, 0, 0, 0], [0, c, -s, 0], [0, s, c, 0], [0, 0, 0, 1.0]])
+
+    def rz(a):
+        c, s = math.cos(a), math.sin(a)
+        return np.array([[c, -s, 0, 0], [s, c, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1.0]])
+
+    def tr(x, z):
+        T = np.eye(4)
+        T[0, 3], T[2, 3] = x, z
+        return T
+
+    T = np.eye(4)
+    for (a, d, al), qi in zip(rows, q):
+        T = T @ rx(al) @ tr(a, 0.0) @ rz(qi) @ tr(0.0, d)
+    return (T @ tr(0.0, 0.107))[:3, 3]
+
+
+def test_franka_kinematics_match_the_published_modified_dh_chain():
+    """The standard-DH rows of the Franka model reproduce the manufacturer's modified-DH chain: the
+    flange at q = 0 is the Panda's documented (0.088, 0, 0.926), and at random joint angles the
+    flange position equals that of an independent modified-DH evaluation."""
+    inst = W.franka(0, T=5)
+    inst.link_spheres = np.array([[7, 0.0, 0.0, 0.0, 0.05]])
+    assert np.allclose(models.arm_link_sphere_centres(inst, np.zeros(7))[0], [0.088, 0.0, 0.926], atol=1e-12)
+    for _ in range(5):
+        q = RNG.uniform(-2.5, 2.5, size=7)
+        assert np.allclose(models.arm_link_sphere_centres(inst, q)[0], _modified_dh_flange(q), atol=1e-12)
+
+
+def test_franka_dynamics_damping_and_clamping():
+    """q̈ = (τ - d q̇)/I with forward Euler, velocity then position clamped to the limits; the
+    Jacobian of a clamped component is zero, elsewhere it matches central differences."""
+    inst = W.franka(1, T=5)
+    dt, d = inst.dt, 0.5
+    x = np.concatenate([inst.x0[:7], 0.3 * RNG.uniform(-1, 1, size=7)])
+    u = RNG.uniform(-5, 5, size=7)
+    y = models.step(inst, x, u)
+    dq1 = x[7:] + (u - d * x[7:]) * dt
+    assert np.allclose(y[7:], dq1, atol=1e-15) and np.allclose(y[:7], x[:7] + dq1 * dt, atol=1e-15)
+    A, B = models.jacobians(inst, x, u)
+    assert np.allclose(A, _central_jac(lambda z: models.step(inst, z, u), x), atol=1e-7)
+    assert np.allclose(B, _central_jac(lambda v: models.step(inst, x, v), u), atol=1e-7)
+    assert np.allclose(A[7:, 7:], (1 - d * dt) * np.eye(7)) and np.allclose(B[7:], dt * np.eye(7))
+    # joint 0 pushed past its velocity limit, joint 1 past its position limit
+    x2 = x.copy()
+    x2[7] = inst.x_hi[7] - 1e-3
+    u2 = u.copy()
+    u2[0] = 80.0
+    x2[1] = inst.x_hi[1] - 1e-4
+    x2[8] = 1.0
+    y2 = models.step(inst, x2, u2)
+    assert y2[7] == inst.x_hi[7] and y2[1] == inst.x_hi[1]
+    A2, B2 = models.jacobians(inst, x2, u2)
+    assert not A2[7].any() and not B2[7].any() and not A2[1].any() and not B2[1].any()
+    assert A2[0, 7] == 0.0 and B2[0, 0] == 0.0          # q_0 moves with the clamped velocity
+    # the 21-value table (no damping, unit inertia, no clamping) is the double integrator
+    dbl = W.arm(0, T=5)
+    yd = models.step(dbl, x, u)
+    assert np.allclose(yd[7:], x[7:] + u * dbl.dt) and np.allclose(yd[:7], x[:7] + yd[7:] * dbl.dt)
