@@ -46,7 +46,12 @@ typedef enum {
 } nrto_status;
 
 typedef enum { NRTO_DYN_UNICYCLE = 0, NRTO_DYN_QUADCOPTER = 1, NRTO_DYN_ARM = 2 } nrto_dyn_kind;
-typedef enum { NRTO_SOLVER_DR = 0, NRTO_SOLVER_FULLADMM = 1 } nrto_solver_kind;
+/* NRTO_SOLVER_FULLADMM: Algorithm 1 with block 2a lifted (the linearized robust constraints and the
+ * trust region as projected slack variables, so that block 2a is an LQ problem with a factorization
+ * fixed per outer step).  NRTO_SOLVER_FULLADMM_AW: block 2a as the paper states it (Sec. IV), the
+ * constrained (δû, p) QP solved exactly every iteration (NRTO-DR's subproblem 2 with v = p̃ - λ_p);
+ * fixed ρ, no carry, no warm start.  Both have the Problem 2 solution as fixed point. */
+typedef enum { NRTO_SOLVER_DR = 0, NRTO_SOLVER_FULLADMM = 1, NRTO_SOLVER_FULLADMM_AW = 2 } nrto_solver_kind;
 typedef enum { NRTO_PREC_FP64 = 0, NRTO_PREC_MIXED = 1 } nrto_precision;
 
 /* One instance of Problem 1 (Sec. II-A).  Dimensions must match the model:
@@ -55,7 +60,12 @@ typedef struct {
   int dyn;                       /* nrto_dyn_kind                                              */
   int nx, nu, T;                 /* state dim, input dim, horizon (1 <= T <= 256/160/128)     */
   double dt;                     /* forward-Euler step (> 0)                                   */
-  const double* dyn_params;      /* quadcopter [m, g, Jx, Jy, Jz]; arm DH (a,d,α)×7; unicycle none */
+  const double* dyn_params;      /* quadcopter [m, g, Jx, Jy, Jz]; unicycle none; arm: standard-DH rows
+                                    (a, d, α) × 7 — 21 values: the double integrator — optionally
+                                    followed by damping d (7), inertia I (7) and a clamping flag (1):
+                                    the Franka model q̈ = (τ - d q̇)/I with the joint position and
+                                    velocity limits (the state bounds) clamped after each Euler step
+                                    (Supplementary Sec. IV-A)                                       */
   int n_dyn_params;
   const double* x0;              /* nx    nominal initial state x̄_0                            */
   const double* x_goal;          /* nx    goal of the state-tracking cost                       */
@@ -235,10 +245,11 @@ enum {
 nrto_status nrto_export(nrto_problem_t p, int field, int instance, double* dst, long long count);
 nrto_status nrto_import(nrto_problem_t p, int field, int instance, const double* src, long long count);
 
-/* Solver-kernel timing with CUDA events recorded on the problem's stream around every launch of the
- * persistent inner-loop kernels.  Returns (and clears) the milliseconds and launch count accumulated
- * since the previous call, then enables (enable != 0) or disables recording for later solves.
- * Synchronizes the stream when events are pending. */
+/* Solver-kernel timing with CUDA events recorded on the problem's stream around the persistent
+ * inner-loop launches of each inner solve (one launch per dynamics kind in the batch; the kinds' launches
+ * run at the same time on two streams).  Returns (and clears) the milliseconds of those intervals and
+ * the number of kernel launches in them since the previous call, then enables (enable != 0) or
+ * disables recording for later solves.  Synchronizes the stream when events are pending. */
 nrto_status nrto_profile(nrto_problem_t p, int enable, double* solver_ms, long long* solver_launches);
 
 /* Per-phase SM cycles of the inner-loop kernels, summed over CTAs (thread 0 of each CTA marks the

@@ -63,6 +63,7 @@ size_t smem_for(int kind, int chunk, int max_rows) {
 struct KindLaunch {
   int kind = 0, count = 0, order0 = 0, tmax = 0, chunk = 0, max_rows = 0;
   size_t smem = 0;
+  long long entries = 0;   // row entries of the kind's instances (the launches start with the largest)
 };
 
 // ---- small kernels of the outer loop ----
@@ -229,6 +230,11 @@ struct nrto_problem {
   double* h_stage = nullptr;
   double* h_ustage = nullptr;
   double* d_ustage = nullptr;
+  // Second stream for running the persistent solver launches of different dynamics kinds at the
+  // same time (the tail of one kind's launch overlaps the next kind's instances), with fork / join
+  // events.  Not created for nrto_solve_noalloc, whose launches run one after another.
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool linearized = false;
   bool warm_pending = false;
   // A FullADMM inner solve ran since the last reset, so its final state can start the next one
@@ -259,6 +265,9 @@ struct nrto_problem {
   }
   ~nrto_problem() {
     for (auto& ev : prof_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (stream2) cudaStreamDestroy(stream2);
     for (void* a : allocs) cudaFree(a);
     if (h_stage) cudaFreeHost(h_stage);
     if (h_ustage) cudaFreeHost(h_ustage);
@@ -317,6 +326,20 @@ void validate(const nrto_problem_desc& d, int idx) {
   const int need_dyn = d.dyn == KIND_QUADCOPTER ? 5 : (d.dyn == KIND_ARM ? 21 : 0);
   if (d.n_dyn_params < need_dyn || d.n_dyn_params > MAX_DYN) bad("wrong number of dyn_params");
   if (!finite_arr(d.dyn_params, d.n_dyn_params)) bad("dyn_params not finite");
+  if (d.dyn == KIND_ARM) {
+    // 21 values: DH table only (double integrator); 36: DH, damping, inertia, clamping flag
+    if (d.n_dyn_params != 21 && d.n_dyn_params != ARM_NPRM) bad("arm dyn_params must hold 21 or 36 values");
+    if (d.n_dyn_params == ARM_NPRM) {
+      for (int i = 0; i < 7; ++i) {
+        if (!(d.dyn_params[ARM_DAMP + i] >= 0)) bad("arm damping must be >= 0");
+        if (!(d.dyn_params[ARM_INERT + i] > 0)) bad("arm inertia must be > 0");
+      }
+      const double cl = d.dyn_params[ARM_CLIP];
+      if (cl != 0.0 && cl != 1.0) bad("arm clamping flag must be 0 or 1");
+      if (cl == 1.0 && (!finite_arr(d.x_lo, 14) || !finite_arr(d.x_hi, 14)))
+        bad("arm clamping needs finite state bounds (the joint position and velocity limits)");
+    }
+  }
   if (!finite_arr(d.x0, d.nx) || !finite_arr(d.x_goal, d.nx) || !finite_arr(d.u_ref, d.nu)) bad("x0/x_goal/u_ref");
   if (!finite_arr(d.u_init, (long long)d.T * d.nu)) num("u_init not finite");
   if (!finite_arr(d.Sigma, (long long)(d.T + 1) * d.nx * d.nx)) num("Sigma not finite");
@@ -398,6 +421,8 @@ void pack_params(const nrto_problem_desc& d, const Arena& L, double* dst) {
   put(L.ulo, d.u_lo, d.nu); put(L.uhi, d.u_hi, d.nu); put(L.xlo, d.x_lo, d.nx); put(L.xhi, d.x_hi, d.nx);
   if (d.n_dyn_params > 0) put(L.dyn, d.dyn_params, d.n_dyn_params);
   for (int i = d.n_dyn_params; i < MAX_DYN; ++i) dst[L.dyn + i] = 0.0;   // the staging is reused across updates
+  if (d.dyn == KIND_ARM && d.n_dyn_params == 21)
+    for (int i = 0; i < 7; ++i) dst[L.dyn + ARM_INERT + i] = 1.0;   // the double integrator: unit inertia
   for (int o = 0; o < d.n_obs; ++o) {
     for (int k = 0; k < 3; ++k) dst[L.obs + 4 * o + k] = (k < d.obs_dim) ? d.obs_center[o * d.obs_dim + k] : 0.0;
     dst[L.obs + 4 * o + 3] = d.obs_radius[o];
@@ -429,7 +454,7 @@ void launch_linearize(nrto_problem* P, int slot_sel) {
 // One persistent launch of a solver kernel (FullADMM or NRTO-DR) for the instances of one kind:
 // as many CTAs as fit on the GPU, at most one per instance; CTAs take instances from the queue.
 template <int NX, int NU, typename Real>
-void launch_solver_kind(nrto_problem* P, int solver, const KindLaunch& kl, SolveParams sp) {
+void launch_solver_kind(nrto_problem* P, int solver, const KindLaunch& kl, SolveParams sp, cudaStream_t st) {
   using SK = SolverKernel<NX, NU, Real>;
   const char* name = solver == SOLVER_KERNEL_FULLADMM ? "k_fulladmm" : "k_dr";
   int dev = 0, nsm = 0, per_sm = 0;
@@ -440,25 +465,52 @@ void launch_solver_kind(nrto_problem* P, int solver, const KindLaunch& kl, Solve
   const int grid = std::min(kl.count, nsm * per_sm);
   sp.chunk = kl.chunk; sp.max_rows = kl.max_rows; sp.tmax = kl.tmax; sp.n_order = kl.count;
   sp.order0 = kl.order0; sp.queue_idx = kl.kind;
+  const cudaError_t le = SK::launch(solver, grid, kl.smem, st, P->dev<Real>(), sp);
+  ++P->launches;
+  if (le != cudaSuccess) fail(NRTO_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(le));
+  if (P->profiling) P->prof_launches++;
+}
+
+// The persistent solver launches of every dynamics kind present: the first on the problem's stream,
+// the others on the second stream between fork / join events, so that a kind's CTAs start on the SMs
+// that the previous kind's launch frees at its end.  Profiling records one event pair around them.
+template <typename Real>
+void launch_solver_kinds(nrto_problem* P, int solver, const SolveParams& sp) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (P->profiling) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, P->stream));
   }
-  const cudaError_t le = SK::launch(solver, grid, kl.smem, P->stream, P->dev<Real>(), sp);
-  ++P->launches;
-  if (le != cudaSuccess) fail(NRTO_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(le));
+  int kinds[3] = {0, 1, 2};
+  std::stable_sort(kinds, kinds + 3, [&](int a, int b) { return P->kl[a].entries > P->kl[b].entries; });
+  int launched = 0;
+  bool forked = false;
+  for (int k : kinds) {
+    const KindLaunch& kl = P->kl[k];
+    if (kl.count == 0) continue;
+    cudaStream_t st = P->stream;
+    if (launched > 0 && P->stream2) {
+      if (!forked) {
+        CK(cudaEventRecord(P->ev_fork, P->stream));
+        CK(cudaStreamWaitEvent(P->stream2, P->ev_fork, 0));
+        forked = true;
+      }
+      st = P->stream2;
+    }
+    if (k == KIND_UNICYCLE) launch_solver_kind<3, 2, Real>(P, solver, kl, sp, st);
+    else if (k == KIND_QUADCOPTER) launch_solver_kind<12, 4, Real>(P, solver, kl, sp, st);
+    else launch_solver_kind<14, 7, Real>(P, solver, kl, sp, st);
+    ++launched;
+  }
+  if (forked) {
+    CK(cudaEventRecord(P->ev_join, P->stream2));
+    CK(cudaStreamWaitEvent(P->stream, P->ev_join, 0));
+  }
   if (P->profiling) {
     CK(cudaEventRecord(e1, P->stream));
     P->prof_events.push_back({e0, e1});
-    P->prof_launches++;
   }
-}
-
-template <int NX, int NU, typename Real>
-void launch_fa_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
-  launch_solver_kind<NX, NU, Real>(P, SOLVER_KERNEL_FULLADMM, kl, sp);
 }
 
 template <typename Real>
@@ -475,19 +527,20 @@ void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
   sp.fallback = o.warm_fallback;
   P->warm_pending = false;
   if (o.solver == NRTO_SOLVER_FULLADMM) {
-    k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.rho, 0.0);
+    k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.rho, 0.0, sp.warm);
     P->check_launch("k_gain_factors");
-    k_riccati_factor<Real><<<P->n, 32, 0, P->stream>>>(D, o.rho);
+    k_riccati_factor<Real><<<P->n, 32, 0, P->stream>>>(D, o.rho, sp.warm);
     P->check_launch("k_riccati_factor");
     CK(cudaMemsetAsync(P->d_queue, 0, 4 * sizeof(int), P->stream));
-    for (int k = 0; k < 3; ++k) {
-      const KindLaunch& kl = P->kl[k];
-      if (kl.count == 0) continue;
-      if (k == KIND_UNICYCLE) launch_fa_kind<3, 2, Real>(P, kl, sp);
-      else if (k == KIND_QUADCOPTER) launch_fa_kind<12, 4, Real>(P, kl, sp);
-      else launch_fa_kind<14, 7, Real>(P, kl, sp);
-    }
+    launch_solver_kinds<Real>(P, SOLVER_KERNEL_FULLADMM, sp);
     P->carry_ok = true;
+  } else if (o.solver == NRTO_SOLVER_FULLADMM_AW) {
+    // block 2a factors its own Newton systems; only the gain-solve factors are needed
+    k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.rho, 0.0, 0);
+    P->check_launch("k_gain_factors");
+    CK(cudaMemsetAsync(P->d_queue, 0, 4 * sizeof(int), P->stream));
+    launch_solver_kinds<Real>(P, SOLVER_KERNEL_FULLADMM_AW, sp);
+    P->carry_ok = false;
   } else {
     launch_dr<Real>(P, o, sp);
     P->carry_ok = false;
@@ -528,8 +581,26 @@ void launch_outer_step(nrto_problem* P, const nrto_solver_opts& o) {
   P->check_launch("k_accept");
 }
 
+// Threads of one row group of the solver kernels' row pass for the longest horizon of a launch; it
+// must not exceed the CTA, or some columns of the rows would have no thread.
+template <int NX, int NU, typename Real>
+int row_group_threads(int tmax) {
+  using C = FACfg<NX, NU, Real>;
+  return ((tmax / 2 + 1) * C::NCG + 31) / 32 * 32;
+}
+
+template <typename Real>
+void check_row_groups(const KindLaunch& kl) {
+  int tpg = 0, nt = 0;
+  if (kl.kind == KIND_UNICYCLE) { tpg = row_group_threads<3, 2, Real>(kl.tmax); nt = FACfg<3, 2, Real>::NT; }
+  else if (kl.kind == KIND_QUADCOPTER) { tpg = row_group_threads<12, 4, Real>(kl.tmax); nt = FACfg<12, 4, Real>::NT; }
+  else { tpg = row_group_threads<14, 7, Real>(kl.tmax); nt = FACfg<14, 7, Real>::NT; }
+  if (tpg > nt) fail(NRTO_ERR_INVALID, "horizon too long for the solver kernel's thread block");
+}
+
 template <typename Real>
 void choose_chunk(KindLaunch& kl) {
+  check_row_groups<Real>(kl);
   const int nx = kind_nx(kl.kind);
   const int minc = ((kl.tmax + 1) * nx + 3) & ~3;
   int chunk = 12288;
@@ -644,7 +715,8 @@ void upload_params(nrto_problem* P, const nrto_problem_desc* descs) {
 
 void check_opts(const nrto_solver_opts* o) {
   if (!o) fail(NRTO_ERR_INVALID, "null options");
-  if (o->solver != NRTO_SOLVER_DR && o->solver != NRTO_SOLVER_FULLADMM) fail(NRTO_ERR_INVALID, "unknown solver");
+  if (o->solver != NRTO_SOLVER_DR && o->solver != NRTO_SOLVER_FULLADMM && o->solver != NRTO_SOLVER_FULLADMM_AW)
+    fail(NRTO_ERR_INVALID, "unknown solver");
   if (!(o->rho > 0)) fail(NRTO_ERR_INVALID, "rho must be positive");
   if (o->max_inner < 0 || o->max_inner > 1000000) fail(NRTO_ERR_INVALID, "max_inner out of range");
   if (o->adapt_every < 0 || o->stall_every < 0) fail(NRTO_ERR_INVALID, "adapt_every and stall_every must be >= 0");
@@ -863,6 +935,11 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
     P->n = n;
     P->prec = precision;
     P->stream = static_cast<cudaStream_t>(stream);
+    if (!carve_base) {
+      CK(cudaStreamCreateWithFlags(&P->stream2, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    }
     for (int k = 0; k < 3; ++k) P->kl[k].kind = k;
     for (int i = 0; i < n; ++i) {
       KindLaunch& kl = P->kl[descs[i].dyn];
@@ -996,7 +1073,10 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
       for (int i = 0; i < n; ++i)
         if (P->h_inst[i].kind == k) ids.push_back(i);
       std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return P->h_inst[a].n_ent > P->h_inst[b].n_ent; });
-      for (int id : ids) P->h_order.push_back(id);
+      for (int id : ids) {
+        P->h_order.push_back(id);
+        P->kl[k].entries += P->h_inst[id].n_ent;
+      }
       o += (int)ids.size();
     }
     const size_t rs = precision == NRTO_PREC_FP64 ? sizeof(double) : sizeof(float);
@@ -1419,23 +1499,12 @@ extern "C" nrto_status nrto_solve_noalloc(const nrto_problem_desc* descs, int n,
   }
 }
 
-template <int NX, int NU, typename Real>
-void launch_dr_kind(nrto_problem* P, const KindLaunch& kl, SolveParams sp) {
-  launch_solver_kind<NX, NU, Real>(P, SOLVER_KERNEL_DR, kl, sp);
-}
-
 // NRTO-DR: gain-solve factors for (Q_v + r_χ I + σ Σ Â_jᵀÂ_j), then one persistent launch per kind.
 template <typename Real>
 void launch_dr(nrto_problem* P, const nrto_solver_opts& o, SolveParams sp) {
   Dev<Real> D = P->dev<Real>();
-  k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.sigma, o.r_chi);
+  k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.sigma, o.r_chi, 0);
   P->check_launch("k_gain_factors");
   CK(cudaMemsetAsync(P->d_queue, 0, 4 * sizeof(int), P->stream));
-  for (int k = 0; k < 3; ++k) {
-    const KindLaunch& kl = P->kl[k];
-    if (kl.count == 0) continue;
-    if (k == KIND_UNICYCLE) launch_dr_kind<3, 2, Real>(P, kl, sp);
-    else if (k == KIND_QUADCOPTER) launch_dr_kind<12, 4, Real>(P, kl, sp);
-    else launch_dr_kind<14, 7, Real>(P, kl, sp);
-  }
+  launch_solver_kinds<Real>(P, SOLVER_KERNEL_DR, sp);
 }

@@ -15,7 +15,8 @@
 //        v = p̃ - λ/ρ leaves a strongly convex squared hinge in δû.  It is minimized by semismooth
 //        Newton with Armijo backtracking.  Each Newton target is an LQ problem whose stage costs
 //        carry ρ a_j a_jᵀ for the active rows, solved by a Riccati recursion (warp 0).  The trust
-//        region ‖F_u δû‖ ≤ r is enforced by a multiplier μ ≥ 0 found by bisection.
+//        region ‖F_u δû‖ ≤ r is enforced by a multiplier μ ≥ 0, the root of ‖F_u δû(μ)‖² = r²
+//        (bracket grown by 4, then Illinois regula falsi).
 //   (4c) λ ← λ + ρ(p - p̃);  r_p = ‖p - p̃‖,  r_d = ρ‖p^l - p^{l-1}‖.
 //
 // Per-row storage in the DR path: p → D.p, λ (unscaled) → D.lamp, p̃ → D.pt, p̃̃ → D.w, t̃ → D.lamw,
@@ -340,17 +341,16 @@ __device__ void sub2_ssn(const Dev<Real>& D, const Inst& I, const LinSlot<Real>&
   (void)s_int;
 }
 
-// Subproblem 2 (exact): δû, δx into the arena (du, dx), ℓ_j = b_jᵀδû into D.ell.  v = p̃ - λ/ρ.
+// Subproblem 2 (exact) with w_j = v_j + g_j already in D.ptn: δû, δx into the arena (du, dx),
+// ℓ_j = b_jᵀδû into D.ell.  Shared by NRTO-DR (v = p̃ - λ/ρ) and the as-written FullADMM block 2a
+// (v = p̃ - λ_p, scaled dual).
 template <int NX, int NU, typename Real>
-__device__ __noinline__ void sub2_solve(const Dev<Real>& D, const Inst& I, const LinSlot<Real>& S, double* ar,
-                                        const Arena& L, const double* sa, const SlotL& SL, double rho, double r_trust,
-                                        double* red, double* vec, double* scr, int* s_int) {
+__device__ __noinline__ void sub2_solve_w(const Dev<Real>& D, const Inst& I, const LinSlot<Real>& S, double* ar,
+                                          const Arena& L, const double* sa, const SlotL& SL, double rho,
+                                          double r_trust, double* red, double* vec, double* scr, int* s_int) {
   const int T = I.T, tid = threadIdx.x, warp = tid >> 5;
   const int n_rows = I.n_sr + I.n_cr;
-  for (int r = tid; r < n_rows; r += blockDim.x) {
-    const long long R = I.row0 + r;
-    D.ptn[R] = (D.pt[R] - D.lamp[R] / rho) + S.g0[R];   // w_j = v_j + g_j
-  }
+  __syncthreads();
   double* xu = ar + L.du_prev;
   double* xx = ar + L.dx_prev;
   double* hu = ar + L.Ws1;
@@ -368,29 +368,47 @@ __device__ __noinline__ void sub2_solve(const Dev<Real>& D, const Inst& I, const
   __syncthreads();
   sub2_ssn<NX, NU, Real>(D, I, S, ar, L, sa, SL, xu, xx, 0.0, rho, cnorm, red, vec, scr, s_int);
   const double r2 = r_trust * r_trust;
-  if (traj_norm2(xx, T, NX, red) > r2) {
+  // φ(μ) = ‖F̃ δû(μ)‖² - r², decreasing in μ: the trust multiplier is its root when φ(0) > 0
+  double fa = traj_norm2(xx, T, NX, red) - r2;
+  if (fa > 0.0) {
+    // bracket [lo, hi] with φ(lo) > 0 >= φ(hi), growing hi by 4
     double lo = 0.0, hi = 1.0;
     sub2_ssn<NX, NU, Real>(D, I, S, ar, L, sa, SL, xu, xx, hi, rho, cnorm, red, vec, scr, s_int);
-    for (int grow = 0; grow < 64 && traj_norm2(xx, T, NX, red) > r2; ++grow) {
+    double fb = traj_norm2(xx, T, NX, red) - r2;
+    for (int grow = 0; grow < 64 && fb > 0.0; ++grow) {
       lo = hi;
+      fa = fb;
       hi *= 4.0;
       sub2_ssn<NX, NU, Real>(D, I, S, ar, L, sa, SL, xu, xx, hi, rho, cnorm, red, vec, scr, s_int);
+      fb = traj_norm2(xx, T, NX, red) - r2;
     }
     copy_vec(hu, xu, nu_t);
     copy_vec(hx, xx, nx_t);
+    // Illinois regula falsi (a bracketing secant; the endpoint kept twice in a row has its φ
+    // halved), each point solved from the feasible end's solution; the feasible end is returned
+    // once the bracket is 1e-14 relative
+    int side = 0;
     for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
+      double mc = hi - fb * (hi - lo) / (fb - fa);
+      if (!(lo < mc && mc < hi)) mc = 0.5 * (lo + hi);
       copy_vec(xu, hu, nu_t);
       copy_vec(xx, hx, nx_t);
-      sub2_ssn<NX, NU, Real>(D, I, S, ar, L, sa, SL, xu, xx, mid, rho, cnorm, red, vec, scr, s_int);
-      if (traj_norm2(xx, T, NX, red) > r2) {
-        lo = mid;
+      sub2_ssn<NX, NU, Real>(D, I, S, ar, L, sa, SL, xu, xx, mc, rho, cnorm, red, vec, scr, s_int);
+      const double fc = traj_norm2(xx, T, NX, red) - r2;
+      if (fc > 0.0) {
+        lo = mc;
+        fa = fc;
+        if (side == -1) fb *= 0.5;
+        side = -1;
       } else {
-        hi = mid;
+        hi = mc;
+        fb = fc;
         copy_vec(hu, xu, nu_t);
         copy_vec(hx, xx, nx_t);
+        if (side == 1) fa *= 0.5;
+        side = 1;
       }
-      if (hi - lo <= 1e-14 * hi) break;
+      if (hi - lo <= 1e-14 * hi || fc == 0.0) break;
     }
     copy_vec(xu, hu, nu_t);
     copy_vec(xx, hx, nx_t);
@@ -400,6 +418,18 @@ __device__ __noinline__ void sub2_solve(const Dev<Real>& D, const Inst& I, const
   for (int r = tid; r < n_rows; r += blockDim.x)
     D.ell[I.row0 + r] = row_ell<NX, NU, Real>(D, I, S, r, ar + L.du, ar + L.dx);
   __syncthreads();
+}
+
+// Subproblem 2 of NRTO-DR: v = p̃ - λ/ρ (unscaled λ).
+template <int NX, int NU, typename Real>
+__device__ __forceinline__ void sub2_solve(const Dev<Real>& D, const Inst& I, const LinSlot<Real>& S, double* ar,
+                                           const Arena& L, const double* sa, const SlotL& SL, double rho,
+                                           double r_trust, double* red, double* vec, double* scr, int* s_int) {
+  for (int r = threadIdx.x; r < I.n_sr + I.n_cr; r += blockDim.x) {
+    const long long R = I.row0 + r;
+    D.ptn[R] = (D.pt[R] - D.lamp[R] / rho) + S.g0[R];   // w_j = v_j + g_j
+  }
+  sub2_solve_w<NX, NU, Real>(D, I, S, ar, L, sa, SL, rho, r_trust, red, vec, scr, s_int);
 }
 
 // ----------------------------------------------------------------------------------------------

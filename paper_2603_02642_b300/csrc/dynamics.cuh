@@ -1,16 +1,18 @@
 // Analytic dynamics, Jacobians and constraint gradients (device side of libnrto).
 //
 // Models (Supplementary Sec. IV-A, forward Euler): unicycle (3,2), quadcopter (12,4) with
-// R = Rz(ψ)Ry(θ)Rx(φ) and Euler-rate map T(φ,θ), and a 7-joint double integrator whose link
-// spheres move through a Denavit–Hartenberg chain (the arm workload).
+// R = Rz(ψ)Ry(θ)Rx(φ) and Euler-rate map T(φ,θ), and the 7-joint Franka joint-space model (damping,
+// inertia, clamped limits; the double integrator when those are off) whose link spheres move through
+// a Denavit–Hartenberg chain.
 #pragma once
 #include "nrto_dev.cuh"
 
 namespace nrto {
 
 // x_{k+1} = f(x_k, u_k); A = ∂f/∂x, B = ∂f/∂u (row-major nx×nx, nx×nu). A, B may be null.
+// xlo, xhi: the state bounds (the arm's clamping limits).
 __device__ inline void dyn_step(int kind, const double* prm, double dt, const double* x, const double* u,
-                                double* xn, double* A, double* B) {
+                                double* xn, double* A, double* B, const double* xlo, const double* xhi) {
   if (kind == KIND_UNICYCLE) {
     double c = cos(x[2]), s = sin(x[2]);
     xn[0] = x[0] + u[0] * c * dt;
@@ -81,20 +83,38 @@ __device__ inline void dyn_step(int kind, const double* prm, double dt, const do
     }
     return;
   }
-  // arm: q̇' = q̇ + u dt, q' = q + q̇' dt
+  // arm (Franka joint-space model): q̈ = (τ - d q̇)/I; q̇' = clip(q̇ + q̈ dt), q' = clip(q + q̇' dt) when
+  // clamping is on (limits: the state bounds).  A clamped component has zero derivatives.
+  const double* dmp = prm + ARM_DAMP;
+  const double* inr = prm + ARM_INERT;
+  const bool clamp = prm[ARM_CLIP] != 0.0;
+  if (A) for (int i = 0; i < 196; ++i) A[i] = 0.0;
+  if (B) for (int i = 0; i < 98; ++i) B[i] = 0.0;
   for (int i = 0; i < 7; ++i) {
-    double dq1 = x[7 + i] + u[i] * dt;
-    xn[7 + i] = dq1;
-    xn[i] = x[i] + dq1 * dt;
-  }
-  if (A) {
-    for (int i = 0; i < 196; ++i) A[i] = 0.0;
-    for (int i = 0; i < 14; ++i) A[i * 14 + i] = 1.0;
-    for (int i = 0; i < 7; ++i) A[i * 14 + 7 + i] = dt;
-  }
-  if (B) {
-    for (int i = 0; i < 98; ++i) B[i] = 0.0;
-    for (int i = 0; i < 7; ++i) { B[i * 7 + i] = dt * dt; B[(7 + i) * 7 + i] = dt; }
+    double v = x[7 + i] + (u[i] - dmp[i] * x[7 + i]) / inr[i] * dt;
+    double sv = 1.0;
+    if (clamp) {
+      if (v < xlo[7 + i]) { v = xlo[7 + i]; sv = 0.0; }
+      else if (v > xhi[7 + i]) { v = xhi[7 + i]; sv = 0.0; }
+    }
+    double qn = x[i] + v * dt;
+    double sq = 1.0;
+    if (clamp) {
+      if (qn < xlo[i]) { qn = xlo[i]; sq = 0.0; }
+      else if (qn > xhi[i]) { qn = xhi[i]; sq = 0.0; }
+    }
+    xn[7 + i] = v;
+    xn[i] = qn;
+    const double dv_dv = sv * (1.0 - dt * dmp[i] / inr[i]), dv_du = sv * dt / inr[i];
+    if (A) {
+      A[(7 + i) * 14 + 7 + i] = dv_dv;
+      A[i * 14 + i] = sq;
+      A[i * 14 + 7 + i] = sq * dt * dv_dv;
+    }
+    if (B) {
+      B[(7 + i) * 7 + i] = dv_du;
+      B[i * 7 + i] = sq * dt * dv_du;
+    }
   }
 }
 

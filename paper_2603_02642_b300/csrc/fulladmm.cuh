@@ -50,6 +50,10 @@ struct SolveParams {
 #ifndef NRTO_FA_MINB_F32
 #define NRTO_FA_MINB_F32 1
 #endif
+// consecutive components of a ζ-block per thread in the quadcopter's row pass (2, 3 or 4; 12 = NCG·W)
+#ifndef NRTO_FA_W_QUAD
+#define NRTO_FA_W_QUAD 2
+#endif
 
 template <int NX, int NU, typename Real>
 struct FACfg {
@@ -57,7 +61,7 @@ struct FACfg {
   static constexpr int MINB = sizeof(Real) == 4 ? NRTO_FA_MINB_F32 : 1;   // resident CTAs per SM
   static constexpr int NW = NT / 32;
   static constexpr int TMAXC = (NX == 3) ? 256 : (NX == 12 ? 160 : 128);
-  static constexpr int W = (NX == 3) ? 3 : 2;            // consecutive components of a block per thread
+  static constexpr int W = (NX == 3) ? 3 : (NX == 12 ? NRTO_FA_W_QUAD : 2);   // components of a block per thread
   static constexpr int NCG = NX / W;                     // column groups per ζ-block
   static constexpr int PAIRS = 2;                        // a thread owns blocks m and T - m
   static constexpr int NPAIR_MAX = TMAXC / 2 + 1;        // block pairs of the longest horizon
@@ -786,6 +790,8 @@ template <int N, typename Real>
 __device__ __forceinline__ void st_vec(Real* p, const Real (&v)[N]) {
   if constexpr (N == 2 && sizeof(Real) == 4) {
     *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (N == 4 && sizeof(Real) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   } else if constexpr (N == 2 && sizeof(Real) == 8) {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
   } else {
@@ -800,6 +806,10 @@ template <int N, typename Real>
 __device__ __forceinline__ void st_vec_stream(Real* p, const Real (&v)[N], uint64_t pol) {
   if constexpr (N == 2 && sizeof(Real) == 4) {
     asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"((float)v[0]), "f"((float)v[1]), "l"(pol)
+                 : "memory");
+  } else if constexpr (N == 4 && sizeof(Real) == 4) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"((float)v[0]), "f"((float)v[1]),
+                 "f"((float)v[2]), "f"((float)v[3]), "l"(pol)
                  : "memory");
   } else if constexpr (sizeof(Real) == 4) {
 #pragma unroll
@@ -1122,6 +1132,107 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
   return true;
 }
 
+// Control rows of one FullADMM iteration (block 1 for the rows b_j = ±e_i, b̂_j = 0): the λ_ν update of
+// the previous iteration (first: none), η̂, the cone in the compute precision, Z' and the residual
+// sums prp, prd.  Shared by the lifted and the as-written iterations.
+template <int NX, int NU, typename Real>
+__device__ __forceinline__ void fa_control_rows(const Dev<Real>& D, const Inst& I, double* ar, const Arena& L,
+                                                const double* gtc_arena, const double* gto_arena, bool first,
+                                                bool block1, Real lscale, double& prp, double& prd) {
+  constexpr int NT = FACfg<NX, NU, Real>::NT;
+  const int tid = threadIdx.x;
+  Real* lam = D.lam;
+  // ---------------- control rows (one block each; b = ±e_i, b̂ = 0) ----------------
+  // A group holds the rows of one (k, i), upper before lower bound, which update the same Z'
+  // elements; a thread takes whole groups.  For the common two-row group the loads of both rows
+  // are issued together, in few dependent rounds: each round trip costs a full memory latency while
+  // the row streams keep the memory system loaded.  Both paths update Z' and the residual sums row
+  // after row, in the same order.
+  auto ctrl_row = [&](long long R, const int4 ri, long long e0, Real sold, Real tt, Real (&l)[NX], const Real (&gcv)[NX],
+                      const Real (&gov)[NX], Real& snew, Real (&et)[NX], Real (&lv)[NX]) {
+    const Real sg = (ri.y == ROW_UHI) ? (Real)1 : (Real)-1;
+    Real an = 0, lrp = 0, lrd = 0;   // per-row sums in the compute precision, like the state rows
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      const Real y = sg * gcv[c];
+      Real lc = l[c];
+      if (!first) {
+        const Real yo = sg * gov[c];
+        const Real nu = sold * (yo + lc);
+        const Real ln = lc + y - nu;
+        lrp += (y - nu) * (y - nu);
+        lrd += (y - yo) * (y - yo);
+        lc = ln * lscale;
+        lam[e0 + c] = lc;
+      }
+      lv[c] = lc;
+      et[c] = y + lc;
+      an += et[c] * et[c];
+    }
+    prp += (double)lrp; prd += (double)lrd;
+    if (block1) {
+      // the cone in the compute precision (FP32 cones in mixed mode), as for the state rows
+      Real ptn;
+      soc_case_r<Real>(tt, sqrt(an), snew, ptn);
+      D.s[R] = (double)snew; D.ptn[R] = (double)ptn;
+    }
+  };
+  for (int g = tid; g < I.n_groups; g += NT) {
+    const int2 gr = D.groups[I.grp0 + g];
+    if (gr.y == 2) {
+      const long long RA = gr.x, RB = (long long)gr.x + 1;
+      const int4 riA = D.rinfo[RA], riB = D.rinfo[RB];
+      const long long eA = D.rent[RA], eB = D.rent[RB];
+      const Real sA = (Real)D.s[RA], sB = (Real)D.s[RB];
+      const Real tA = block1 ? (Real)(D.p[RA] + D.lamp[RA]) : (Real)0;
+      const Real tB = block1 ? (Real)(D.p[RB] + D.lamp[RB]) : (Real)0;
+      const long long gofs = (long long)riA.x * NU * NX + riA.z * NX;   // the group's (k, i)
+      Real gcv[NX], gov[NX], lA[NX], lB[NX];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) {
+        gcv[c] = (Real)gtc_arena[gofs + c];
+        gov[c] = first ? (Real)0 : (Real)gto_arena[gofs + c];
+        lA[c] = lam[eA + c];
+        lB[c] = lam[eB + c];
+      }
+      Real snA = 1, snB = 1, etA[NX], etB[NX], lvA[NX], lvB[NX];
+      ctrl_row(RA, riA, eA, sA, tA, lA, gcv, gov, snA, etA, lvA);
+      ctrl_row(RB, riB, eB, sB, tB, lB, gcv, gov, snB, etB, lvB);
+      if (block1) {
+        const Real sgA = (riA.y == ROW_UHI) ? (Real)1 : (Real)-1, sgB = (riB.y == ROW_UHI) ? (Real)1 : (Real)-1;
+#pragma unroll
+        for (int c = 0; c < NX; ++c) {
+          double z = ar[L.Zp + gofs + c];
+          z += (double)(sgA * (snA * etA[c] - lvA[c]));
+          z += (double)(sgB * (snB * etB[c] - lvB[c]));
+          ar[L.Zp + gofs + c] = z;
+        }
+      }
+    } else {
+      for (int q = 0; q < gr.y; ++q) {
+        const long long R = gr.x + q;
+        const int4 ri = D.rinfo[R];
+        const long long e0 = D.rent[R];
+        const long long gofs = (long long)ri.x * NU * NX + ri.z * NX;
+        Real gcv[NX], gov[NX], l[NX];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) {
+          gcv[c] = (Real)gtc_arena[gofs + c];
+          gov[c] = first ? (Real)0 : (Real)gto_arena[gofs + c];
+          l[c] = lam[e0 + c];
+        }
+        Real sn = 1, et[NX], lv[NX];
+        ctrl_row(R, ri, e0, (Real)D.s[R], block1 ? (Real)(D.p[R] + D.lamp[R]) : (Real)0, l, gcv, gov, sn, et, lv);
+        if (block1) {
+          const Real sg = (ri.y == ROW_UHI) ? (Real)1 : (Real)-1;
+#pragma unroll
+          for (int c = 0; c < NX; ++c) ar[L.Zp + gofs + c] += (double)(sg * (sn * et[c] - lv[c]));
+        }
+      }
+    }
+  }
+}
+
 template <int NX, int NU, typename Real>
 __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int inst, FASmem<NX, NU, Real>& sm,
                                   uint64_t* bars, uint32_t* phase, int* s_flag, double* ric_scr) {
@@ -1158,8 +1269,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   // p, p̃, λ_p, λ_ν, λ_w, λ_e and the penalty they are scaled for; δû, δx, e and ℓ too unless the
   // nominal moved to û + δû since (then the previous solution is δû = 0 in the new coordinates).
   // A previous solve that ended on a non-finite residual or a copy timeout is not carried. ----
-  const int prev_st = isr[IS_STATUS];
-  const bool carry = sp.warm == 2 && (prev_st == ST_CONVERGED || prev_st == ST_MAXITER || prev_st == ST_STALLED);
+  const bool carry = carry_applies(D.is, inst, sp.warm);
   const int winit = carry ? 2 : (sp.warm == 1 ? 1 : 0);
   const bool keep_dx = carry && isr[IS_MOVED] == 0;
   if (winit != 2)
@@ -1181,14 +1291,10 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   if (winit == 0)
     for (int q = tid; q < T * NU * NX; q += NT) ar[L.K1 + q] = 0.0;
   if (winit == 2) {
-    // start at the penalty the carried duals are scaled for (block 2 and the gain divisors follow it)
+    // start at the penalty the carried duals are scaled for; the factor kernels launched before
+    // this solve factored block 2 and the gain divisors for it (start_rho)
     rho = sc[SC_RHOD];
     rho_done = rho;
-    if (rho != sp.rho) {
-      gain_divisors<Real>(D, inst, rho);
-      __syncthreads();
-      if (warp == 0) riccati_factor_warp<Real>(D, inst, rho, ric_scr);
-    }
   }
   __syncthreads();
   // Gtᵀ of the initial gains into Gt1 ("current"); Gt0 is the "previous" table
@@ -1252,96 +1358,8 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     }
     __syncthreads();
     tm.mark(PH_ROWS);
-    // ---------------- control rows (one block each; b = ±e_i, b̂ = 0) ----------------
-    // A group holds the rows of one (k, i), upper before lower bound, which update the same Z'
-    // elements; a thread takes whole groups.  For the common two-row group the loads of both rows
-    // are issued together, in few dependent rounds: each round trip costs a full memory latency while
-    // the row streams keep the memory system loaded.  Both paths update Z' and the residual sums row
-    // after row, in the same order.
     double prp = (double)arp, prd = (double)ard;
-    auto ctrl_row = [&](long long R, const int4 ri, long long e0, Real sold, Real tt, Real (&l)[NX], const Real (&gcv)[NX],
-                        const Real (&gov)[NX], Real& snew, Real (&et)[NX], Real (&lv)[NX]) {
-      const Real sg = (ri.y == ROW_UHI) ? (Real)1 : (Real)-1;
-      Real an = 0, lrp = 0, lrd = 0;   // per-row sums in the compute precision, like the state rows
-#pragma unroll
-      for (int c = 0; c < NX; ++c) {
-        const Real y = sg * gcv[c];
-        Real lc = l[c];
-        if (!first) {
-          const Real yo = sg * gov[c];
-          const Real nu = sold * (yo + lc);
-          const Real ln = lc + y - nu;
-          lrp += (y - nu) * (y - nu);
-          lrd += (y - yo) * (y - yo);
-          lc = ln * lscale;
-          lam[e0 + c] = lc;
-        }
-        lv[c] = lc;
-        et[c] = y + lc;
-        an += et[c] * et[c];
-      }
-      prp += (double)lrp; prd += (double)lrd;
-      if (block1) {
-        // the cone in the compute precision (FP32 cones in mixed mode), as for the state rows
-        Real ptn;
-        soc_case_r<Real>(tt, sqrt(an), snew, ptn);
-        D.s[R] = (double)snew; D.ptn[R] = (double)ptn;
-      }
-    };
-    for (int g = tid; g < I.n_groups; g += NT) {
-      const int2 gr = D.groups[I.grp0 + g];
-      if (gr.y == 2) {
-        const long long RA = gr.x, RB = (long long)gr.x + 1;
-        const int4 riA = D.rinfo[RA], riB = D.rinfo[RB];
-        const long long eA = D.rent[RA], eB = D.rent[RB];
-        const Real sA = (Real)D.s[RA], sB = (Real)D.s[RB];
-        const Real tA = block1 ? (Real)(D.p[RA] + D.lamp[RA]) : (Real)0;
-        const Real tB = block1 ? (Real)(D.p[RB] + D.lamp[RB]) : (Real)0;
-        const long long gofs = (long long)riA.x * NU * NX + riA.z * NX;   // the group's (k, i)
-        Real gcv[NX], gov[NX], lA[NX], lB[NX];
-#pragma unroll
-        for (int c = 0; c < NX; ++c) {
-          gcv[c] = (Real)gtc_arena[gofs + c];
-          gov[c] = first ? (Real)0 : (Real)gto_arena[gofs + c];
-          lA[c] = lam[eA + c];
-          lB[c] = lam[eB + c];
-        }
-        Real snA = 1, snB = 1, etA[NX], etB[NX], lvA[NX], lvB[NX];
-        ctrl_row(RA, riA, eA, sA, tA, lA, gcv, gov, snA, etA, lvA);
-        ctrl_row(RB, riB, eB, sB, tB, lB, gcv, gov, snB, etB, lvB);
-        if (block1) {
-          const Real sgA = (riA.y == ROW_UHI) ? (Real)1 : (Real)-1, sgB = (riB.y == ROW_UHI) ? (Real)1 : (Real)-1;
-#pragma unroll
-          for (int c = 0; c < NX; ++c) {
-            double z = ar[L.Zp + gofs + c];
-            z += (double)(sgA * (snA * etA[c] - lvA[c]));
-            z += (double)(sgB * (snB * etB[c] - lvB[c]));
-            ar[L.Zp + gofs + c] = z;
-          }
-        }
-      } else {
-        for (int q = 0; q < gr.y; ++q) {
-          const long long R = gr.x + q;
-          const int4 ri = D.rinfo[R];
-          const long long e0 = D.rent[R];
-          const long long gofs = (long long)ri.x * NU * NX + ri.z * NX;
-          Real gcv[NX], gov[NX], l[NX];
-#pragma unroll
-          for (int c = 0; c < NX; ++c) {
-            gcv[c] = (Real)gtc_arena[gofs + c];
-            gov[c] = first ? (Real)0 : (Real)gto_arena[gofs + c];
-            l[c] = lam[e0 + c];
-          }
-          Real sn = 1, et[NX], lv[NX];
-          ctrl_row(R, ri, e0, (Real)D.s[R], block1 ? (Real)(D.p[R] + D.lamp[R]) : (Real)0, l, gcv, gov, sn, et, lv);
-          if (block1) {
-            const Real sg = (ri.y == ROW_UHI) ? (Real)1 : (Real)-1;
-#pragma unroll
-            for (int c = 0; c < NX; ++c) ar[L.Zp + gofs + c] += (double)(sg * (sn * et[c] - lv[c]));
-          }
-        }
-      }
-    }
+    fa_control_rows<NX, NU, Real>(D, I, ar, L, gtc_arena, gto_arena, first, block1, lscale, prp, prd);
     double z2 = 0.0, z3 = 0.0;
     block_sum4(prp, prd, z2, z3, sm.red);
     tm.mark(PH_CTRL);

@@ -66,13 +66,13 @@ __global__ void k_rollout_jac(Dev<Real> D, int slot_sel) {
     for (int c = 0; c < nx; ++c) x[c] = ar[L.x0 + c];
     for (int k = 0; k < I.T; ++k)
       dyn_step(I.kind, ar + L.dyn, I.dt, x + (long long)k * nx, sa + SL.u_hat + (long long)k * nu,
-               x + (long long)(k + 1) * nx, nullptr, nullptr);
+               x + (long long)(k + 1) * nx, nullptr, nullptr, ar + L.xlo, ar + L.xhi);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < I.T; k += blockDim.x) {
     double xn[14];
     dyn_step(I.kind, ar + L.dyn, I.dt, sa + SL.x_hat + (long long)k * nx, sa + SL.u_hat + (long long)k * nu, xn,
-             sa + SL.A + (long long)k * nx * nx, sa + SL.B + (long long)k * nx * nu);
+             sa + SL.A + (long long)k * nx * nx, sa + SL.B + (long long)k * nx * nu, ar + L.xlo, ar + L.xhi);
   }
 }
 
@@ -319,8 +319,9 @@ __global__ void k_gram(Dev<Real> D, int slot_sel) {
 // with a = (2W+shift)^{-1/2}, a G_m a = V diag(γ) Vᵀ:  Pf_m = a V,  Dv_m[u][c] = 1/(1 + coef τ γ_u λ_c).
 // Then H_m vec(K) = vec(R) is solved by K = Pf X U_mᵀ with X = (Pfᵀ R U_m) ⊙ Dv.  Thread per (inst, m).
 template <typename Real>
-__global__ void k_gain_factors(Dev<Real> D, double coef, double shift) {
+__global__ void k_gain_factors(Dev<Real> D, double coef0, double shift, int warm) {
   const int i = blockIdx.x;
+  const double coef = start_rho(D.is, D.sc, i, warm, coef0);
   const Inst I = D.inst[i];
   const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
   const SlotL SL = slot_layout(I.nx, I.nu, I.T);
@@ -605,9 +606,10 @@ __device__ void riccati_factor_staged(const Dev<Real>& D, int i, double rho, dou
 }
 
 template <typename Real>
-__global__ void k_riccati_factor(Dev<Real> D, double rho) {
+__global__ void k_riccati_factor(Dev<Real> D, double rho0, int warm) {
   __shared__ double scr[RIC_SCRATCH_STAGED];
   const int kind = D.inst[blockIdx.x].kind;
+  const double rho = start_rho(D.is, D.sc, blockIdx.x, warm, rho0);
   if (kind == KIND_UNICYCLE) riccati_factor_staged<3, 2, Real>(D, blockIdx.x, rho, scr);
   else if (kind == KIND_QUADCOPTER) riccati_factor_staged<12, 4, Real>(D, blockIdx.x, rho, scr);
   else riccati_factor_staged<14, 7, Real>(D, blockIdx.x, rho, scr);

@@ -102,6 +102,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
+  int issued = 0;   // stages the producer has issued loads for (thread 0)
   if (tid == 0) {
     // producer: bulk tensor loads of the A and B stages
     for (int k = 0; k < nk; ++k) {
@@ -114,6 +115,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
       mbar_arrive_expect_tx(&full[s], STAGE);
       tma_load_2d(sa, &ta, k * 64, m0, &full[s]);
       tma_load_2d(sa + A_BYTES, &tb, k * 64, n0, &full[s]);
+      issued = k + 1;
     }
   } else if (tid == 32) {
     // MMA issuer
@@ -218,6 +220,13 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
   }
   tc_fence_before();
   __syncthreads();
+  // After a wait gave up (any thread), tensor loads the producer issued may still be landing in this
+  // CTA's shared memory: wait (bounded) for the last stages it issued before the CTA exits.
+  if (tid == 0 && s_err) {
+    for (int k = issued > GEMM_STAGES ? issued - GEMM_STAGES : 0; k < issued; ++k)
+      (void)mbar_wait_bounded(&full[k % GEMM_STAGES], (uint32_t)(k / GEMM_STAGES) & 1u);
+  }
+  __syncwarp();
   if (warp == 0) tmem_dealloc(tmem, BN);
   if (tid == 0 && s_err) atomicExch(ep.err, 1);
 }

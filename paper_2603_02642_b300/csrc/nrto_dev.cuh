@@ -27,7 +27,10 @@ enum : int { ROW_SPHERE = 0, ROW_XHI = 1, ROW_XLO = 2, ROW_UHI = 3, ROW_ULO = 4 
 // instance status
 enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NUMERIC = 3, ST_TIMEOUT = 4, ST_STALLED = 5 };
 
-constexpr int MAX_DYN = 24;
+constexpr int MAX_DYN = 40;
+// Arm parameters (dyn_params): DH rows (a, d, α) × 7, damping (7), inertia (7), clamping flag; the host
+// completes a 21-value table (the double integrator) with zero damping, unit inertia and no clamping.
+enum : int { ARM_DH = 0, ARM_DAMP = 21, ARM_INERT = 28, ARM_CLIP = 35, ARM_NPRM = 36 };
 
 // Per-instance metadata (host builds it at create time).
 struct Inst {
@@ -159,6 +162,18 @@ struct Dev {
   const int* order;             // instance order per launch
   unsigned long long* phase_cycles;   // NPHASE counters, or null when phase timing is off
 };
+
+// Inner-state carry: the next FullADMM inner solve of instance i starts from the previous one's final
+// state when it is requested (warm mode 2) and the previous solve ended with a usable state.  The
+// factor kernels launched before the solve and the solve itself take the same decision.
+__device__ __forceinline__ bool carry_applies(const int* is, int i, int warm) {
+  const int st = is[i * NIS + IS_STATUS];
+  return warm == 2 && (st == ST_CONVERGED || st == ST_MAXITER || st == ST_STALLED);
+}
+// Penalty the inner solve of instance i starts with: the carried one, else rho0.
+__device__ __forceinline__ double start_rho(const int* is, const double* sc, int i, int warm, double rho0) {
+  return carry_applies(is, i, warm) ? sc[(long long)i * NSC + SC_RHOD] : rho0;
+}
 
 // Phases of one inner iteration timed by the persistent solvers (thread 0 of each CTA, SM cycles).
 enum : int { PH_INIT = 0, PH_ROWS, PH_CTRL, PH_SCAL1, PH_QR, PH_GAIN, PH_RICCATI, PH_DUALS, PH_WAIT, NPHASE };

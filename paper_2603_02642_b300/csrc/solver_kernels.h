@@ -11,7 +11,7 @@ namespace nrto {
 
 struct SolveParams;
 
-enum : int { SOLVER_KERNEL_FULLADMM = 0, SOLVER_KERNEL_DR = 1 };
+enum : int { SOLVER_KERNEL_FULLADMM = 0, SOLVER_KERNEL_DR = 1, SOLVER_KERNEL_FULLADMM_AW = 2 };
 
 template <int NX, int NU, typename Real>
 struct SolverKernel {

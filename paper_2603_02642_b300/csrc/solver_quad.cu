@@ -1,4 +1,4 @@
-// Persistent FullADMM and NRTO-DR kernels of the quadcopter (n_x, n_u) = (12, 4), in both compute precisions.
+// Persistent FullADMM (lifted and as-written block 2) and NRTO-DR kernels of the quadcopter (n_x, n_u) = (12, 4), in both compute precisions.
 #include "solver_impl.cuh"
 
 namespace nrto {

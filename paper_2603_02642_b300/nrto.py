@@ -14,7 +14,7 @@ LIB_PATH = os.environ.get("NRTO_LIB", os.path.join(HERE, "libnrto.so"))
 
 PREC_FP64, PREC_MIXED = 0, 1
 NSTAT = 14   # NRTO_NSTAT
-SOLVER_DR, SOLVER_FULLADMM = 0, 1
+SOLVER_DR, SOLVER_FULLADMM, SOLVER_FULLADMM_AW = 0, 1, 2
 
 (F_XHAT, F_UHAT, F_A, F_B, F_G0, F_BHAT, F_BVEC, F_LAMNU, F_K, F_DU, F_P, F_PT, F_LAMP, F_GM, F_KACC,
  F_DX, F_SCAL, F_STATS) = range(18)

@@ -67,9 +67,10 @@ def test_dr_iterates_parity_fp64(cases, name, n_admm, n_dr):
     prob.close()
 
 
-@pytest.mark.parametrize("r", [0.05, 5.0])
+@pytest.mark.parametrize("r", [0.05, 50.0])
 def test_dr_trust_region_active_and_inactive(cases, r):
-    """Subproblem 2 with the trust multiplier at work (r small) and without it (r large)."""
+    """Subproblem 2 with the trust multiplier at work (r small) and without it (r large: the
+    unconstrained ‖F_u δû‖ of this case is about 6.4)."""
     lin, res, prob, out = _run(cases["uni_T20_o3"], 2, 4, r=r)
     assert_close(out["du"][0], res.du, RTOL64, "du")
     assert_close(out["p"][0], res.p, RTOL64, "p")

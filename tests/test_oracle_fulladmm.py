@@ -284,7 +284,7 @@ def test_as_written_block2_reaches_the_interior_point_solution():
     inst = tiny_unicycle()
     lin = P.linearize(inst, inst.u_init)
     du_ip, K_ip = problem2_ip(inst, lin, r=0.5)
-    o = F.FullADMMOptions(rho=10.0, r_trust=0.5, eps_p=1e-9, eps_d=1e-9, max_iter=30000)
+    o = F.FullADMMOptions(rho=10.0, r_trust=0.5, eps_p=1e-8, eps_d=1e-8, max_iter=30000)
     aw = F.iterate_as_written(inst, lin, o)
     lifted = F.iterate(inst, lin, o)
     assert aw.converged and lifted.converged

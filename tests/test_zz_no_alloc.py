@@ -63,3 +63,40 @@ def test_noalloc_rejects_batches_beyond_the_static_area():
     assert e.value.code == 1 and "static device area" in str(e.value)
     # The area is still usable after a refused call.
     _assert_same(nrto.solve_noalloc(_batch_a(), OPTS, N_OUTER), _allocating(_batch_a()))
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After a first call (which looks up the static area and, with lazy module loading, loads the
+    kernels it launches), further calls leave the device's free memory unchanged: the call allocates
+    nothing.  The library calls the CUDA runtime directly, so any cudaMalloc would show in the
+    driver's free-memory count (the torch caching allocator is not involved)."""
+    import torch
+    nrto.solve_noalloc(_batch_b(), OPTS, N_OUTER)   # every dynamics kind: all FP64 kernels loaded
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for batch in (_batch_a, _batch_b, _batch_a):
+        nrto.solve_noalloc(batch(), OPTS, N_OUTER)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_serializes_concurrent_callers():
+    """Two host threads calling at once on their own streams: the library's lock serializes the calls
+    on the shared area, so both get the results of the allocating path."""
+    import threading
+    import torch
+    ref_a, ref_b = _allocating(_batch_a()), _allocating(_batch_b())
+    got = {}
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+
+    def run(key, batch, st):
+        got[key] = nrto.solve_noalloc(batch, OPTS, N_OUTER, stream=st.cuda_stream)
+
+    ths = [threading.Thread(target=run, args=("a", _batch_a(), streams[0])),
+           threading.Thread(target=run, args=("b", _batch_b(), streams[1]))]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    _assert_same(got["a"], ref_a)
+    _assert_same(got["b"], ref_b)
