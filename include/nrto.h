@@ -184,9 +184,36 @@ nrto_status nrto_solve_socp(nrto_problem_t p, const nrto_solver_opts* opts, nrto
 nrto_status nrto_outer_step(nrto_problem_t p, const nrto_solver_opts* opts, int* accepted);
 
 /* Full solve: reset to u_init and r = opts->r0, linearize, then n_outer outer steps.  Outputs
- * (host, may be NULL): u_bar Σ T*nu, K Σ T*nu*nx, merit n. */
+ * (host, may be NULL): u_bar Σ T*nu, K Σ T*nu*nx, merit n.
+ * The launch sequence (one persistent solver launch per dynamics kind and outer step, and the
+ * outer-loop kernels) is captured into a CUDA graph on a call and replayed by later calls with the same
+ * options, n_outer and warm-start state, unless graphs are off (nrto_set_graph), solver profiling is
+ * on (nrto_profile) or the problem runs on a default stream (NULL, legacy or per-thread; those cannot
+ * be captured).  The first call with new options captures; make it outside any stream capture. */
 nrto_status nrto_solve(nrto_problem_t p, const nrto_solver_opts* opts, int n_outer,
                        double* u_bar, double* K, double* merit);
+
+/* Enable (default) or disable the CUDA graph of nrto_solve; disabling drops the captured graph. */
+nrto_status nrto_set_graph(nrto_problem_t p, int enable);
+/* Number of captures and of replays of nrto_solve's graph since create. */
+nrto_status nrto_graph_info(nrto_problem_t p, long long* captures, long long* replays);
+
+/* Launch mapping of the persistent inner-loop launches (one per dynamics kind of the batch; each CTA
+ * takes whole instances from the kind's largest-first queue):
+ *   0  the kinds one after another, each with as many CTAs as fit on the GPU;
+ *   1  the kinds at the same time (largest kind first; the next kind's CTAs take the SMs the first
+ *      frees), each with as many CTAs as fit — the default;
+ *   2  the kinds at the same time with the SMs split in proportion to the kinds' row entries;
+ *   3  as 2, in proportion to row entries × horizon.
+ * Results do not depend on the mapping (instances are independent): only the time does. */
+#define NRTO_NMAPPING 4
+nrto_status nrto_set_launch_mapping(nrto_problem_t p, int mapping);
+/* Autotuner of the launch mapping: for each mapping, one warm-up nrto_solve(opts, n_outer) and then
+ * reps timed ones (CUDA events on the problem's stream); keeps the fastest for later launches.  ms_out
+ * (may be NULL, NRTO_NMAPPING values) receives each mapping's milliseconds per solve, chosen the pick.
+ * The solves replace the problem's solver state like nrto_solve does.  Profiling must be off. */
+nrto_status nrto_autotune(nrto_problem_t p, const nrto_solver_opts* opts, int n_outer, int reps, double* ms_out,
+                          int* chosen);
 
 /* Warm start of the next inner solve from a network (the library's learned warm start; the paper
  * names it as future work): runs nrto_mlp_forward on features (host, n × network input) with the

@@ -235,6 +235,15 @@ struct nrto_problem {
   // events.  Not created for nrto_solve_noalloc, whose launches run one after another.
   cudaStream_t stream2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // CUDA graph of nrto_solve's launch sequence: captured on a call, replayed by later calls with the
+  // same options, outer-step count and warm-start state.  Off while profiling (per-launch events)
+  // and for nrto_solve_noalloc (graph instantiation may allocate device memory).
+  bool graph_enabled = true;
+  int mapping = 1;   // launch mapping of the persistent solver launches (launch_solver_kinds)
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned char> graph_key;
+  long long graph_launches = 0, graph_captures = 0, graph_replays = 0;
+  bool graph_carry_after = false;
   bool linearized = false;
   bool warm_pending = false;
   // A FullADMM inner solve ran since the last reset, so its final state can start the next one
@@ -265,6 +274,7 @@ struct nrto_problem {
   }
   ~nrto_problem() {
     for (auto& ev : prof_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (stream2) cudaStreamDestroy(stream2);
@@ -454,7 +464,8 @@ void launch_linearize(nrto_problem* P, int slot_sel) {
 // One persistent launch of a solver kernel (FullADMM or NRTO-DR) for the instances of one kind:
 // as many CTAs as fit on the GPU, at most one per instance; CTAs take instances from the queue.
 template <int NX, int NU, typename Real>
-void launch_solver_kind(nrto_problem* P, int solver, const KindLaunch& kl, SolveParams sp, cudaStream_t st) {
+void launch_solver_kind(nrto_problem* P, int solver, const KindLaunch& kl, SolveParams sp, cudaStream_t st,
+                        int grid_cap) {
   using SK = SolverKernel<NX, NU, Real>;
   const char* name = solver == SOLVER_KERNEL_FULLADMM ? "k_fulladmm" : "k_dr";
   int dev = 0, nsm = 0, per_sm = 0;
@@ -462,7 +473,8 @@ void launch_solver_kind(nrto_problem* P, int solver, const KindLaunch& kl, Solve
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   CK(SK::configure(solver, kl.smem, &per_sm));
   if (per_sm < 1) fail(NRTO_ERR_CUDA, std::string(name) + " does not fit on an SM");
-  const int grid = std::min(kl.count, nsm * per_sm);
+  int grid = std::min(kl.count, nsm * per_sm);
+  if (grid_cap > 0) grid = std::min(grid, grid_cap);
   sp.chunk = kl.chunk; sp.max_rows = kl.max_rows; sp.tmax = kl.tmax; sp.n_order = kl.count;
   sp.order0 = kl.order0; sp.queue_idx = kl.kind;
   const cudaError_t le = SK::launch(solver, grid, kl.smem, st, P->dev<Real>(), sp);
@@ -484,13 +496,30 @@ void launch_solver_kinds(nrto_problem* P, int solver, const SolveParams& sp) {
   }
   int kinds[3] = {0, 1, 2};
   std::stable_sort(kinds, kinds + 3, [&](int a, int b) { return P->kl[a].entries > P->kl[b].entries; });
+  // launch mapping (nrto_set_launch_mapping / nrto_autotune): 0 kinds one after another on the problem's
+  // stream; 1 kinds at the same time, each with as many CTAs as fit; 2 and 3 at the same time with the
+  // SMs split between the kinds in proportion to their row entries (2) or row entries × horizon (3)
+  int caps[3] = {0, 0, 0};
+  if (P->mapping >= 2) {
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    double wsum = 0.0, wk[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k)
+      if (P->kl[k].count > 0) {
+        wk[k] = (double)P->kl[k].entries * (P->mapping == 3 ? (double)P->kl[k].tmax : 1.0);
+        wsum += wk[k];
+      }
+    for (int k = 0; k < 3; ++k)
+      if (P->kl[k].count > 0) caps[k] = std::max(1, (int)(nsm * wk[k] / wsum));
+  }
   int launched = 0;
   bool forked = false;
   for (int k : kinds) {
     const KindLaunch& kl = P->kl[k];
     if (kl.count == 0) continue;
     cudaStream_t st = P->stream;
-    if (launched > 0 && P->stream2) {
+    if (launched > 0 && P->stream2 && P->mapping != 0) {
       if (!forked) {
         CK(cudaEventRecord(P->ev_fork, P->stream));
         CK(cudaStreamWaitEvent(P->stream2, P->ev_fork, 0));
@@ -498,9 +527,9 @@ void launch_solver_kinds(nrto_problem* P, int solver, const SolveParams& sp) {
       }
       st = P->stream2;
     }
-    if (k == KIND_UNICYCLE) launch_solver_kind<3, 2, Real>(P, solver, kl, sp, st);
-    else if (k == KIND_QUADCOPTER) launch_solver_kind<12, 4, Real>(P, solver, kl, sp, st);
-    else launch_solver_kind<14, 7, Real>(P, solver, kl, sp, st);
+    if (k == KIND_UNICYCLE) launch_solver_kind<3, 2, Real>(P, solver, kl, sp, st, caps[k]);
+    else if (k == KIND_QUADCOPTER) launch_solver_kind<12, 4, Real>(P, solver, kl, sp, st, caps[k]);
+    else launch_solver_kind<14, 7, Real>(P, solver, kl, sp, st, caps[k]);
     ++launched;
   }
   if (forked) {
@@ -1281,21 +1310,66 @@ nrto_status nrto_solve(nrto_problem_t p, const nrto_solver_opts* o, int n_outer,
     check_opts(o);
     if (n_outer < 0) fail(NRTO_ERR_INVALID, "n_outer < 0");
     const bool f64 = p->prec == NRTO_PREC_FP64;
-    if (f64) k_reset_outer<double><<<p->n, 128, 0, p->stream>>>(p->dev<double>(), o->r0);
-    else k_reset_outer<float><<<p->n, 128, 0, p->stream>>>(p->dev<float>(), o->r0);
-    p->check_launch("k_reset_outer");
-    p->carry_ok = false;
-    k_scatter_uhat<<<p->n, 128, 0, p->stream>>>(p->d_slot_arena[0], p->d_inst, p->d_ustage, p->d_uoff, p->n);
-    p->check_launch("k_scatter_uhat");
-    if (f64) { launch_linearize<double>(p, -1); launch_merit_current<double>(p, o->w_p); }
-    else { launch_linearize<float>(p, -1); launch_merit_current<float>(p, o->w_p); }
-    p->linearized = true;
-    nrto_solver_opts last = *o;
-    if (o->max_inner_final > 0) last.max_inner = o->max_inner_final;
-    for (int it = 0; it < n_outer; ++it) {
-      const nrto_solver_opts& oi = (it == n_outer - 1) ? last : *o;
-      if (f64) launch_outer_step<double>(p, oi); else launch_outer_step<float>(p, oi);
+    auto enqueue = [&]() {
+      if (f64) k_reset_outer<double><<<p->n, 128, 0, p->stream>>>(p->dev<double>(), o->r0);
+      else k_reset_outer<float><<<p->n, 128, 0, p->stream>>>(p->dev<float>(), o->r0);
+      p->check_launch("k_reset_outer");
+      p->carry_ok = false;
+      k_scatter_uhat<<<p->n, 128, 0, p->stream>>>(p->d_slot_arena[0], p->d_inst, p->d_ustage, p->d_uoff, p->n);
+      p->check_launch("k_scatter_uhat");
+      if (f64) { launch_linearize<double>(p, -1); launch_merit_current<double>(p, o->w_p); }
+      else { launch_linearize<float>(p, -1); launch_merit_current<float>(p, o->w_p); }
+      nrto_solver_opts last = *o;
+      if (o->max_inner_final > 0) last.max_inner = o->max_inner_final;
+      for (int it = 0; it < n_outer; ++it) {
+        const nrto_solver_opts& oi = (it == n_outer - 1) ? last : *o;
+        if (f64) launch_outer_step<double>(p, oi); else launch_outer_step<float>(p, oi);
+      }
+    };
+    // the legacy and per-thread default streams cannot be captured: those callers launch directly
+    const bool capturable = p->stream != nullptr && p->stream != cudaStreamLegacy && p->stream != cudaStreamPerThread;
+    if (p->graph_enabled && capturable && !p->profiling && !p->carve_base) {
+      // key: the options, the outer-step count and whether a learned warm start is pending
+      std::vector<unsigned char> key(sizeof(nrto_solver_opts) + sizeof(int) + 2);
+      std::memcpy(key.data(), o, sizeof(nrto_solver_opts));
+      std::memcpy(key.data() + sizeof(nrto_solver_opts), &n_outer, sizeof(int));
+      key[key.size() - 2] = (unsigned char)p->mapping;
+      key.back() = p->warm_pending ? 1 : 0;
+      if (!p->graph_exec || key != p->graph_key) {
+        if (p->graph_exec) { cudaGraphExecDestroy(p->graph_exec); p->graph_exec = nullptr; }
+        const long long l0 = p->launches;
+        const bool warm0 = p->warm_pending;
+        CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeRelaxed));
+        cudaGraph_t g = nullptr;
+        try {
+          enqueue();
+        } catch (...) {
+          cudaStreamEndCapture(p->stream, &g);
+          if (g) cudaGraphDestroy(g);
+          cudaGetLastError();
+          p->launches = l0;
+          p->warm_pending = warm0;
+          throw;
+        }
+        CK(cudaStreamEndCapture(p->stream, &g));
+        const cudaError_t ie = cudaGraphInstantiate(&p->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) { p->graph_exec = nullptr; fail(NRTO_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie)); }
+        p->graph_launches = p->launches - l0;
+        p->launches = l0;
+        p->graph_key = key;
+        p->graph_carry_after = p->carry_ok;
+        ++p->graph_captures;
+      }
+      CK(cudaGraphLaunch(p->graph_exec, p->stream));
+      p->launches += p->graph_launches;
+      ++p->graph_replays;
+      p->carry_ok = p->graph_carry_after;
+      p->warm_pending = false;
+    } else {
+      enqueue();
     }
+    p->linearized = true;
     if (u_bar) copy_arena_field(p, GF_UHAT, u_bar);
     if (K) copy_arena_field(p, GF_KACC, K);
     if (merit) {
@@ -1398,6 +1472,79 @@ nrto_status nrto_export(nrto_problem_t p, int field, int i, double* dst, long lo
 
 nrto_status nrto_import(nrto_problem_t p, int field, int i, const double* src, long long count) {
   return exchange(p, field, i, const_cast<double*>(src), count, false);
+}
+
+nrto_status nrto_set_graph(nrto_problem_t p, int enable) {
+  try {
+    if (!p) fail(NRTO_ERR_INVALID, "null problem");
+    p->graph_enabled = enable != 0;
+    if (!p->graph_enabled && p->graph_exec) {
+      CK(cudaStreamSynchronize(p->stream));
+      cudaGraphExecDestroy(p->graph_exec);
+      p->graph_exec = nullptr;
+    }
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_set_launch_mapping(nrto_problem_t p, int mapping) {
+  try {
+    if (!p) fail(NRTO_ERR_INVALID, "null problem");
+    if (mapping < 0 || mapping >= NRTO_NMAPPING) fail(NRTO_ERR_INVALID, "unknown launch mapping");
+    p->mapping = mapping;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_autotune(nrto_problem_t p, const nrto_solver_opts* o, int n_outer, int reps, double* ms_out,
+                          int* chosen) {
+  try {
+    if (!p) fail(NRTO_ERR_INVALID, "null problem");
+    check_opts(o);
+    if (n_outer < 1 || reps < 1) fail(NRTO_ERR_INVALID, "n_outer and reps must be >= 1");
+    const bool prof = p->profiling;
+    if (prof) fail(NRTO_ERR_STATE, "disable solver profiling before nrto_autotune");
+    double best = 0.0;
+    int best_m = p->mapping;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int m = 0; m < NRTO_NMAPPING; ++m) {
+      p->mapping = m;
+      nrto_status st = nrto_solve(p, o, n_outer, nullptr, nullptr, nullptr);   // warm-up (and capture)
+      if (st != NRTO_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+      CK(cudaEventRecord(e0, p->stream));
+      for (int r = 0; r < reps; ++r) {
+        st = nrto_solve(p, o, n_outer, nullptr, nullptr, nullptr);
+        if (st != NRTO_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+      }
+      CK(cudaEventRecord(e1, p->stream));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      const double ms = t / reps;
+      if (ms_out) ms_out[m] = ms;
+      if (m == 0 || ms < best) { best = ms; best_m = m; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->mapping = best_m;
+    if (chosen) *chosen = best_m;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_graph_info(nrto_problem_t p, long long* captures, long long* replays) {
+  if (!p) { g_last_error = "null problem"; return NRTO_ERR_INVALID; }
+  if (captures) *captures = p->graph_captures;
+  if (replays) *replays = p->graph_replays;
+  return NRTO_OK;
 }
 
 nrto_status nrto_profile(nrto_problem_t p, int enable, double* solver_ms, long long* solver_launches) {

@@ -14,6 +14,7 @@ LIB_PATH = os.environ.get("NRTO_LIB", os.path.join(HERE, "libnrto.so"))
 
 PREC_FP64, PREC_MIXED = 0, 1
 NSTAT = 14   # NRTO_NSTAT
+NMAPPING = 4  # NRTO_NMAPPING
 SOLVER_DR, SOLVER_FULLADMM, SOLVER_FULLADMM_AW = 0, 1, 2
 
 (F_XHAT, F_UHAT, F_A, F_B, F_G0, F_BHAT, F_BVEC, F_LAMNU, F_K, F_DU, F_P, F_PT, F_LAMP, F_GM, F_KACC,
@@ -106,6 +107,14 @@ def load():
     lib.nrto_mlp_profile.restype = C.c_int
     lib.nrto_mlp_kernel_launches.argtypes = [P]
     lib.nrto_mlp_kernel_launches.restype = C.c_longlong
+    lib.nrto_set_launch_mapping.argtypes = [P, C.c_int]
+    lib.nrto_set_launch_mapping.restype = C.c_int
+    lib.nrto_autotune.argtypes = [P, C.POINTER(SolverOpts), C.c_int, C.c_int, _dp, _ip]
+    lib.nrto_autotune.restype = C.c_int
+    lib.nrto_set_graph.argtypes = [P, C.c_int]
+    lib.nrto_set_graph.restype = C.c_int
+    lib.nrto_graph_info.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    lib.nrto_graph_info.restype = C.c_int
     lib.nrto_get_stats.argtypes = [P, _dp, C.c_int]
     lib.nrto_get_stats.restype = C.c_int
     lib.nrto_kernel_launches.argtypes = [P]
@@ -340,6 +349,26 @@ class Problem:
 
     def kernel_launches(self):
         return int(load().nrto_kernel_launches(self._h))
+
+    def set_graph(self, enable=True):
+        """Capture / replay nrto_solve's launch sequence as a CUDA graph (default on)."""
+        _check(load().nrto_set_graph(self._h, int(enable)))
+
+    def set_launch_mapping(self, mapping):
+        _check(load().nrto_set_launch_mapping(self._h, int(mapping)))
+
+    def autotune(self, opts: Options, n_outer=1, reps=1):
+        """Time every launch mapping on this batch and keep the fastest: (chosen, ms per mapping)."""
+        ms = np.zeros(NMAPPING)
+        ch = C.c_int(-1)
+        _check(load().nrto_autotune(self._h, C.byref(opts.c()), int(n_outer), int(reps), _ptr(ms), C.byref(ch)))
+        return ch.value, ms
+
+    def graph_info(self):
+        """(captures, replays) of nrto_solve's CUDA graph."""
+        c, r = C.c_longlong(0), C.c_longlong(0)
+        _check(load().nrto_graph_info(self._h, C.byref(c), C.byref(r)))
+        return c.value, r.value
 
     STATS = ["cum_iters", "iters", "status", "n_accepted", "rho", "dr_iters", "fallback", "accepted_status",
              "merit", "cost", "max_violation", "trust_radius", "r_p", "r_d"]
