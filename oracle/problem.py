@@ -40,9 +40,21 @@ class Linearization:
 
 
 def psi_blocks(Sigma):
-    """Ψ_i = L_iᵀ with L_i L_iᵀ = Σ_i (Cholesky), so ΨᵀΨ = blkdiag(Σ_i) = S^{-1}
-    (Supplementary Sec. I: 'there exists Ψ ≻ 0 such that ΨᵀΨ = S^{-1}')."""
-    return np.stack([np.linalg.cholesky(S).T for S in Sigma])
+    """Ψ_i with Ψ_iᵀΨ_i = Σ_i, so ΨᵀΨ = blkdiag(Σ_i) (Supplementary Sec. I: Ψ with ΨᵀΨ = S^{-1},
+    for Γ = I).  Σ_i ≻ 0: Ψ_i = L_iᵀ with L_i L_iᵀ = Σ_i (Cholesky).  With a general block-diagonal
+    Γ = blkdiag(Γ_i) (the disturbance of step i enters through Γ_i: ζ_i = Γ_i z_i, zᵀSz ≤ τ), the
+    robust term is ‖Ψ Γᵀ c‖ with (ΨΓᵀ)ᵀ(ΨΓᵀ) = Γ S^{-1} Γᵀ = blkdiag(Γ_i S_i^{-1} Γ_iᵀ), so the same
+    construction applies to Σ_i = Γ_i S_i^{-1} Γ_iᵀ, which is only positive semidefinite when Γ_i has
+    fewer columns than rows; then Ψ_i = Λ_i^{1/2} V_iᵀ from Σ_i = V_i Λ_i V_iᵀ (negative rounding
+    residue of zero eigenvalues taken as zero)."""
+    out = []
+    for S in Sigma:
+        try:
+            out.append(np.linalg.cholesky(S).T)
+        except np.linalg.LinAlgError:
+            lam, V = np.linalg.eigh(S)
+            out.append(np.sqrt(np.maximum(lam, 0.0))[:, None] * V.T)
+    return np.stack(out)
 
 
 def transition(A, t, m):

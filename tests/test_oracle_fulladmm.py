@@ -316,3 +316,16 @@ def test_as_written_block2_is_the_dr_subproblem_2_minimizer():
     f = torch.sum(ub * ub * t(inst.Ru)) + torch.sum(xb * xb * t(inst.Qx)) + 0.5 * 7.0 * torch.sum(torch.clamp(z, min=0) ** 2)
     g, = torch.autograd.grad(f, [du_t])
     assert g.abs().max().item() < 1e-9
+
+
+def test_fixed_point_with_singular_sigma_matches_interior_point():
+    """Disturbance through a per-step input map Γ_i that misses the heading (Σ_i = Γ_i S_i^{-1} Γ_iᵀ of
+    rank 2): the FullADMM fixed point is still the interior-point solution of Problem 2."""
+    inst = tiny_unicycle()
+    inst.Sigma = np.stack([np.diag([0.02 ** 2, 0.02 ** 2, 0.0])] * (inst.T + 1))
+    lin = P.linearize(inst, inst.u_init)
+    du_ip, K_ip = problem2_ip(inst, lin, r=0.5)
+    s = F.iterate(inst, lin, F.FullADMMOptions(rho=10.0, r_trust=0.5, eps_p=1e-9, eps_d=1e-9, max_iter=30000))
+    assert s.converged
+    assert np.allclose(s.du, du_ip, atol=2e-6) and np.allclose(s.K, K_ip, atol=2e-6)
+    assert np.abs(s.K[:, :, 2]).max() < 1e-12        # no disturbance on θ: its feedback column is zero

@@ -157,3 +157,40 @@ def test_row_support_is_blocks_zero_to_t():
         assert np.all(lin.bhat[j, t + 1:] == 0) and np.all(lin.bvec[j, t:] == 0)
     for j in range(n_state, lin.g0.shape[0]):
         assert np.all(lin.bhat[j] == 0) and np.count_nonzero(lin.bvec[j]) == 1
+
+
+def test_general_gamma_robust_term_with_singular_sigma():
+    """General block-diagonal Γ: the disturbance of each step enters through Γ_i (n_x × n_w, here the
+    quadcopter's three velocity states only), z_i ∈ {zᵀS_i z ≤ τ}.  With Σ_i = Γ_i S_i^{-1} Γ_iᵀ of rank
+    3, the SOC row ‖Â_j k_v + b̂_j‖ still equals max over the ellipsoid of ∇gᵀ(F_ζ + F_u K̄) Γ z:
+    attained at the analytic maximizer and never exceeded on sampled boundary points of the z-ellipsoid."""
+    inst = W.quadcopter(3, T=5, n_obs=2)
+    T, nx, nu = inst.T, inst.nx, inst.nu
+    G = np.zeros((nx, 3))
+    G[3:6, :] = np.eye(3)
+    Sw = np.diag([1.0 / 4e-4, 1.0 / 1e-4, 1.0 / 9e-4])
+    inst.Sigma = np.stack([G @ np.linalg.inv(Sw) @ G.T for _ in range(T + 1)])
+    u = inst.u_init + 0.05 * RNG.normal(size=inst.u_init.shape)
+    lin = P.linearize(inst, u)
+    Psi = lin.Psi
+    assert np.allclose(np.einsum("ikr,ikc->irc", Psi, Psi), inst.Sigma, atol=1e-14)
+    K = 0.3 * RNG.normal(size=(T, nu, nx))
+    Kbar = np.zeros((T * nu, (T + 1) * nx))
+    for k in range(T):
+        Kbar[k * nu:(k + 1) * nu, k * nx:(k + 1) * nx] = K[k]
+    Gbig = np.kron(np.eye(T + 1), G)                       # ζ = Γ z
+    Swi = np.kron(np.eye(T + 1), np.linalg.inv(Sw))        # S^{-1} of z
+    Y = P.Ahat_apply(lin, K) + lin.bhat
+    st = models.state_rows(inst)
+    for j in range(len(st)):
+        t = st[j][0]
+        a = np.zeros((T + 1) * nx)
+        a[t * nx:(t + 1) * nx] = models.g_state_grad(inst, st[j], lin.x_hat[t])
+        c = Gbig.T @ (lin.Fz + lin.Fu @ Kbar).T @ a        # ∇gᵀ(F_ζ + F_u K̄) Γ
+        val = np.linalg.norm(Y[j])
+        zstar = inst.tau * Swi @ c / np.sqrt(inst.tau * c @ Swi @ c)
+        assert np.isclose(c @ zstar, val, rtol=1e-10)
+        w = RNG.normal(size=(500, c.shape[0]))
+        w /= np.linalg.norm(w, axis=1, keepdims=True)
+        zs = np.sqrt(inst.tau) * w @ np.linalg.cholesky(Swi).T
+        assert np.all(zs @ c <= val * (1 + 1e-12))
