@@ -71,7 +71,10 @@ typedef struct {
   const double* x_goal;          /* nx    goal of the state-tracking cost                       */
   const double* u_init;          /* T*nu  initial nominal controls û                            */
   const double* u_ref;           /* nu    reference of the input cost                           */
-  const double* Sigma;           /* (T+1)*nx*nx  blocks Σ_i = S_i^{-1} (Γ = I, S block diagonal) */
+  const double* Sigma;           /* (T+1)*nx*nx  blocks Σ_i = Γ_i S_i^{-1} Γ_iᵀ of the disturbance set
+                                    {ζ = Γz, zᵀSz ≤ τ} with Γ and S block diagonal per step (Γ = I:
+                                    Σ_i = S_i^{-1}); symmetric positive semidefinite (a Γ_i with fewer
+                                    columns than rows gives a singular block)                       */
   double tau;                    /* ellipsoid radius τ >= 0                                     */
   const double* Qx;              /* nx    diagonal state-tracking weight                        */
   const double* Ru;              /* nu    diagonal input weight R_u (> 0)                       */
@@ -153,7 +156,8 @@ typedef struct nrto_mlp* nrto_mlp_t;   /* the warm-start network (nrto_mlp_*) */
 
 /* Create a batch of n_instances problems (descs[0..n-1]) in the given precision on `cuda_stream`
  * (a cudaStream_t, or NULL for the default stream).  Copies all inputs to the device, allocates all
- * device memory of the batch, validates every descriptor (dims, finiteness, Σ_i SPD, τ >= 0).
+ * device memory of the batch, validates every descriptor (dims, finiteness, Σ_i symmetric positive
+ * semidefinite, τ >= 0).
  * The nominal of each instance is its u_init; the trust radius is 2.0 until set by nrto_solve or
  * nrto_set_trust_radius. */
 nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n_instances, int precision,

@@ -385,7 +385,15 @@ void validate(const nrto_problem_desc& d, int idx) {
     for (int r = 0; r < d.nx; ++r)
       for (int c = 0; c < r; ++c)
         if (std::fabs(C[r * d.nx + c] - C[c * d.nx + r]) > 1e-12 * (std::fabs(C[r * d.nx + c]) + 1e-300)) bad("Sigma block not symmetric");
-    if (!chol_inplace(C.data(), d.nx)) bad("Sigma block not positive definite");
+    if (!chol_inplace(C.data(), d.nx)) {
+      // a singular block (a per-step disturbance map Γ_i of lower rank): positive semidefinite is enough
+      std::vector<double> A(d.nx * d.nx), V(d.nx * d.nx), lam(d.nx);
+      for (int k = 0; k < d.nx * d.nx; ++k) A[k] = d.Sigma[(long long)m * d.nx * d.nx + k];
+      jacobi_eig(A.data(), d.nx, lam.data(), V.data());
+      double lmax = 0.0, lmin = 0.0;
+      for (int k = 0; k < d.nx; ++k) { lmax = std::max(lmax, std::fabs(lam[k])); lmin = std::min(lmin, lam[k]); }
+      if (lmin < -1e-12 * std::max(lmax, 1e-300)) bad("Sigma block not positive semidefinite");
+    }
   }
 }
 

@@ -32,11 +32,17 @@ __global__ void k_setup(Dev<Real> D) {
   for (int m = threadIdx.x; m <= I.T; m += blockDim.x) {
     double S[196], V[196], lam[14], C[196];
     for (int k = 0; k < nx * nx; ++k) { S[k] = ar[L.Sigma + (long long)m * nx * nx + k]; C[k] = S[k]; }
-    chol_inplace(C, nx);
+    const bool pd = chol_inplace(C, nx);
     double* Psi = ar + L.Psi + (long long)m * nx * nx;
-    for (int r = 0; r < nx; ++r)
-      for (int c = 0; c < nx; ++c) Psi[r * nx + c] = C[c * nx + r];   // Ψ = Lᵀ (upper triangular)
+    if (pd)
+      for (int r = 0; r < nx; ++r)
+        for (int c = 0; c < nx; ++c) Psi[r * nx + c] = C[c * nx + r];   // Ψ = Lᵀ (upper triangular)
     jacobi_eig(S, nx, lam, V);
+    if (!pd) {
+      // Σ_i = Γ_i S_i⁻¹ Γ_iᵀ of a general block-diagonal Γ, positive semidefinite: Ψ = Λ^{1/2} Vᵀ
+      for (int r = 0; r < nx; ++r)
+        for (int c = 0; c < nx; ++c) Psi[r * nx + c] = sqrt(fmax(lam[r], 0.0)) * V[c * nx + r];
+    }
     double* U = ar + L.SigU + (long long)m * nx * nx;
     for (int k = 0; k < nx * nx; ++k) U[k] = V[k];
     for (int k = 0; k < nx; ++k) ar[L.SigL + (long long)m * nx + k] = lam[k];

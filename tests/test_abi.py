@@ -52,10 +52,10 @@ def test_invalid_descriptors_rejected_on_host():
         nrto.Problem([inst])
     assert e.value.code == 4
     inst = W.quadcopter(0, T=5, n_obs=1)
-    inst.Sigma[3] = -inst.Sigma[3]            # covariance block not positive definite
+    inst.Sigma[3] = -inst.Sigma[3]            # covariance block not positive semidefinite
     with pytest.raises(nrto.NrtoError) as e:
         nrto.Problem([inst])
-    assert e.value.code == 1 and b"positive definite" in nrto.load().nrto_last_error()
+    assert e.value.code == 1 and b"positive semidefinite" in nrto.load().nrto_last_error()
     inst = W.unicycle(0, T=300)               # horizon beyond the model's limit
     with pytest.raises(nrto.NrtoError):
         nrto.Problem([inst])
@@ -66,4 +66,16 @@ def test_create_without_device_reports_cuda_error():
     build.build()
     with pytest.raises(nrto.NrtoError) as e:
         nrto.Problem([W.unicycle(0, T=5)])
+    assert e.value.code == 2
+
+
+@pytest.mark.skipif(_has_gpu(), reason="checks validation on the host before the device is used")
+def test_singular_sigma_blocks_pass_validation():
+    """A disturbance map Γ_i of lower rank gives Σ_i = Γ_i S_i^{-1} Γ_iᵀ singular: validation accepts it
+    (creation then stops at the missing device, not at the descriptor check)."""
+    build.build()
+    inst = W.unicycle(0, T=5)
+    inst.Sigma[:, 2, 2] = 0.0
+    with pytest.raises(nrto.NrtoError) as e:
+        nrto.Problem([inst])
     assert e.value.code == 2
