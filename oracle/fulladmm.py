@@ -54,6 +54,10 @@ class FullADMMOptions:
     # linearization.  0 disables it.
     stall_every: int = 0
     stall_ratio: float = 0.9
+    # k_v update by matrix-free Jacobi-preconditioned CG (problem.gain_solve_pcg) from the previous
+    # gains, with this iteration cap and relative tolerance; 0 iterations: the exact per-step solve.
+    kv_pcg_iters: int = 0
+    kv_pcg_tol: float = 0.05
 
 
 @dataclass
@@ -79,6 +83,7 @@ class FullADMMState:
     stalled: bool = False
     rho: float = np.nan
     history: list = field(default_factory=list)
+    pcg_iters: int = 0            # PCG iterations summed over the solve (kv_pcg_iters > 0)
 
 
 def zero_state(lin) -> FullADMMState:
@@ -165,8 +170,13 @@ def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None
         l_prev = P.ell(lin, s.du)
         w = np.maximum(0.0, -(lin.g0 + l_prev + s.p + s.lam_w))
         e = soc.project_ball((s.dx[1:] + s.lam_e).reshape(-1), opts.r_trust).reshape(s.e.shape)
-        # Block 2b (14b), direct form: k = M ρ Σ_j Â_jᵀ(ν_j - b̂_j - λ_ν,j).
-        K_new = P.gain_solve(H, rho * P.Ahat_T_apply(lin, nu - lin.bhat - s.lam_nu))
+        # Block 2b (14b), direct form: k = M ρ Σ_j Â_jᵀ(ν_j - b̂_j - λ_ν,j), exactly or by PCG.
+        rhs = rho * P.Ahat_T_apply(lin, nu - lin.bhat - s.lam_nu)
+        n_cg = 0
+        if opts.kv_pcg_iters > 0:
+            K_new, n_cg = P.gain_solve_pcg(lin, inst, rho, rhs, s.K, opts.kv_pcg_tol, opts.kv_pcg_iters)
+        else:
+            K_new = P.gain_solve(H, rhs)
         # Block 2a (14a): (δû, p).
         du, dx, p = block2_solve(inst, lin, rho, mats, pt_new, s.lam_p, w, s.lam_w, e, s.lam_e)
         l_new = P.ell(lin, du)
@@ -188,7 +198,8 @@ def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None
         s = FullADMMState(K=K_new, du=du, dx=dx, p=p, pt=pt_new, lam_p=lam_p, lam_nu=lam_nu,
                           w=w, lam_w=lam_w, e=e, lam_e=lam_e, nu=nu, iters=s.iters + 1,
                           r_p=float(r_p), r_d=float(r_d), r_p_paper=r_p_paper, r_d_paper=r_d_paper,
-                          rho=rho, history=s.history + [(float(r_p), float(r_d))])
+                          rho=rho, history=s.history + [(float(r_p), float(r_d))],
+                          pcg_iters=s.pcg_iters + n_cg)
         Y_prev = Y_new
         if opts.check and r_p <= opts.eps_p and r_d <= opts.eps_d:
             s.converged = True

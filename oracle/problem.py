@@ -182,6 +182,48 @@ def gain_hessian_blocks(lin, inst, coef, shift=0.0):
     return H
 
 
+def gain_solve_pcg(lin, inst, coef, R, X0, tol, max_iter):
+    """Matrix-free preconditioned conjugate gradients for (Q_v + coef·Σ_j Â_jᵀÂ_j) k = r, the k_v
+    system of the FullADMM gain update solved iteratively as in Sec. IV ("GPU Implementation": the
+    k_v update by PCG; Supplementary Tables VI-VIII: iteration cap and tolerance).  The operator is
+    applied per step without forming it, (H X)_m = 2 R_KᵀR_K X_m + coef τ G_m X_m Σ_m with
+    G_m = Σ_j b_{j,m} b_{j,m}ᵀ; the preconditioner is its diagonal (Jacobi),
+    2 (R_K)_u² + coef τ (G_m)_uu (Σ_m)_cc.  Starts from X0 and stops before an iteration when
+    ‖r - H x‖ ≤ tol ‖r‖, or after max_iter iterations.  Returns (X, iterations)."""
+    T, nu = lin.bvec.shape[1], lin.bvec.shape[2]
+    nx = lin.Psi.shape[1]
+    W = inst.RK ** 2
+    G = np.einsum("jmu,jmv->muv", lin.bvec, lin.bvec)
+    Sig = np.einsum("mka,mkb->mab", lin.Psi[:T], lin.Psi[:T])
+    ct = coef * inst.tau
+
+    def apply(X):
+        return 2.0 * W[None, :, None] * X + ct * np.einsum("muv,mvr,mrc->muc", G, X, Sig)
+
+    dinv = 1.0 / (2.0 * W[None, :, None] + ct * np.einsum("muu->mu", G)[:, :, None]
+                  * np.einsum("mcc->mc", Sig)[:, None, :])
+    x = np.array(X0, dtype=np.float64)
+    r = R - apply(x)
+    z = dinv * r
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    rn0 = float(np.sqrt(np.sum(R * R)))
+    it = 0
+    while it < max_iter:
+        if np.sqrt(np.sum(r * r)) <= tol * rn0:
+            break
+        Ap = apply(p)
+        alpha = rz / float(np.sum(p * Ap))
+        x = x + alpha * p
+        r = r - alpha * Ap
+        z = dinv * r
+        rz_new = float(np.sum(r * z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+    return x, it
+
+
 def gain_solve(H, R):
     """Solve blkdiag(H_m) k = r for gain-shaped R (T, nu, nx); returns (T, nu, nx)."""
     T, nu, nx = R.shape

@@ -329,3 +329,40 @@ def test_fixed_point_with_singular_sigma_matches_interior_point():
     assert s.converged
     assert np.allclose(s.du, du_ip, atol=2e-6) and np.allclose(s.K, K_ip, atol=2e-6)
     assert np.abs(s.K[:, :, 2]).max() < 1e-12        # no disturbance on θ: its feedback column is zero
+
+
+def test_pcg_gain_solve_matches_the_exact_solve_and_meets_its_tolerance():
+    """The PCG k_v update converges to the exact per-step (Kronecker) solve, and at a loose
+    tolerance returns an x whose residual meets it; the operator it applies without forming is the
+    assembled Q_v + ρ Σ_j Â_jᵀÂ_j (checked against the dense Â_j)."""
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    rho = 7.0
+    T, nu, nx = inst.T, inst.nu, inst.nx
+    R = RNG.normal(size=(T, nu, nx))
+    H = P.gain_hessian_blocks(lin, inst, coef=rho)
+    exact = P.gain_solve(H, R)
+    x, it = P.gain_solve_pcg(lin, inst, rho, R, np.zeros_like(R), 1e-13, 500)
+    assert np.allclose(x, exact, atol=1e-11 * np.abs(exact).max())
+    assert it <= T * nu * nx
+    # dense operator check: Q_v + ρ Σ Â_jᵀÂ_j applied to a random gain vs the exact solve's inverse
+    Ad = [P.dense_Ahat(lin, j) for j in range(lin.g0.shape[0])]
+    Hd = 2 * np.kron(np.eye(T * nx), np.diag(inst.RK ** 2)) + rho * sum(a.T @ a for a in Ad)
+    kv = np.linalg.solve(Hd, P.kv_from_K(R))
+    assert np.allclose(P.K_from_kv(kv, T, nu, nx), exact, atol=1e-10 * np.abs(exact).max())
+    x2, it2 = P.gain_solve_pcg(lin, inst, rho, R, np.zeros_like(R), 0.05, 500)
+    res = np.linalg.norm(P.kv_from_K(R) - Hd @ P.kv_from_K(x2))
+    assert res <= 0.05 * np.linalg.norm(R) and 0 < it2 < it
+    # warm start at the solution: nothing to do
+    _, it3 = P.gain_solve_pcg(lin, inst, rho, R, exact, 1e-8, 500)
+    assert it3 == 0
+
+
+def test_fulladmm_with_tight_pcg_equals_the_exact_gain_update():
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    a = F.iterate(inst, lin, F.FullADMMOptions(rho=10.0, r_trust=0.5, check=False), n_iter=30)
+    b = F.iterate(inst, lin, F.FullADMMOptions(rho=10.0, r_trust=0.5, check=False, kv_pcg_iters=500,
+                                               kv_pcg_tol=1e-13), n_iter=30)
+    assert np.allclose(a.K, b.K, atol=1e-10 * np.abs(a.K).max()) and np.allclose(a.du, b.du, atol=1e-10)
+    assert b.pcg_iters > 0
