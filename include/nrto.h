@@ -128,6 +128,14 @@ typedef struct {
    * iterations per outer step, Supplementary Tables VI-VIII) while the subproblem of the returned step
    * is solved to the tolerances. */
   int max_inner_final;
+  /* FullADMM (NRTO_SOLVER_FULLADMM) k_v update by matrix-free Jacobi-preconditioned conjugate
+   * gradients (Sec. IV, GPU implementation: the k_v update by PCG) instead of the exact per-step
+   * Kronecker solve: the system (Q_v + ρ Σ_j Â_jᵀÂ_j) k = r is applied step by step without being
+   * formed, the preconditioner is its diagonal, each update starts from the previous gains and stops
+   * when ‖r - H k‖ ≤ kv_pcg_tol ‖r‖ or after kv_pcg_iters iterations.  0 iterations: the exact solve.
+   * Other solver kinds reject kv_pcg_iters > 0. */
+  int kv_pcg_iters;
+  double kv_pcg_tol;
 } nrto_solver_opts;
 
 /* Per-instance sizes, for sizing output buffers. */
@@ -244,8 +252,9 @@ nrto_status nrto_set_warm_start(nrto_problem_t p, const double* K, const double*
  *    Problem 2 at δû = 0, linearized at the accepted nominal x̄ (≤ 0: every robust constraint holds
  *    for all disturbances of the ellipsoid, to first order about x̄; -INFINITY without rows)
  * 11 trust radius                                         12, 13 full r_p, r_d of the last inner solve
+ * 14 PCG iterations of the k_v updates of the last inner solve (kv_pcg_iters > 0; else 0)
  * Synchronizes the problem's stream. */
-#define NRTO_NSTAT 14
+#define NRTO_NSTAT 15
 nrto_status nrto_get_stats(nrto_problem_t p, double* out, int width);
 
 /* Named internal arrays of one instance, converted to float64 (checkpointing and testing).

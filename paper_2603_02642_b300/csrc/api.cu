@@ -562,6 +562,8 @@ void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
   sp.adapt_mu = o.adapt_mu; sp.adapt_tau = o.adapt_tau; sp.rho_min = o.rho_min; sp.rho_max = o.rho_max;
   sp.stall_ratio = o.stall_ratio;
   sp.fallback = o.warm_fallback;
+  sp.kv_pcg_iters = o.solver == NRTO_SOLVER_FULLADMM ? o.kv_pcg_iters : 0;
+  sp.kv_pcg_tol = o.kv_pcg_tol;
   P->warm_pending = false;
   if (o.solver == NRTO_SOLVER_FULLADMM) {
     k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.rho, 0.0, sp.warm);
@@ -762,6 +764,10 @@ void check_opts(const nrto_solver_opts* o) {
   if (o->stall_every > 0 && !(o->stall_ratio > 0 && o->stall_ratio < 1)) fail(NRTO_ERR_INVALID, "stall_ratio must be in (0,1)");
   if (o->carry != 0 && o->carry != 1) fail(NRTO_ERR_INVALID, "carry must be 0 or 1");
   if (o->max_inner_final < 0 || o->max_inner_final > 1000000) fail(NRTO_ERR_INVALID, "max_inner_final out of range");
+  if (o->kv_pcg_iters < 0 || o->kv_pcg_iters > 1000000) fail(NRTO_ERR_INVALID, "kv_pcg_iters out of range");
+  if (o->kv_pcg_iters > 0 && o->solver != NRTO_SOLVER_FULLADMM)
+    fail(NRTO_ERR_INVALID, "kv_pcg_iters applies to NRTO_SOLVER_FULLADMM only");
+  if (o->kv_pcg_iters > 0 && !(o->kv_pcg_tol >= 0 && o->kv_pcg_tol < 1)) fail(NRTO_ERR_INVALID, "kv_pcg_tol must be in [0,1)");
   if (o->solver == NRTO_SOLVER_DR) {
     if (!(o->alpha > 0 && o->alpha < 2)) fail(NRTO_ERR_INVALID, "alpha must be in (0,2)");
     if (!(o->r_chi > 0) || !(o->sigma > 0)) fail(NRTO_ERR_INVALID, "r_chi and sigma must be positive");
@@ -1465,7 +1471,7 @@ nrto_status nrto_get_stats(nrto_problem_t p, double* out, int width) {
       o[0] = a[IS_CUMITERS]; o[1] = a[IS_ITERS]; o[2] = a[IS_STATUS]; o[3] = a[IS_NACC];
       o[4] = c[SC_RHO]; o[5] = a[IS_DRITERS]; o[6] = a[IS_FALLBACK]; o[7] = a[IS_ACCST];
       o[8] = c[SC_PHI]; o[9] = c[SC_COST_ACC]; o[10] = c[SC_VIOL]; o[11] = c[SC_RTRUST];
-      o[12] = c[SC_RP]; o[13] = c[SC_RD];
+      o[12] = c[SC_RP]; o[13] = c[SC_RD]; o[14] = a[IS_PCG];
       for (int k = NRTO_NSTAT; k < width; ++k) o[k] = 0.0;
     }
     return NRTO_OK;

@@ -27,6 +27,8 @@
 namespace nrto {
 
 struct SolveParams {
+  int kv_pcg_iters;                     // k_v update by Jacobi-PCG with this cap (0: exact per-step solve)
+  double kv_pcg_tol;
   double rho, eps_p, eps_d;
   double alpha, r_chi, sigma, eps_dr;   // DR
   int max_iter, check, warm, max_dr;
@@ -431,6 +433,116 @@ __device__ __forceinline__ void gain_solve_warps(const double* ar, const Arena& 
     for (int q = lane; q < NE; q += 32) gt_out[(long long)T * NE + q] = 0.0;
 }
 
+// The k_v update by matrix-free Jacobi-preconditioned conjugate gradients (Sec. IV: the k_v update
+// by PCG), run by threads 32 .. blockDim-1 with named barrier 1 while warp 0 runs the block-2 sweep.
+// System: (H X)_m = 2 R_KᵀR_K X_m + ρτ G_m X_m Σ_m = R_m = ρ√τ Z'_m Ψ_m (the same right-hand side as
+// the exact per-step solve); preconditioner: the diagonal 2 (R_K)_u² + ρτ (G_m)_uu (Σ_m)_cc.  Starts
+// from the gains in Kout, stops before an iteration when ‖R - H X‖ ≤ tol ‖R‖ or after max_iter
+// iterations, leaves X in Kout and its table √τ X_m Ψ_mᵀ in gt_out.  FP64.  Returns the iterations.
+struct PcgArgs {
+  int max_iter;
+  double tol, rho, tau;
+  const double* Gm;      // slot arena's G_m blocks (T × nu × nu)
+  double* red;           // shared scratch: 3 × (warps) doubles
+};
+
+template <int NX, int NU>
+__device__ __noinline__ int gain_pcg_group(double* ar, const Arena& L, int T, double sqrt_tau, const PcgArgs& pa,
+                                           double* Kout, double* gt_out) {
+  constexpr int NE = NU * NX;
+  const int me = threadIdx.x - 32, ng = blockDim.x - 32, n = T * NE;
+  const int lane = threadIdx.x & 31, gw = me >> 5, nwg = ng >> 5;
+  double* x = Kout;
+  double* r = ar + L.Ws1;
+  double* p = ar + L.Ws2;
+  double* Ap = ar + L.Pc1;
+  const double* Sig = ar + L.Sigma;
+  const double* RK = ar + L.RK;
+  const double ct = pa.rho * pa.tau;
+  auto hop = [&](const double* v, int q) {
+    const int m = q / NE, u = (q / NX) % NU, c = q % NX;
+    const double* vm = v + (long long)m * NE;
+    const double* G = pa.Gm + (long long)m * NU * NU + u * NU;
+    const double* S = Sig + (long long)m * NX * NX;
+    double acc = 0.0;
+    for (int w = 0; w < NU; ++w) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < NX; ++k) t += vm[w * NX + k] * S[k * NX + c];
+      acc += G[w] * t;
+    }
+    return 2.0 * RK[u] * RK[u] * v[q] + ct * acc;
+  };
+  auto dinv = [&](int q) {
+    const int m = q / NE, u = (q / NX) % NU, c = q % NX;
+    return 1.0 / (2.0 * RK[u] * RK[u] + ct * pa.Gm[(long long)m * NU * NU + u * NU + u] * Sig[(long long)m * NX * NX + c * NX + c]);
+  };
+  auto gsum3 = [&](double& a, double& b, double& c) {
+    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+    if (lane == 0) { pa.red[3 * gw] = a; pa.red[3 * gw + 1] = b; pa.red[3 * gw + 2] = c; }
+    group_sync(1, ng);
+    a = b = c = 0.0;
+    for (int w = 0; w < nwg; ++w) { a += pa.red[3 * w]; b += pa.red[3 * w + 1]; c += pa.red[3 * w + 2]; }
+    group_sync(1, ng);
+  };
+  // r = R - H x,  p = D⁻¹ r
+  double rn0 = 0.0, rz = 0.0, rr = 0.0;
+  for (int q = me; q < n; q += ng) {
+    const int m = q / NE, u = (q / NX) % NU, c = q % NX;
+    const double* Zp = ar + L.Zp + (long long)m * NE + u * NX;
+    const double* Ps = ar + L.Psi + (long long)m * NX * NX;
+    double R = 0.0;
+#pragma unroll
+    for (int k = 0; k < NX; ++k) R += Zp[k] * Ps[k * NX + c];
+    R *= pa.rho * sqrt_tau;
+    const double rq = R - hop(x, q);
+    const double zq = dinv(q) * rq;
+    r[q] = rq;
+    p[q] = zq;
+    rn0 += R * R; rz += rq * zq; rr += rq * rq;
+  }
+  gsum3(rn0, rz, rr);
+  rn0 = sqrt(rn0);
+  int it = 0;
+  while (it < pa.max_iter && !(sqrt(rr) <= pa.tol * rn0)) {
+    double pap = 0.0, z0 = 0.0, z1 = 0.0;
+    for (int q = me; q < n; q += ng) {
+      const double a = hop(p, q);
+      Ap[q] = a;
+      pap += p[q] * a;
+    }
+    gsum3(pap, z0, z1);
+    const double alpha = rz / pap;
+    double rzn = 0.0, rrn = 0.0, z2 = 0.0;
+    for (int q = me; q < n; q += ng) {
+      x[q] += alpha * p[q];
+      const double rq = r[q] - alpha * Ap[q];
+      r[q] = rq;
+      rzn += rq * dinv(q) * rq;
+      rrn += rq * rq;
+    }
+    gsum3(rzn, rrn, z2);
+    const double beta = rzn / rz;
+    for (int q = me; q < n; q += ng) p[q] = dinv(q) * r[q] + beta * p[q];
+    group_sync(1, ng);
+    rz = rzn;
+    rr = rrn;
+    ++it;
+  }
+  // the gain table of the new gains for the row pass: √τ X_m Ψ_mᵀ
+  for (int q = me; q < n; q += ng) {
+    const int m = q / NE, u = (q / NX) % NU, c = q % NX;
+    const double* xm = x + (long long)m * NE + u * NX;
+    const double* Ps = ar + L.Psi + (long long)m * NX * NX + c * NX;
+    double g = 0.0;
+#pragma unroll
+    for (int k = 0; k < NX; ++k) g += xm[k] * Ps[k];
+    gt_out[q] = sqrt_tau * g;
+  }
+  for (int q = me; q < NE; q += ng) gt_out[(long long)T * NE + q] = 0.0;
+  return it;
+}
+
 // Block-2 (δû) LQ sweep with fixed factors (warp 0 only).  Linear terms q_t (t = 0..T, index t
 // of qv; q_0 unused) and r_k in the arena.  Writes du, dx.  Arithmetic in Real.
 // Each lane keeps the factor rows it needs for one step in registers and loads the next step's rows
@@ -603,7 +715,8 @@ struct B2Smem {
 template <int NX, int NU, typename Real>
 __device__ __noinline__ bool block2_sweep_and_gain(double* ar, const Arena& L, int T, const B2Smem<NX, NU, Real> b2,
                                                    uint64_t* bars, uint32_t* phase, int* s_flag, Real* gscr,
-                                                   const double* gargs, double* Kout, double* gt_out) {
+                                                   const double* gargs, double* Kout, double* gt_out,
+                                                   const PcgArgs& pcg, int* pcg_iters) {
   constexpr int BW = pk_stride(NX, NU);
   constexpr int oM = NU * NU, oL = oM + NU * NX, oA = oL + NU * NX, oB = oA + NX * NX;
   const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
@@ -642,8 +755,13 @@ __device__ __noinline__ bool block2_sweep_and_gain(double* ar, const Arena& L, i
   __syncthreads();
   bool ok = true;
   if (tid >= 32) {
-    gain_solve_warps<NX, NU, Real>(ar, L, T, gargs[0], gargs[1], Kout, gt_out, 1,
-                                   GainScratch<NX, NU, Real>::warps(nthr / 32 - 1), gscr);
+    if (pcg.max_iter > 0) {
+      const int it = gain_pcg_group<NX, NU>(ar, L, T, gargs[0], pcg, Kout, gt_out);
+      if (tid == 32) *pcg_iters += it;
+    } else {
+      gain_solve_warps<NX, NU, Real>(ar, L, T, gargs[0], gargs[1], Kout, gt_out, 1,
+                                     GainScratch<NX, NU, Real>::warps(nthr / 32 - 1), gscr);
+    }
   } else {
     // ---- backward: p_k = c_k + A_cl,kᵀ p_{k+1}; lane j < NX owns p_j ----
     Real p = (lane < NX) ? b2.qs[(size_t)T * NX + lane] : (Real)0;
@@ -1272,6 +1390,7 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   const bool carry = carry_applies(D.is, inst, sp.warm);
   const int winit = carry ? 2 : (sp.warm == 1 ? 1 : 0);
   const bool keep_dx = carry && isr[IS_MOVED] == 0;
+  if (tid == 0) isr[IS_PCG] = 0;
   if (winit != 2)
     for (long long e = tid; e < I.n_ent; e += NT) lam[I.ent0 + e] = (Real)0;
   for (int r = tid; r < n_rows; r += NT) {
@@ -1431,7 +1550,9 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     {
       const double gargs[2] = {I.sqrt_tau, rho * I.sqrt_tau};
       double* gt_new = ar + (gsel ? L.Gt0 : L.Gt1);
-      if (!block2_sweep_and_gain<NX, NU, Real>(ar, L, T, b2, bars, phase, s_flag, sm.rowpart, gargs, ar + L.K1, gt_new)) {
+      const PcgArgs pcg{sp.kv_pcg_iters, sp.kv_pcg_tol, rho, I.tau, sa + SL.Gm, sm.red};
+      if (!block2_sweep_and_gain<NX, NU, Real>(ar, L, T, b2, bars, phase, s_flag, sm.rowpart, gargs, ar + L.K1, gt_new,
+                                               pcg, isr + IS_PCG)) {
         status = ST_TIMEOUT;
         goto done;
       }

@@ -71,7 +71,7 @@ struct Arena {
   long long Psi, SigU, SigL, Phi;
   long long K0, K1, Kt, Kacc, Gt0, Gt1, Zp;
   long long du, dx, du_prev, dx_prev, e, lam_e, qv, rv;
-  long long Pf, Gam, Dv, RicL, RicAcl, RicN, RicM, Ws1, Ws2, RicPk;
+  long long Pf, Gam, Dv, RicL, RicAcl, RicN, RicM, Ws1, Ws2, Pc1, RicPk;
   long long total;
 };
 
@@ -97,7 +97,7 @@ NRTO_HD Arena arena_layout(int nx, int nu, int T, int n_obs, int n_link) {
   a.rv = take((long long)T * nu);
   a.Pf = take((long long)T * nu * nu); a.Gam = take((long long)T * nu); a.Dv = take(g);
   a.RicL = take(g); a.RicAcl = take((long long)T * nx * nx); a.RicN = take((long long)T * nu * nu);
-  a.RicM = take(g); a.Ws1 = take(g); a.Ws2 = take(g);
+  a.RicM = take(g); a.Ws1 = take(g); a.Ws2 = take(g); a.Pc1 = take(g);
   a.RicPk = take((long long)T * pk_stride(nx, nu));   // sized for double records
   a.total = o;
   return a;
@@ -128,8 +128,9 @@ enum : int { SC_RTRUST = 0, SC_RP, SC_RD, SC_RPP, SC_RDP, SC_SCAL_RP, SC_SCAL_RD
              SC_PHI, SC_PHI_CAND, SC_COST, SC_RHO, SC_RDR, SC_RHOD, SC_VIOL, SC_VIOLC, SC_COST_ACC, NSC = 20 };
 // IS_ACCST: status of the inner solve whose candidate became the accepted iterate (0: none yet);
 // IS_MOVED: the nominal moved to û + δû since the last inner solve (an accepted outer step).
+// IS_PCG: PCG iterations of the k_v updates of the last inner solve (kv_pcg_iters > 0).
 enum : int { IS_STATUS = 0, IS_ITERS, IS_SLOT, IS_ACCEPT, IS_DRITERS, IS_CUMITERS, IS_NACC, IS_FALLBACK, IS_ACCST,
-             IS_MOVED, NIS = 10 };
+             IS_MOVED, IS_PCG, NIS = 11 };
 
 template <typename Real>
 struct LinSlot {

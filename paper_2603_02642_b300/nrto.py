@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("NRTO_LIB", os.path.join(HERE, "libnrto.so"))
 
 PREC_FP64, PREC_MIXED = 0, 1
-NSTAT = 14   # NRTO_NSTAT
+NSTAT = 15   # NRTO_NSTAT
 NMAPPING = 4  # NRTO_NMAPPING
 SOLVER_DR, SOLVER_FULLADMM, SOLVER_FULLADMM_AW = 0, 1, 2
 
@@ -49,7 +49,8 @@ class SolverOpts(C.Structure):
                 ("adapt_every", C.c_int), ("adapt_mu", C.c_double), ("adapt_tau", C.c_double),
                 ("rho_min", C.c_double), ("rho_max", C.c_double),
                 ("stall_every", C.c_int), ("stall_ratio", C.c_double), ("warm_fallback", C.c_int),
-                ("carry", C.c_int), ("max_inner_final", C.c_int)]
+                ("carry", C.c_int), ("max_inner_final", C.c_int),
+                ("kv_pcg_iters", C.c_int), ("kv_pcg_tol", C.c_double)]
 
 
 class InstanceInfo(C.Structure):
@@ -172,13 +173,15 @@ class Options:
     warm_fallback: int = 0
     carry: int = 0
     max_inner_final: int = 0
+    kv_pcg_iters: int = 0
+    kv_pcg_tol: float = 0.05
 
     def c(self) -> SolverOpts:
         return SolverOpts(self.solver, self.rho, self.alpha, self.r_chi, self.sigma, self.eps_p, self.eps_d,
                           self.eps_dr, self.max_inner, self.max_dr, self.check, self.r0, self.r_min, self.w_p,
                           self.adapt_every, self.adapt_mu, self.adapt_tau, self.rho_min, self.rho_max,
                           self.stall_every, self.stall_ratio, self.warm_fallback, self.carry,
-                          self.max_inner_final)
+                          self.max_inner_final, self.kv_pcg_iters, self.kv_pcg_tol)
 
 
 _ZERO1 = np.zeros(1)
@@ -371,7 +374,7 @@ class Problem:
         return c.value, r.value
 
     STATS = ["cum_iters", "iters", "status", "n_accepted", "rho", "dr_iters", "fallback", "accepted_status",
-             "merit", "cost", "max_violation", "trust_radius", "r_p", "r_d"]
+             "merit", "cost", "max_violation", "trust_radius", "r_p", "r_d", "pcg_iters"]
 
     def stats(self):
         """Per-instance statistics of the batch (nrto_get_stats): a dict of arrays named by STATS."""
