@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--stall", type=int, default=100, help="stall-stop period (0 = off)")
     ap.add_argument("--carry", type=int, default=1, help="inner-state carry across outer steps")
     ap.add_argument("--feas-tol", type=float, default=1e-4)
+    ap.add_argument("--r0", type=float, default=0.5, help="initial and largest trust radius of the outer loop")
+    ap.add_argument("--w-p", type=float, default=1000.0, help="merit weight of the robust-constraint violation")
+    ap.add_argument("--mc", type=int, default=1000, help="Monte Carlo interior and edge samples per instance")
     ap.add_argument("--plain-n", type=int, default=16, help="instances of the plain batch-1 FP64 arm")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -89,7 +92,7 @@ def entries(inst):
 def solver_options(args, carry=None):
     from paper_2603_02642_b300 import nrto
     return nrto.Options(rho=args.rho, max_inner=args.max_inner, max_inner_final=args.max_inner_final,
-                        eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0, adapt_every=args.adapt,
+                        eps_p=1e-4, eps_d=1e-4, check=1, r0=args.r0, w_p=args.w_p, adapt_every=args.adapt,
                         stall_every=args.stall, stall_ratio=0.9, carry=args.carry if carry is None else carry)
 
 
@@ -115,7 +118,7 @@ def _oracle_task(task):
         return {"kind": "cost", "S": sum(entries(inst)), "t_lin": t1 - t0, "t_it": (t2 - t1) / prm["k_it"]}
     # a complete solve with the benchmark's schedule
     t0 = time.perf_counter()
-    res = O.solve(inst, O.OuterOptions(n_outer=prm["n_outer"], r0=2.0, carry=bool(prm["carry"]),
+    res = O.solve(inst, O.OuterOptions(n_outer=prm["n_outer"], r0=prm["r0"], w_p=prm["w_p"], carry=bool(prm["carry"]),
                                        max_inner_final=prm["max_inner_final"]),
                   admm=F.FullADMMOptions(rho=prm["rho"], max_iter=prm["max_inner"], eps_p=1e-4, eps_d=1e-4,
                                          adapt_every=prm["adapt"], stall_every=prm["stall"], stall_ratio=0.9))
@@ -146,7 +149,7 @@ def oracle_tasks(instances, args, cores):
     n_full = int(min(max(cores, 4), 16))
     prm = dict(rho=args.rho, k_it=4, n_outer=args.n_outer, max_inner=args.max_inner,
                max_inner_final=args.max_inner_final, adapt=args.adapt, stall=args.stall, carry=args.carry,
-               feas_tol=args.feas_tol)
+               feas_tol=args.feas_tol, r0=args.r0, w_p=args.w_p)
     return ([("full", instances[int(i)], prm) for i in order[:n_full]]
             + [("cost", instances[int(order[i])], prm) for i in q])
 
@@ -683,6 +686,23 @@ def main():
         e2e = {"value": float(tt[1].item()) * n_e2e / float(tt[0].item()), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
 
+    # Monte Carlo robust-constraint satisfaction of the returned iterates (Sec. V, Methodology),
+    # outside the timed region: interior and edge disturbances per instance, rollouts through the
+    # nonlinear dynamics, a rollout counting when every constraint holds to the solve's tolerance
+    mc = None
+    if args.mc > 0:
+        st_mc = prob.stats()
+        ok_mc = counted(st_mc, args.feas_tol)
+        t0 = time.perf_counter()
+        sat = prob.monte_carlo(args.mc, args.mc, seed=2603, tol=args.feas_tol)
+        mc_s = time.perf_counter() - t0
+        ns = 2 * args.mc
+        mc = {"samples_per_instance": ns, "interior": args.mc, "edge": args.mc, "tol": args.feas_tol,
+              "satisfied_frac_counted": float(sat[ok_mc].sum() / (ns * max(1, int(ok_mc.sum())))),
+              "counted_all_satisfied": int((sat[ok_mc] == ns).sum()), "counted": int(ok_mc.sum()),
+              "satisfied_frac_all": float(sat.sum() / (ns * len(insts))),
+              "seconds": mc_s, "precision": "f64", "iterate": "the returned iterate of the end-to-end run"}
+
     plain = errs = cfgs = warm = cpu = None
     if rank == 0:
         if not args.no_plain:
@@ -707,6 +727,7 @@ def main():
                        "n_outer": args.n_outer, "max_inner": args.max_inner, "max_inner_final": args.max_inner_final,
                        "precision": args.prec, "rho0": args.rho, "adapt_every": args.adapt,
                        "stall_every": args.stall, "carry": args.carry, "feas_tol": args.feas_tol,
+                       "r0": args.r0, "w_p": args.w_p,
                        "l2": "inputs larger than L2 (row arrays of several GB)",
                        "counted": n_ok, "counted_frac": n_ok / prob.n,
                        "counted_by_kind": {"unicycle": int(ok[kinds == 0].sum()), "quadcopter": int(ok[kinds == 1].sum())},
@@ -718,6 +739,7 @@ def main():
             "plain_fp64_gpu": plain,
             "ratio_vs_plain": (value / plain["value"]) if plain and plain["value"] > 0 else None,
             "error_vs_fp64": errs,
+            "monte_carlo": mc,
             "gpu_launches": int(launches),
             "graph_replays": int(graph_replays),
             "autotune": {"chosen_mapping": int(tuned), "ms_per_mapping": [float(x) for x in tune_ms],

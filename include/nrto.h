@@ -257,6 +257,30 @@ nrto_status nrto_set_warm_start(nrto_problem_t p, const double* K, const double*
 #define NRTO_NSTAT 15
 nrto_status nrto_get_stats(nrto_problem_t p, double* out, int width);
 
+/* Monte Carlo check of robust-constraint satisfaction (Sec. V, Methodology: disturbances drawn
+ * uniformly from the interior of the uncertainty set and reproducible edge cases on its boundary
+ * along convex combinations of the constraints' worst-case directions; the satisfaction
+ * probability is the fraction of rollouts that violate no constraint).  Per instance, the policy
+ * u_k = ū_k + K_k ζ_k at the nominal ū of the current linearization (after nrto_solve: the accepted
+ * iterate) is rolled out through the nonlinear dynamics, x_0 = x̄_0 + ζ_0,
+ * x_{k+1} = f(x_k, u_k) + ζ_{k+1}, under n_interior + n_edge disturbances ζ_i = √τ Ψ_iᵀ w_i
+ * (Ψ_iᵀΨ_i = Σ_i, w ∈ R^{(T+1) n_x}):
+ *  - samples 0 .. n_interior-1: w uniform in the unit ball (ζ uniform in the ellipsoid for Γ = I);
+ *  - edge sample e: w = v/‖v‖, v = Σ_c a_c y_{j_c}/‖y_{j_c}‖ over n_c = 1 + (e mod 3) rows j_c drawn
+ *    uniformly (state rows, then control rows), weights a_c in (0, 1], y_j = Â_j k + b̂_j the row's
+ *    SOC vector of Problem 2 at the current linearization;
+ * random numbers from SplitMix64 streams keyed by (seed, instance index, sample index), so that a
+ * sample is reproducible on its own.  A rollout counts when every constraint of Problem 1 (state
+ * rows at t = 1..T, control bounds at k = 0..T-1) is ≤ tol.  FP64 in both precisions (the SOC
+ * vectors use the problem's stored b̂, b).
+ * K: host, Σ T*nu*nx, the layout of nrto_socp_out.K, or null for the gains of the accepted iterate.
+ * n_ok: host, n ints, the rollouts that satisfied every constraint.  worst: host,
+ * n × (n_interior + n_edge) doubles (row i = instance i) or null: per sample the largest constraint
+ * value.  Allocates and frees its own device scratch; synchronizes the problem's stream.
+ * NRTO_ERR_STATE before the first linearization. */
+nrto_status nrto_monte_carlo(nrto_problem_t p, const double* K, int n_interior, int n_edge, unsigned long long seed,
+                             double tol, int* n_ok, double* worst);
+
 /* Named internal arrays of one instance, converted to float64 (checkpointing and testing).
  * field: one of NRTO_F_*; count must equal the field's size for that instance. */
 enum {

@@ -99,8 +99,8 @@ def whitened_sample(inst, lin, K, seed, inst_index, sample, n_interior, Y=None):
     if Y is None:
         Y = soc_rows(lin, K)
     e = sample - n_interior
-    nc = 1 + e % 3
     n_rows = Y.shape[0]
+    nc = 1 + e % 3 if n_rows > 0 else 0
     u = uniforms(key, np.arange(2 * nc))
     rows = np.minimum((u[:nc] * n_rows).astype(np.int64), n_rows - 1)
     wts = 1.0 - u[nc:]

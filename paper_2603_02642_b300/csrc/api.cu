@@ -19,6 +19,7 @@
 
 #include "../../include/nrto.h"
 #include "fulladmm.cuh"
+#include "montecarlo.cuh"
 #include "solver_kernels.h"
 
 using namespace nrto;
@@ -1192,6 +1193,17 @@ nrto_status create_problem(const nrto_problem_desc* descs, int n, int precision,
 
 }  // namespace
 
+template <typename Real>
+void launch_monte_carlo(nrto_problem* P, const double* dK, int n_int, int n_edge, unsigned long long seed, double tol,
+                        double* d_worst, int* d_ok) {
+  size_t smem = 0;
+  for (const Inst& I : P->h_inst) smem = std::max(smem, sizeof(double) * (size_t)(I.T + 1) * I.nu * I.nx);
+  CK(cudaFuncSetAttribute(k_monte_carlo<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_monte_carlo<Real><<<P->n, 128, smem, P->stream>>>(P->dev<Real>(), dK, P->d_koff, n_int, n_edge, seed, tol, d_worst,
+                                                       d_ok);
+  P->check_launch("k_monte_carlo");
+}
+
 extern "C" {
 
 nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int precision, void* stream,
@@ -1451,6 +1463,48 @@ nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, con
     p->warm_pending = true;
     return NRTO_OK;
   } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_monte_carlo(nrto_problem_t p, const double* K, int n_interior, int n_edge, unsigned long long seed,
+                             double tol, int* n_ok, double* worst) {
+  double* dK = nullptr;
+  double* dw = nullptr;
+  int* dok = nullptr;
+  auto release = [&]() {
+    if (dK) cudaFree(dK);
+    if (dw) cudaFree(dw);
+    if (dok) cudaFree(dok);
+  };
+  try {
+    if (!p || !n_ok) fail(NRTO_ERR_INVALID, "null argument");
+    if (n_interior < 0 || n_edge < 0 || (long long)n_interior + n_edge > (1 << 24))
+      fail(NRTO_ERR_INVALID, "sample counts out of range");
+    if (std::isnan(tol)) fail(NRTO_ERR_INVALID, "tol is NaN");
+    if (!p->linearized) fail(NRTO_ERR_STATE, "nrto_linearize or nrto_solve must come before nrto_monte_carlo");
+    if (K && !finite_arr(K, p->k_total)) fail(NRTO_ERR_NUMERIC, "K not finite");
+    const long long ns = (long long)n_interior + n_edge;
+    size_t smem = 0;
+    for (const Inst& I : p->h_inst) smem = std::max(smem, sizeof(double) * (size_t)(I.T + 1) * I.nu * I.nx);
+    if (smem > 227 * 1024) fail(NRTO_ERR_INVALID, "horizon too long for the Monte Carlo kernel's gain table");
+    CK(cudaStreamSynchronize(p->stream));
+    if (K) {
+      CK(cudaMalloc(&dK, sizeof(double) * std::max<long long>(p->k_total, 1)));
+      CK(cudaMemcpyAsync(dK, K, sizeof(double) * p->k_total, cudaMemcpyHostToDevice, p->stream));
+    }
+    if (worst && ns > 0) CK(cudaMalloc(&dw, sizeof(double) * (size_t)p->n * ns));
+    CK(cudaMalloc(&dok, sizeof(int) * std::max(p->n, 1)));
+    if (p->prec == NRTO_PREC_FP64) launch_monte_carlo<double>(p, dK, n_interior, n_edge, seed, tol, dw, dok);
+    else launch_monte_carlo<float>(p, dK, n_interior, n_edge, seed, tol, dw, dok);
+    CK(cudaMemcpyAsync(n_ok, dok, sizeof(int) * p->n, cudaMemcpyDeviceToHost, p->stream));
+    if (dw) CK(cudaMemcpyAsync(worst, dw, sizeof(double) * (size_t)p->n * ns, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    release();
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    if (p) cudaStreamSynchronize(p->stream);
+    release();
     return handle(e);
   }
 }

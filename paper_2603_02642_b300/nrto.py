@@ -118,6 +118,8 @@ def load():
     lib.nrto_graph_info.restype = C.c_int
     lib.nrto_get_stats.argtypes = [P, _dp, C.c_int]
     lib.nrto_get_stats.restype = C.c_int
+    lib.nrto_monte_carlo.argtypes = [P, _dp, C.c_int, C.c_int, C.c_ulonglong, C.c_double, _ip, _dp]
+    lib.nrto_monte_carlo.restype = C.c_int
     lib.nrto_kernel_launches.argtypes = [P]
     lib.nrto_kernel_launches.restype = C.c_longlong
     lib.nrto_last_error.restype = C.c_char_p
@@ -381,6 +383,20 @@ class Problem:
         out = np.zeros((self.n, NSTAT))
         _check(load().nrto_get_stats(self._h, _ptr(out), NSTAT))
         return {k: out[:, i] for i, k in enumerate(self.STATS)}
+
+    def monte_carlo(self, n_interior=1000, n_edge=1000, seed=0, tol=0.0, K=None, per_sample=False):
+        """Monte Carlo robust-constraint satisfaction per instance (nrto_monte_carlo) at the nominal of
+        the current linearization, with the gains K (list of (T, nu, nx) arrays, one per instance) or
+        those of the accepted iterate.  Returns the satisfied-rollout counts, and with per_sample the
+        (n, n_interior + n_edge) worst constraint values as well."""
+        ok = np.zeros(self.n, dtype=np.int32)
+        Kf = None
+        if K is not None:
+            Kf = np.ascontiguousarray(np.concatenate([np.asarray(k, dtype=np.float64).reshape(-1) for k in K]))
+        worst = np.zeros((self.n, n_interior + n_edge)) if per_sample else None
+        _check(load().nrto_monte_carlo(self._h, _ptr(Kf), n_interior, n_edge, seed, tol,
+                                       ok.ctypes.data_as(_ip), _ptr(worst)))
+        return (ok, worst) if per_sample else ok
 
 
 def solve_noalloc(instances, opts: Options, n_outer=10, precision=PREC_FP64, stream=None):
