@@ -46,12 +46,16 @@ int kind_nx(int k) { return k == KIND_UNICYCLE ? 3 : (k == KIND_QUADCOPTER ? 12 
 int kind_nu(int k) { return k == KIND_UNICYCLE ? 2 : (k == KIND_QUADCOPTER ? 4 : 7); }
 int kind_tmax(int k) { return k == KIND_UNICYCLE ? 256 : (k == KIND_QUADCOPTER ? 160 : 128); }
 
-// opt-in shared memory per block on sm_103a is 227 KB; keep 1 KB for static shared variables
-// Dynamic shared memory per solver CTA: the SM's 228 KB are shared by the resident CTAs, each of which
-// also holds ~9.5 KB of static shared memory (mbarriers, flags, Riccati scratch) and 1 KB reserved.
+// Dynamic shared memory per solver CTA: the SM's 228 KB (227 KB opt-in per block) are shared by the
+// kind's resident CTAs, each of which also holds ~9.5 KB of static shared memory (mbarriers, flags,
+// Riccati scratch) and 1 KB reserved.
 template <typename Real>
-constexpr int smem_budget() {
-  return (sizeof(Real) == 4 && NRTO_FA_MINB_F32 > 1) ? (228 * 1024) / NRTO_FA_MINB_F32 - 12 * 1024 : 227 * 1024 - 12 * 1024;
+int smem_budget(int kind) {
+  int minb = 1;
+  if (kind == KIND_UNICYCLE) minb = FACfg<3, 2, Real>::MINB;
+  else if (kind == KIND_QUADCOPTER) minb = FACfg<12, 4, Real>::MINB;
+  else minb = FACfg<14, 7, Real>::MINB;
+  return minb > 1 ? (228 * 1024) / minb - 12 * 1024 : 227 * 1024 - 12 * 1024;
 }
 
 template <typename Real>
@@ -644,12 +648,12 @@ void choose_chunk(KindLaunch& kl) {
   const int nx = kind_nx(kl.kind);
   const int minc = ((kl.tmax + 1) * nx + 3) & ~3;
   int chunk = 12288;
-  while (chunk > minc && smem_for<Real>(kl.kind, chunk, chunk / (2 * nx) + 2) > (size_t)smem_budget<Real>()) chunk -= 256;
+  while (chunk > minc && smem_for<Real>(kl.kind, chunk, chunk / (2 * nx) + 2) > (size_t)smem_budget<Real>(kl.kind)) chunk -= 256;
   if (chunk < minc) chunk = minc;
   kl.chunk = chunk;
   kl.max_rows = chunk / (2 * nx) + 2;
   kl.smem = smem_for<Real>(kl.kind, chunk, kl.max_rows);
-  if (kl.smem > (size_t)smem_budget<Real>()) fail(NRTO_ERR_INVALID, "horizon too long for the shared-memory budget of this precision");
+  if (kl.smem > (size_t)smem_budget<Real>(kl.kind)) fail(NRTO_ERR_INVALID, "horizon too long for the shared-memory budget of this precision");
   // the block-2 sweep keeps q, r, l and a ring of >= 2 factor records in the chunk buffers
   const int nu = kind_nu(kl.kind);
   size_t bb = 0;

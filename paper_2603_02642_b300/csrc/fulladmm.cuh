@@ -57,10 +57,20 @@ struct SolveParams {
 #define NRTO_FA_W_QUAD 2
 #endif
 
+// The unicycle's CTA shape in the compute precision float (its rows need at most 128 threads per row
+// group up to T = 254, so two 256-thread CTAs can share an SM).
+#ifndef NRTO_FA_NT_UNI
+#define NRTO_FA_NT_UNI NRTO_FA_NT_F32
+#endif
+#ifndef NRTO_FA_MINB_UNI
+#define NRTO_FA_MINB_UNI NRTO_FA_MINB_F32
+#endif
+
 template <int NX, int NU, typename Real>
 struct FACfg {
-  static constexpr int NT = sizeof(Real) == 4 ? NRTO_FA_NT_F32 : 512;
-  static constexpr int MINB = sizeof(Real) == 4 ? NRTO_FA_MINB_F32 : 1;   // resident CTAs per SM
+  static constexpr bool UNI32 = sizeof(Real) == 4 && NX == 3;
+  static constexpr int NT = UNI32 ? NRTO_FA_NT_UNI : (sizeof(Real) == 4 ? NRTO_FA_NT_F32 : 512);
+  static constexpr int MINB = UNI32 ? NRTO_FA_MINB_UNI : (sizeof(Real) == 4 ? NRTO_FA_MINB_F32 : 1);   // resident CTAs per SM
   static constexpr int NW = NT / 32;
   static constexpr int TMAXC = (NX == 3) ? 256 : (NX == 12 ? 160 : 128);
   static constexpr int W = (NX == 3) ? 3 : (NX == 12 ? NRTO_FA_W_QUAD : 2);   // components of a block per thread
