@@ -245,7 +245,12 @@ def clocks_summary(path, dev_index):
 # instances.  The launch at the benchmark size is scaled from it by its algorithmic bytes (traffic
 # grows with row entries x iterations).  Valid only for the kernel sources it was measured on: any
 # change to them makes the reported traffic null until it is measured again.
-TRAFFIC = {"sources_sha256": None, "ratio": {}}
+# DRAM traffic of k_fulladmm per algorithmic byte (survey count), from the full ncu capture of the
+# 148-instance case (dram__bytes_read.sum + dram__bytes_write.sum over both kinds' launches, 40 iterations
+# each); valid while the kernel sources hash to sources_sha256.
+TRAFFIC = {"sources_sha256": "cc51bd258a13fb67e3994b370db5b42b4df7974ffdc6b6d20296f9ee9e1d6f9a",
+           "ratio": {"both": 1.021, "quadcopter": 1.097, "unicycle": 0.861},
+           "capture": "ncu --set full, batched_mix(148), one 40-iteration launch per kind"}
 KERNEL_SOURCES = ["fulladmm.cuh", "nrto_dev.cuh", "tma.cuh", "linearize.cuh", "dynamics.cuh"]
 
 
@@ -655,7 +660,10 @@ def main():
     solver_s_step = solver_ms / 1000.0
     achieved = bytes_step / solver_s_step / 1e9
     peak, peak_kind = measured_peak("hbm_gbs", 6400.0)
+    # per-launch DRAM traffic scaled from the capture by the algorithmic bytes (units processed)
     traffic = None
+    if kernel_sources_sha() == TRAFFIC["sources_sha256"]:
+        traffic = TRAFFIC["ratio"]["both"] * bytes_step / max(launches_per_step, 1e-30)
     # the batch's mixed-precision results of the sample, for the per-result comparison with FP64
     ids = sample_ids(args, len(insts))
     sol_mixed = mixed_results(prob, ids) if rank == 0 and not args.no_plain else None
