@@ -107,6 +107,25 @@ def warm_state(lin, K0, pt0, lam_p0) -> FullADMMState:
     return s
 
 
+def warm_state_lifted(lin, K0, pt0, lam_p0, theta0, du0, lam_w0, lam_e0) -> FullADMMState:
+    """Warm start of the lifted iteration (reading R8) from a predicted
+    (K, p̃, λ_p, θ, δû, λ_w, λ_e): warm_state plus
+      λ_ν,j^0 = θ_j (Â_j k^0 + b̂_j)   (at a fixed point ν_j = Â_j k + b̂_j = s_j(ν_j/s_j) with
+                                       ν_j = Π(Â_j k + b̂_j + λ_ν,j), so λ_ν,j = (1/s_j - 1)(Â_j k + b̂_j):
+                                       one scalar per row θ_j = 1/s_j - 1 ≥ 0 fixes the S-length dual),
+      δû^0 = du0 with δx^0 = F_u δû^0 (its linearized trajectory),
+      λ_w^0 = lam_w0 (orthant coupling) and λ_e^0 = lam_e0 (trust-region coupling, rows t = 1..T).
+    At a solution's values and the penalty its scaled duals belong to, the first iteration is at the
+    fixed point."""
+    s = warm_state(lin, K0, pt0, lam_p0)
+    s.lam_nu = np.asarray(theta0, dtype=np.float64)[:, None, None] * (P.Ahat_apply(lin, s.K) + lin.bhat)
+    s.du = np.array(du0, dtype=np.float64)
+    s.dx = P.delta_x(lin, s.du)
+    s.lam_w = np.array(lam_w0, dtype=np.float64)
+    s.lam_e = np.array(lam_e0, dtype=np.float64)
+    return s
+
+
 def block2_matrices(inst, lin, rho):
     """Hessian of the Block-2 (δû) quadratic after eliminating p (fixed per outer step):
     2R̄ + F̃ᵀ(2Q̄ + ρI)F̃ + (ρ/2) Σ_j b_j b_jᵀ, F̃ = rows t = 1..T of F_u."""

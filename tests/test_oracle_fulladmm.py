@@ -366,3 +366,34 @@ def test_fulladmm_with_tight_pcg_equals_the_exact_gain_update():
                                                kv_pcg_tol=1e-13), n_iter=30)
     assert np.allclose(a.K, b.K, atol=1e-10 * np.abs(a.K).max()) and np.allclose(a.du, b.du, atol=1e-10)
     assert b.pcg_iters > 0
+
+
+def test_lifted_warm_start_at_a_solution_is_its_fixed_point():
+    """At a converged solution the scaled dual λ_ν,j of a row whose cone is not projected to zero is
+    a non-negative multiple of Â_j k + b̂_j (the SOC fixed point), so one scalar per row rebuilds it;
+    from the solution's (k_v, p̃, λ_p, θ, δû, λ_w, λ_e) at the penalty its scaled duals belong to, the
+    first iteration meets the tolerances and returns the same solution.  With θ clipped at zero (rows
+    projected to zero, whose SOC vector vanishes, restart λ_ν at zero) it takes at most one more.
+    The plain (k_v, p̃, λ_p) warm start, which restarts the rest at zero, does not."""
+    inst = W.quadcopter(1, T=12, n_obs=3)
+    lin = P.linearize(inst, inst.u_init)
+    o = F.FullADMMOptions(rho=10.0, r_trust=2.0, max_iter=20000, eps_p=1e-8, eps_d=1e-8, adapt_every=25)
+    ref = F.iterate(inst, lin, o)
+    assert ref.converged and ref.iters > 20 and ref.rho != 10.0
+    Y = P.Ahat_apply(lin, ref.K) + lin.bhat
+    yy = np.sum(Y * Y, axis=(1, 2))
+    theta = np.where(yy > 0, np.sum(ref.lam_nu * Y, axis=(1, 2)) / np.where(yy > 0, yy, 1.0), 0.0)
+    resid = ref.lam_nu - theta[:, None, None] * Y
+    assert np.max(np.abs(resid)) < 1e-6 * max(1.0, np.max(np.abs(ref.lam_nu)))
+    live = yy > 1e-12                 # rows whose SOC vector does not vanish at the solution
+    assert live.sum() > 10 and np.all(theta[live] > -1e-6)
+    st = F.warm_state_lifted(lin, ref.K, ref.pt, ref.lam_p, theta, ref.du, ref.lam_w, ref.lam_e)
+    assert np.allclose(st.dx, ref.dx, atol=1e-9)          # δx = F_u δû of the solution
+    s1 = F.iterate(inst, lin, o, st, rho0=ref.rho)
+    assert s1.converged and s1.iters == 1
+    assert np.allclose(s1.du, ref.du, rtol=1e-6, atol=1e-8) and np.allclose(s1.K, ref.K, rtol=1e-3, atol=1e-8)
+    st0 = F.warm_state_lifted(lin, ref.K, ref.pt, ref.lam_p, np.maximum(theta, 0.0), ref.du, ref.lam_w, ref.lam_e)
+    s2 = F.iterate(inst, lin, o, st0, rho0=ref.rho)
+    assert s2.converged and s2.iters <= 2 and np.allclose(s2.du, ref.du, rtol=1e-6, atol=1e-8)
+    plain = F.iterate(inst, lin, o, F.warm_state(lin, ref.K, ref.pt, ref.lam_p), rho0=ref.rho)
+    assert plain.iters > 10
