@@ -236,9 +236,32 @@ nrto_status nrto_autotune(nrto_problem_t p, const nrto_solver_opts* opts, int n_
 nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, const float* features,
                                             const int* row_map, int k_off, int pt_off, int lp_off);
 
+/* The lifted warm start (nrto_set_warm_start_lifted) from the network in one call: offsets (host,
+ * 8 ints) into output[i]: K, p̃, λ_p as above, then per row θ (clipped at 0) and λ_w through row_map,
+ * δû (T*nu), λ_e (T*nx, steps 1..T), and log ρ (offsets[7] < 0: the solver's ρ). */
+nrto_status nrto_set_warm_start_from_network_lifted(nrto_problem_t p, nrto_mlp_t m, const float* features,
+                                                    const int* row_map, const int* offsets);
+
 /* Warm start for the next inner solve only: K (Σ T*nu*nx), p̃ and λ_p (Σ n_rows each); λ_ν = 0. */
 nrto_status nrto_set_warm_start(nrto_problem_t p, const double* K, const double* ptilde,
                                 const double* lambda_p);
+
+/* Lifted warm start (NRTO_SOLVER_FULLADMM with the lifted block 2), on top of the pending
+ * nrto_set_warm_start (NRTO_ERR_STATE without one): the rest of the iteration's state, so that a
+ * solution's values restart at its fixed point.
+ *   theta    host, Σ n_rows: per row θ_j ≥ 0 (negative values count as 0); the SOC dual becomes
+ *            λ_ν,j = θ_j (Â_j k + b̂_j) with the warm-start gains k: at a fixed point
+ *            ν_j = Π(Â_j k + b̂_j + λ_ν,j) = Â_j k + b̂_j, so λ_ν,j = (1/s_j - 1)(Â_j k + b̂_j) with the
+ *            projection scale s_j (NRTO_F_S) of a row not projected to zero;
+ *   lambda_w host, Σ n_rows: the orthant coupling's scaled dual (NRTO_F_LAMW);
+ *   du       host, Σ T*nu: δû (then δx = F_u δû and b_jᵀδû are formed on the device);
+ *   lambda_e host, Σ T*nx: the trust-region coupling's scaled dual at steps 1..T (NRTO_F_LAME);
+ *   rho      host, n doubles, or null: the penalty the scaled duals belong to, at which the solve
+ *            starts (and block 2 is factored); null: the solver's ρ.
+ * The next inner solve must be FullADMM (another solver kind returns NRTO_ERR_STATE); a later
+ * nrto_set_warm_start replaces the lifted start. */
+nrto_status nrto_set_warm_start_lifted(nrto_problem_t p, const double* theta, const double* lambda_w,
+                                       const double* du, const double* lambda_e, const double* rho);
 
 /* Per-instance solve statistics of the whole batch in one call: out (host, n × width doubles,
  * width >= NRTO_NSTAT), row i = instance i:
@@ -301,10 +324,14 @@ enum {
   NRTO_F_KACC = 14,  /* T*nu*nx    gains of the accepted nominal (outer loop)                 */
   NRTO_F_DX = 15,    /* (T+1)*nx   δx of the last inner solve                                */
   NRTO_F_SCAL = 16,  /* 8: r_p, r_d, r_p(paper), r_d(paper), merit, candidate merit, cost, trust r */
-  NRTO_F_STATS = 17  /* 7, read-only: inner iterations since the last nrto_solve reset, iterations of
+  NRTO_F_STATS = 17, /* 7, read-only: inner iterations since the last nrto_solve reset, iterations of
                         the last inner solve, its status, accepted outer steps, its final ρ,
                         (NRTO-DR) the DR iterations summed over its ADMM iterations, and 1 if the
                         last solve fell back from a warm start to a cold start                    */
+  NRTO_F_LAMW = 18,  /* n_rows     λ_w, the scaled dual of the lifted orthant coupling (FullADMM)     */
+  NRTO_F_LAME = 19,  /* (T+1)*nx   λ_e, the scaled dual of the lifted trust-region coupling (step 0
+                        unused)                                                                   */
+  NRTO_F_S = 20      /* n_rows     projection scale s_j of the last row pass (ν_j = s_j η̂_j)           */
 };
 nrto_status nrto_export(nrto_problem_t p, int field, int instance, double* dst, long long count);
 nrto_status nrto_import(nrto_problem_t p, int field, int instance, const double* src, long long count);

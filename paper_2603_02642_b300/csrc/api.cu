@@ -251,6 +251,7 @@ struct nrto_problem {
   bool graph_carry_after = false;
   bool linearized = false;
   bool warm_pending = false;
+  bool wlift_pending = false;    // nrto_set_warm_start_lifted since the warm start was set
   // A FullADMM inner solve ran since the last reset, so its final state can start the next one
   // (nrto_solver_opts.carry).
   bool carry_ok = false;
@@ -569,7 +570,10 @@ void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
   sp.fallback = o.warm_fallback;
   sp.kv_pcg_iters = o.solver == NRTO_SOLVER_FULLADMM ? o.kv_pcg_iters : 0;
   sp.kv_pcg_tol = o.kv_pcg_tol;
+  if (P->wlift_pending && o.solver != NRTO_SOLVER_FULLADMM)
+    fail(NRTO_ERR_STATE, "a lifted warm start applies to NRTO_SOLVER_FULLADMM only");
   P->warm_pending = false;
+  P->wlift_pending = false;
   if (o.solver == NRTO_SOLVER_FULLADMM) {
     k_gain_factors<Real><<<P->n, 128, 0, P->stream>>>(D, o.rho, 0.0, sp.warm);
     P->check_launch("k_gain_factors");
@@ -817,6 +821,8 @@ long long field_count(const Inst& I, int f) {
     case NRTO_F_GM: return (long long)I.T * I.nu * I.nu;
     case NRTO_F_SCAL: return 8;
     case NRTO_F_STATS: return 7;
+    case NRTO_F_LAMW: case NRTO_F_S: return I.n_sr + I.n_cr;
+    case NRTO_F_LAME: return (long long)(I.T + 1) * I.nx;
   }
   return -1;
 }
@@ -851,6 +857,9 @@ nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long 
       case NRTO_F_KACC: dptr = p->d_arena + I.arena0 + L.Kacc; break;
       case NRTO_F_DU: dptr = p->d_arena + I.arena0 + L.du; break;
       case NRTO_F_DX: dptr = p->d_arena + I.arena0 + L.dx; break;
+      case NRTO_F_LAMW: dptr = p->d_lamw + I.row0; break;
+      case NRTO_F_S: dptr = p->d_s + I.row0; break;
+      case NRTO_F_LAME: dptr = p->d_arena + I.arena0 + L.lam_e; break;
       case NRTO_F_BHAT: rptr = static_cast<char*>(p->d_bhat[sl]) + rs * I.ent0; break;
       case NRTO_F_BVEC: rptr = static_cast<char*>(p->d_bvec[sl]) + rs * I.bent0; break;
       case NRTO_F_LAMNU: rptr = static_cast<char*>(p->d_lam) + rs * I.ent0; break;
@@ -933,22 +942,39 @@ nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long 
 
 }  // namespace
 
-// Warm start from network outputs Y (device, n × out_dim): K from Y[i][k_off ..], p̃ and λ_p of
-// instance row r from Y[i][pt_off + map[r]] and Y[i][lp_off + map[r]] (map < 0: zero).
+// Warm start from network outputs Y (device, n × out_dim): K from Y[i][k ..], p̃ and λ_p of instance
+// row r from Y[i][pt + map[r]] and Y[i][lp + map[r]] (map < 0: zero).  With lifted offsets (th >= 0):
+// per row θ (clipped at 0, into D.dd) and λ_w, per instance δû (T·nu) and λ_e (steps 1..T, T·nx),
+// and the penalty exp(Y[i][rho]) (rho < 0: the solver's).
+struct WarmOffsets {
+  int k, pt, lp, th, lw, du, le, rho;
+};
 template <typename Real>
-__global__ void k_scatter_warm(Dev<Real> D, const float* Y, int out_dim, const int* map, int k_off, int pt_off,
-                               int lp_off) {
+__global__ void k_scatter_warm(Dev<Real> D, const float* Y, int out_dim, const int* map, WarmOffsets o) {
   const int i = blockIdx.x;
   const Inst I = D.inst[i];
   const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
   double* ar = D.arena + I.arena0;
   const float* y = Y + (long long)i * out_dim;
-  for (int q = threadIdx.x; q < I.T * I.nu * I.nx; q += blockDim.x) ar[L.K1 + q] = (double)y[k_off + q];
+  for (int q = threadIdx.x; q < I.T * I.nu * I.nx; q += blockDim.x) ar[L.K1 + q] = (double)y[o.k + q];
   for (int r = threadIdx.x; r < I.n_sr + I.n_cr; r += blockDim.x) {
     const long long R = I.row0 + r;
     const int m = map[R];
-    D.pt[R] = m >= 0 ? (double)y[pt_off + m] : 0.0;
-    D.lamp[R] = m >= 0 ? (double)y[lp_off + m] : 0.0;
+    D.pt[R] = m >= 0 ? (double)y[o.pt + m] : 0.0;
+    D.lamp[R] = m >= 0 ? (double)y[o.lp + m] : 0.0;
+    if (o.th >= 0) {
+      D.dd[R] = m >= 0 ? fmax((double)y[o.th + m], 0.0) : 0.0;
+      D.lamw[R] = m >= 0 ? (double)y[o.lw + m] : 0.0;
+    }
+  }
+  if (o.th < 0 && threadIdx.x == 0) D.is[i * NIS + IS_WLIFT] = 0;
+  if (o.th >= 0) {
+    for (int q = threadIdx.x; q < I.T * I.nu; q += blockDim.x) ar[L.du + q] = (double)y[o.du + q];
+    for (int q = threadIdx.x; q < I.T * I.nx; q += blockDim.x) ar[L.lam_e + I.nx + q] = (double)y[o.le + q];
+    if (threadIdx.x == 0) {
+      D.is[i * NIS + IS_WLIFT] = 1;
+      D.sc[(long long)i * NSC + SC_RHOW] = o.rho >= 0 ? exp((double)y[o.rho]) : 0.0;
+    }
   }
 }
 
@@ -1429,16 +1455,23 @@ nrto_status nrto_set_warm_start(nrto_problem_t p, const double* K, const double*
     if (!finite_arr(ptilde, p->n_rows) || !finite_arr(lambda_p, p->n_rows)) fail(NRTO_ERR_NUMERIC, "warm start not finite");
     CK(cudaMemcpyAsync(p->d_pt, ptilde, sizeof(double) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
     CK(cudaMemcpyAsync(p->d_lamp, lambda_p, sizeof(double) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
+    // a plain warm start replaces a lifted one that was not used
+    std::vector<int> is(p->n * NIS);
+    CK(cudaMemcpyAsync(is.data(), p->d_is, sizeof(int) * is.size(), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    for (int i = 0; i < p->n; ++i) is[i * NIS + IS_WLIFT] = 0;
+    CK(cudaMemcpyAsync(p->d_is, is.data(), sizeof(int) * is.size(), cudaMemcpyHostToDevice, p->stream));
     CK(cudaStreamSynchronize(p->stream));
     p->warm_pending = true;
+    p->wlift_pending = false;
     return NRTO_OK;
   } catch (const std::exception& e) {
     return handle(e);
   }
 }
 
-nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, const float* features,
-                                            const int* row_map, int k_off, int pt_off, int lp_off) {
+static nrto_status warm_from_network(nrto_problem_t p, nrto_mlp_t m, const float* features, const int* row_map,
+                                     WarmOffsets o) {
   try {
     if (!p || !m || !features || !row_map) fail(NRTO_ERR_INVALID, "null argument");
     for (long long r = 0; r < p->n_rows; ++r)
@@ -1447,24 +1480,96 @@ nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, con
     cudaStream_t ms = nullptr;
     const float* Y = nrto_mlp_internal_forward_device(m, features, p->n, &out_dim, &ms);
     if (!Y) return NRTO_ERR_INVALID;
-    long long kmax = 0;
-    for (int i = 0; i < p->n; ++i)
-      kmax = std::max(kmax, (long long)p->h_inst[i].T * p->h_inst[i].nu * p->h_inst[i].nx);
+    long long kmax = 0, umax = 0, xmax = 0;
+    for (int i = 0; i < p->n; ++i) {
+      const Inst& I = p->h_inst[i];
+      kmax = std::max(kmax, (long long)I.T * I.nu * I.nx);
+      umax = std::max(umax, (long long)I.T * I.nu);
+      xmax = std::max(xmax, (long long)I.T * I.nx);
+    }
     int mmax = -1;
     for (long long r = 0; r < p->n_rows; ++r) mmax = std::max(mmax, row_map[r]);
-    if (k_off < 0 || pt_off < 0 || lp_off < 0 || k_off + kmax > out_dim || pt_off + mmax >= out_dim ||
-        lp_off + mmax >= out_dim)
+    auto fits = [&](int off, long long n) { return off >= 0 && off + n <= out_dim; };
+    if (!fits(o.k, kmax) || !fits(o.pt, mmax + 1) || !fits(o.lp, mmax + 1))
       fail(NRTO_ERR_INVALID, "offsets and row map do not fit the network output");
+    if (o.th >= 0 && (!fits(o.th, mmax + 1) || !fits(o.lw, mmax + 1) || !fits(o.du, umax) || !fits(o.le, xmax) ||
+                      (o.rho >= 0 && !fits(o.rho, 1))))
+      fail(NRTO_ERR_INVALID, "lifted offsets do not fit the network output");
     if (!p->d_wsmap) p->d_wsmap = p->dalloc<int>(p->n_rows);
     CK(cudaMemcpyAsync(p->d_wsmap, row_map, sizeof(int) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
     CK(cudaStreamSynchronize(ms));   // network output ready
     if (p->prec == NRTO_PREC_FP64)
-      k_scatter_warm<double><<<p->n, 256, 0, p->stream>>>(p->dev<double>(), Y, out_dim, p->d_wsmap, k_off, pt_off, lp_off);
+      k_scatter_warm<double><<<p->n, 256, 0, p->stream>>>(p->dev<double>(), Y, out_dim, p->d_wsmap, o);
     else
-      k_scatter_warm<float><<<p->n, 256, 0, p->stream>>>(p->dev<float>(), Y, out_dim, p->d_wsmap, k_off, pt_off, lp_off);
+      k_scatter_warm<float><<<p->n, 256, 0, p->stream>>>(p->dev<float>(), Y, out_dim, p->d_wsmap, o);
     p->check_launch("k_scatter_warm");
     CK(cudaStreamSynchronize(p->stream));   // the network's output buffer may be reused after return
     p->warm_pending = true;
+    p->wlift_pending = o.th >= 0;
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    return handle(e);
+  }
+}
+
+nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, const float* features,
+                                            const int* row_map, int k_off, int pt_off, int lp_off) {
+  return warm_from_network(p, m, features, row_map, WarmOffsets{k_off, pt_off, lp_off, -1, -1, -1, -1, -1});
+}
+
+nrto_status nrto_set_warm_start_from_network_lifted(nrto_problem_t p, nrto_mlp_t m, const float* features,
+                                                    const int* row_map, const int* offsets) {
+  if (!offsets) {
+    g_last_error = "null offsets";
+    return NRTO_ERR_INVALID;
+  }
+  if (offsets[3] < 0 || offsets[4] < 0 || offsets[5] < 0 || offsets[6] < 0) {
+    g_last_error = "the lifted offsets (theta, lambda_w, du, lambda_e) must be >= 0";
+    return NRTO_ERR_INVALID;
+  }
+  return warm_from_network(p, m, features, row_map,
+                           WarmOffsets{offsets[0], offsets[1], offsets[2], offsets[3], offsets[4], offsets[5], offsets[6],
+                                       offsets[7]});
+}
+
+nrto_status nrto_set_warm_start_lifted(nrto_problem_t p, const double* theta, const double* lambda_w, const double* du,
+                                       const double* lambda_e, const double* rho) {
+  try {
+    if (!p || !theta || !lambda_w || !du || !lambda_e) fail(NRTO_ERR_INVALID, "null argument");
+    if (!p->warm_pending) fail(NRTO_ERR_STATE, "nrto_set_warm_start must come first");
+    if (!finite_arr(theta, p->n_rows) || !finite_arr(lambda_w, p->n_rows) || !finite_arr(du, p->u_total))
+      fail(NRTO_ERR_NUMERIC, "lifted warm start not finite");
+    long long xtot = 0;
+    for (const Inst& I : p->h_inst) xtot += (long long)I.T * I.nx;
+    if (!finite_arr(lambda_e, xtot)) fail(NRTO_ERR_NUMERIC, "lifted warm start not finite");
+    if (rho)
+      for (int i = 0; i < p->n; ++i)
+        if (!(rho[i] > 0) || !std::isfinite(rho[i])) fail(NRTO_ERR_INVALID, "warm-start penalties must be positive");
+    std::vector<double> th(theta, theta + p->n_rows);
+    for (double& v : th) v = std::max(v, 0.0);
+    std::vector<int> is(p->n * NIS);
+    std::vector<double> sc(p->n * NSC);
+    CK(cudaMemcpyAsync(is.data(), p->d_is, sizeof(int) * is.size(), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(sc.data(), p->d_sc, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaMemcpyAsync(p->d_dd, th.data(), sizeof(double) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->d_lamw, lambda_w, sizeof(double) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
+    long long xo = 0;
+    for (int i = 0; i < p->n; ++i) {
+      const Inst& I = p->h_inst[i];
+      const Arena L = arena_layout(I.nx, I.nu, I.T, I.n_obs, I.n_link);
+      double* ar = p->d_arena + I.arena0;
+      CK(cudaMemcpyAsync(ar + L.du, du + p->uoff[i], sizeof(double) * I.T * I.nu, cudaMemcpyHostToDevice, p->stream));
+      CK(cudaMemcpyAsync(ar + L.lam_e + I.nx, lambda_e + xo, sizeof(double) * I.T * I.nx, cudaMemcpyHostToDevice,
+                         p->stream));
+      xo += (long long)I.T * I.nx;
+      is[i * NIS + IS_WLIFT] = 1;
+      sc[(size_t)i * NSC + SC_RHOW] = rho ? rho[i] : 0.0;
+    }
+    CK(cudaMemcpyAsync(p->d_is, is.data(), sizeof(int) * is.size(), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->d_sc, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    p->wlift_pending = true;
     return NRTO_OK;
   } catch (const std::exception& e) {
     return handle(e);

@@ -1399,6 +1399,9 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   // A previous solve that ended on a non-finite residual or a copy timeout is not carried. ----
   const bool carry = carry_applies(D.is, inst, sp.warm);
   const int winit = carry ? 2 : (sp.warm == 1 ? 1 : 0);
+  // lifted warm start (with winit 1): λ_w, δû and λ_e are given as well, λ_ν follows from the
+  // per-row factors θ (in D.dd) and the warm gains, δx = F_u δû and ℓ from δû
+  const bool lifted = winit == 1 && isr[IS_WLIFT] != 0;
   const bool keep_dx = carry && isr[IS_MOVED] == 0;
   if (tid == 0) isr[IS_PCG] = 0;
   if (winit != 2)
@@ -1407,15 +1410,16 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     const long long R = I.row0 + r;
     if (winit == 0) { D.p[R] = 0.0; D.pt[R] = 0.0; D.lamp[R] = 0.0; }
     else if (winit == 1) { D.p[R] = D.pt[R]; }
-    if (winit != 2) D.lamw[R] = 0.0;
+    if (winit != 2 && !lifted) D.lamw[R] = 0.0;
     if (!keep_dx) D.ell[R] = 0.0;
     D.w[R] = 0.0; D.s[R] = 1.0; D.sr[R] = (Real)1;
   }
   if (!keep_dx) {
-    for (int q = tid; q < T * NU; q += NT) ar[L.du + q] = 0.0;
+    if (!lifted)
+      for (int q = tid; q < T * NU; q += NT) ar[L.du + q] = 0.0;
     for (int q = tid; q < (T + 1) * NX; q += NT) { ar[L.dx + q] = 0.0; ar[L.e + q] = 0.0; }
   }
-  if (winit != 2)
+  if (winit != 2 && !lifted)
     for (int q = tid; q < (T + 1) * NX; q += NT) ar[L.lam_e + q] = 0.0;
   if (winit == 0)
     for (int q = tid; q < T * NU * NX; q += NT) ar[L.K1 + q] = 0.0;
@@ -1424,8 +1428,46 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
     // this solve factored block 2 and the gain divisors for it (start_rho)
     rho = sc[SC_RHOD];
     rho_done = rho;
+  } else if (lifted && sc[SC_RHOW] > 0.0) {
+    rho = sc[SC_RHOW];   // the lifted warm start's penalty (start_rho, as for the factors)
+    rho_done = rho;
   }
   __syncthreads();
+  if (lifted) {
+    // δx_0 = 0, δx_{k+1} = A_k δx_k + B_k δu_k (warp 0; lane j < NX owns δx_j)
+    if (warp == 0) {
+      double x = 0.0;
+      const int lane = tid & 31;
+      for (int k = 0; k < T; ++k) {
+        double xn = 0.0;
+        const double* A = sa + SL.A + (long long)k * NX * NX;
+        const double* B = sa + SL.B + (long long)k * NX * NU;
+        for (int j = 0; j < NX; ++j) {
+          const double xj = __shfl_sync(0xffffffffu, x, j);
+          if (lane < NX) xn += A[lane * NX + j] * xj;
+        }
+        if (lane < NX) {
+          for (int u = 0; u < NU; ++u) xn += B[lane * NU + u] * ar[L.du + (long long)k * NU + u];
+          ar[L.dx + (long long)(k + 1) * NX + lane] = xn;
+        }
+        x = xn;
+      }
+    }
+    __syncthreads();
+    // ℓ_j = b_jᵀδû: a_j · δx_t for state rows, ±δu_{k,i} for control rows
+    for (int r = tid; r < n_rows; r += NT) {
+      const long long R = I.row0 + r;
+      const int4 ri = D.rinfo[R];
+      double eln = 0.0;
+      if (r < I.n_sr) {
+        for (int c = 0; c < NX; ++c) eln += S.arow[I.arow0 + (long long)r * NX + c] * ar[L.dx + (long long)ri.x * NX + c];
+      } else {
+        eln = ((ri.y == ROW_UHI) ? 1.0 : -1.0) * ar[L.du + (long long)ri.x * NU + ri.z];
+      }
+      D.ell[R] = eln;
+    }
+    if (tid == 0) isr[IS_WLIFT] = 0;
+  }
   // Gtᵀ of the initial gains into Gt1 ("current"); Gt0 is the "previous" table
   for (int q = tid; q < (T + 1) * NU * NX; q += NT) {
     const int m = q / (NU * NX), u = (q / NX) % NU, c = q % NX;
@@ -1437,6 +1479,31 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
   }
   if (tid == 0) { sc[SC_SCAL_RP] = 0; sc[SC_SCAL_RD] = 0; sc[SC_SCAL_RPP] = 0; sc[SC_SCAL_RDP] = 0; }
   __syncthreads();
+  if (lifted) {
+    // λ_ν,j = θ_j (Â_j k + b̂_j) from the warm gains' table (a warp per row, lanes over its entries)
+    const int lane = tid & 31;
+    for (int r = warp; r < n_rows; r += NT / 32) {
+      const long long R = I.row0 + r;
+      const double th = D.dd[R];
+      if (!(th > 0.0)) continue;
+      const int4 ri = D.rinfo[R];
+      const long long e0 = D.rent[R];
+      if (r < I.n_sr) {
+        const long long b0 = D.rbent[R];
+        for (int q = lane; q < (ri.x + 1) * NX; q += 32) {
+          const int m = q / NX, c = q - m * NX;
+          double y = (double)S.bhat[e0 + q];
+          for (int u = 0; u < NU; ++u) y += ar[L.Gt1 + (long long)m * NU * NX + u * NX + c] * (double)S.bvec[b0 + (long long)m * NU + u];
+          lam[e0 + q] = (Real)(th * y);
+        }
+      } else {
+        const double sg = (ri.y == ROW_UHI) ? 1.0 : -1.0;
+        for (int c = lane; c < NX; c += 32)
+          lam[e0 + c] = (Real)(th * sg * ar[L.Gt1 + (long long)ri.x * NU * NX + ri.z * NX + c]);
+      }
+    }
+    __syncthreads();
+  }
   tm.mark(PH_INIT);
   int gsel = 1;           // arena table holding Gtᵀ of the current gains (other one: previous)
   const int Lmax = sp.max_iter;
@@ -1659,7 +1726,7 @@ __global__ void __launch_bounds__(FACfg<NX, NU, Real>::NT, FACfg<NX, NU, Real>::
       {
         // residual balancing or a carried penalty may have refactored block 2 and the gain
         // divisors for another ρ
-        if (sp.adapt_every > 0 || sp.warm == 2) {
+        if (sp.adapt_every > 0 || sp.warm != 0) {
           gain_divisors<Real>(D, inst, sp.rho);
           __syncthreads();
           if ((threadIdx.x >> 5) == 0) riccati_factor_warp<Real>(D, inst, sp.rho, ric_scr);

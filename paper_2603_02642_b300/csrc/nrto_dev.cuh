@@ -125,12 +125,15 @@ NRTO_HD SlotL slot_layout(int nx, int nu, int T) {
 // SC_RHOD: the penalty the stored scaled duals are scaled for (the start penalty of a carried inner
 // solve); SC_VIOL / SC_VIOLC: max_j g_j(x̄) + ‖Â_j k + b̂_j‖ of the accepted / candidate iterate.
 enum : int { SC_RTRUST = 0, SC_RP, SC_RD, SC_RPP, SC_RDP, SC_SCAL_RP, SC_SCAL_RD, SC_SCAL_RPP, SC_SCAL_RDP,
-             SC_PHI, SC_PHI_CAND, SC_COST, SC_RHO, SC_RDR, SC_RHOD, SC_VIOL, SC_VIOLC, SC_COST_ACC, NSC = 20 };
+             SC_PHI, SC_PHI_CAND, SC_COST, SC_RHO, SC_RDR, SC_RHOD, SC_VIOL, SC_VIOLC, SC_COST_ACC,
+             SC_RHOW,   // penalty of a pending lifted warm start (0: the solver's)
+             NSC = 20 };
 // IS_ACCST: status of the inner solve whose candidate became the accepted iterate (0: none yet);
 // IS_MOVED: the nominal moved to û + δû since the last inner solve (an accepted outer step).
 // IS_PCG: PCG iterations of the k_v updates of the last inner solve (kv_pcg_iters > 0).
+// IS_WLIFT: a lifted warm start (θ, λ_w, δû, λ_e, ρ) is pending for the next FullADMM inner solve.
 enum : int { IS_STATUS = 0, IS_ITERS, IS_SLOT, IS_ACCEPT, IS_DRITERS, IS_CUMITERS, IS_NACC, IS_FALLBACK, IS_ACCST,
-             IS_MOVED, IS_PCG, NIS = 11 };
+             IS_MOVED, IS_PCG, IS_WLIFT, NIS = 12 };
 
 template <typename Real>
 struct LinSlot {
@@ -171,9 +174,15 @@ __device__ __forceinline__ bool carry_applies(const int* is, int i, int warm) {
   const int st = is[i * NIS + IS_STATUS];
   return warm == 2 && (st == ST_CONVERGED || st == ST_MAXITER || st == ST_STALLED);
 }
-// Penalty the inner solve of instance i starts with: the carried one, else rho0.
+// A pending lifted warm start with its own penalty (warm mode 1).
+__device__ __forceinline__ bool lifted_warm_rho(const int* is, const double* sc, int i, int warm) {
+  return warm == 1 && is[i * NIS + IS_WLIFT] != 0 && sc[(long long)i * NSC + SC_RHOW] > 0.0;
+}
+// Penalty the inner solve of instance i starts with: the carried one, a lifted warm start's, else rho0.
 __device__ __forceinline__ double start_rho(const int* is, const double* sc, int i, int warm, double rho0) {
-  return carry_applies(is, i, warm) ? sc[(long long)i * NSC + SC_RHOD] : rho0;
+  if (carry_applies(is, i, warm)) return sc[(long long)i * NSC + SC_RHOD];
+  if (lifted_warm_rho(is, sc, i, warm)) return sc[(long long)i * NSC + SC_RHOW];
+  return rho0;
 }
 
 // Phases of one inner iteration timed by the persistent solvers (thread 0 of each CTA, SM cycles).

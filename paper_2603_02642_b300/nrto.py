@@ -18,7 +18,7 @@ NMAPPING = 4  # NRTO_NMAPPING
 SOLVER_DR, SOLVER_FULLADMM, SOLVER_FULLADMM_AW = 0, 1, 2
 
 (F_XHAT, F_UHAT, F_A, F_B, F_G0, F_BHAT, F_BVEC, F_LAMNU, F_K, F_DU, F_P, F_PT, F_LAMP, F_GM, F_KACC,
- F_DX, F_SCAL, F_STATS) = range(18)
+ F_DX, F_SCAL, F_STATS, F_LAMW, F_LAME, F_S) = range(21)
 
 STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "NOT_CONVERGED", 4: "NUMERIC", 5: "TIMEOUT", 6: "STATE"}
 
@@ -118,6 +118,10 @@ def load():
     lib.nrto_graph_info.restype = C.c_int
     lib.nrto_get_stats.argtypes = [P, _dp, C.c_int]
     lib.nrto_get_stats.restype = C.c_int
+    lib.nrto_set_warm_start_lifted.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
+    lib.nrto_set_warm_start_lifted.restype = C.c_int
+    lib.nrto_set_warm_start_from_network_lifted.argtypes = [P, P, C.POINTER(C.c_float), _ip, _ip]
+    lib.nrto_set_warm_start_from_network_lifted.restype = C.c_int
     lib.nrto_monte_carlo.argtypes = [P, _dp, C.c_int, C.c_int, C.c_ulonglong, C.c_double, _ip, _dp]
     lib.nrto_monte_carlo.restype = C.c_int
     lib.nrto_kernel_launches.argtypes = [P]
@@ -220,6 +224,7 @@ class Problem:
         F_BHAT: lambda x: x.n_entries_state, F_BVEC: lambda x: x.n_entries_state // x.nx * x.nu,
         F_LAMNU: lambda x: x.n_entries, F_K: lambda x: x.T * x.nu * x.nx, F_KACC: lambda x: x.T * x.nu * x.nx,
         F_GM: lambda x: x.T * x.nu * x.nu, F_SCAL: lambda x: 8, F_STATS: lambda x: 7,
+        F_LAMW: lambda x: x.n_rows, F_S: lambda x: x.n_rows, F_LAME: lambda x: (x.T + 1) * x.nx,
     }
 
     def __init__(self, instances, precision=PREC_FP64, stream=None):
@@ -317,6 +322,24 @@ class Problem:
         pt = np.ascontiguousarray(np.concatenate([np.asarray(k).reshape(-1) for k in pt]))
         lp = np.ascontiguousarray(np.concatenate([np.asarray(k).reshape(-1) for k in lam_p]))
         _check(load().nrto_set_warm_start(self._h, _ptr(K), _ptr(pt), _ptr(lp)))
+
+    def set_warm_start_lifted(self, theta, lam_w, du, lam_e, rho=None):
+        """The lifted warm start (nrto_set_warm_start_lifted) after set_warm_start: per instance θ and
+        λ_w per row, δû (T, nu), λ_e (T, nx) for steps 1..T, and optionally the penalty per instance."""
+        cat = lambda a: np.ascontiguousarray(np.concatenate([np.asarray(k, dtype=np.float64).reshape(-1) for k in a]))
+        r = None if rho is None else np.ascontiguousarray(np.broadcast_to(np.asarray(rho, dtype=np.float64), (self.n,)).copy())
+        _check(load().nrto_set_warm_start_lifted(self._h, _ptr(cat(theta)), _ptr(cat(lam_w)), _ptr(cat(du)),
+                                                 _ptr(cat(lam_e)), _ptr(r)))
+
+    def set_warm_start_from_network_lifted(self, net, features, row_map, offsets):
+        """Network forward on the device and scatter into the lifted warm start; offsets of K, p̃, λ_p,
+        θ, λ_w, δû, λ_e and log ρ (-1: the solver's ρ) in the network output."""
+        f = np.ascontiguousarray(np.asarray(features, dtype=np.float32))
+        m = np.ascontiguousarray(np.asarray(row_map, dtype=np.int32))
+        o = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+        assert f.shape[0] == self.n and m.size == self.n_rows() and o.size == 8
+        _check(load().nrto_set_warm_start_from_network_lifted(self._h, net._h, f.ctypes.data_as(C.POINTER(C.c_float)),
+                                                              m.ctypes.data_as(_ip), o.ctypes.data_as(_ip)))
 
     def set_warm_start_from_network(self, net, features, row_map, k_off, pt_off, lp_off):
         """Network forward on the device and scatter into the next inner solve's (K, p̃, λ_p)."""

@@ -3,14 +3,19 @@ spherical obstacles).
 
 The paper names learning a warm start as future work; this module is the library's version.
 A GELU MLP (nrto.MLP: tcgen05 kernels) maps an instance's parameters to the inner solver's initial
-(k_v, p̃, λ_p); λ_ν starts at zero (so ν = Π(Â k + b̂)).  Training targets are the converged
-iterates of the cold-started solver at the first outer step.
+(k_v, p̃, λ_p), with λ_ν starting at zero (so ν = Π(Â k + b̂)), or, in the lifted layout, to the
+whole state of the lifted iteration.  Training targets are the converged iterates of the
+cold-started solver at the first outer step.
 
 Layouts (fixed; obstacles padded to 15 and masked):
   features (99) = x̄_0 (12) | goal (12) | 15 × (centre (3), radius) | obstacle mask (15)
   outputs (9400) = K (T·n_u·n_x = 4800, the library's [m][u][c] layout)
                  | p̃ (2300) | λ_p (2300), each over rows: state rows (t-1)·15 + o, then the 800
                    control-bound rows in the library's order (step k, input i, upper before lower).
+  lifted outputs (15608) = the 9400 above | θ (2300) | λ_w (2300) over the same rows | δû (T·n_u)
+                 | λ_e (T·n_x, steps 1..T) | log ρ | 7 unused: the rest of the lifted iteration's state
+                   (nrto_set_warm_start_lifted), with λ_ν = θ (Â k + b̂) and θ = 1/s - 1 from the
+                   rows' projection scales.
 The feature standardization and the target scaling learned on the training set are folded into the
 first and last layers, so the deployed network maps raw features to raw solver values.  This module
 only arranges data; every arithmetic step of training and inference runs in the library's kernels.
@@ -29,6 +34,14 @@ N_ROWS = N_STATE + N_CTRL
 N_OUT = N_K + 2 * N_ROWS
 N_IN = 12 + 12 + 4 * N_OBS_MAX + N_OBS_MAX
 DIMS = [N_IN, 256, 256, 256, N_OUT]
+# lifted layout: offsets of θ, λ_w, δû, λ_e, log ρ after the plain outputs
+O_TH, O_LW = N_OUT, N_OUT + N_ROWS
+O_DU = N_OUT + 2 * N_ROWS
+O_LE = O_DU + T * NU
+O_RHO = O_LE + T * NX
+N_OUT_LIFTED = (O_RHO + 1 + 7) // 8 * 8   # the network's widths are multiples of 8 (7 unused outputs)
+DIMS_LIFTED = [N_IN, 256, 256, 256, N_OUT_LIFTED]
+THETA_MAX = 100.0   # targets θ = 1/s - 1 clipped (a row projected almost to zero)
 
 
 def _check_inst(inst):
@@ -61,12 +74,15 @@ def row_index(inst):
     return np.concatenate([state, ctrl])
 
 
-def collect_targets(prob, insts, statuses):
-    """(features, targets, masks) of the instances whose inner solve converged (status 1)."""
+def collect_targets(prob, insts, statuses, lifted=False):
+    """(features, targets, masks) of the instances whose inner solve converged (status 1); with
+    `lifted`, the lifted layout's targets as well (θ from the projection scales, the final ρ)."""
     keep = [i for i in range(len(insts)) if statuses[i] == 1]
     X = features([insts[i] for i in keep])
-    Y = np.zeros((len(keep), N_OUT), dtype=np.float32)
-    Mk = np.zeros((len(keep), N_OUT), dtype=np.float32)
+    n_out = N_OUT_LIFTED if lifted else N_OUT
+    Y = np.zeros((len(keep), n_out), dtype=np.float32)
+    Mk = np.zeros((len(keep), n_out), dtype=np.float32)
+    rho = prob.stats()["rho"] if lifted else None
     for r, i in enumerate(keep):
         idx = row_index(insts[i])
         Y[r, :N_K] = prob.export(nrto.F_K, i)
@@ -75,25 +91,39 @@ def collect_targets(prob, insts, statuses):
         Y[r, N_K + N_ROWS + idx] = prob.export(nrto.F_LAMP, i)
         Mk[r, N_K + idx] = 1.0
         Mk[r, N_K + N_ROWS + idx] = 1.0
+        if lifted:
+            sc = prob.export(nrto.F_S, i)
+            th = np.where(sc > 0.0, 1.0 / np.where(sc > 0.0, sc, 1.0) - 1.0, 0.0)
+            Y[r, O_TH + idx] = np.clip(th, 0.0, THETA_MAX)
+            Y[r, O_LW + idx] = prob.export(nrto.F_LAMW, i)
+            Y[r, O_DU:O_DU + T * NU] = prob.export(nrto.F_DU, i)
+            Y[r, O_LE:O_LE + T * NX] = prob.export(nrto.F_LAME, i)[NX:]
+            Y[r, O_RHO] = np.log(rho[i])
+            Mk[r, O_TH + idx] = 1.0
+            Mk[r, O_LW + idx] = 1.0
+            Mk[r, O_DU:O_RHO + 1] = 1.0
     return X, Y, Mk
 
 
 class WarmStart:
     """Train and apply the warm-start network."""
 
-    def __init__(self, max_batch=4096, seed=0, stream=None):
-        self.net = nrto.MLP(DIMS, max_batch=max_batch, stream=stream)
+    def __init__(self, max_batch=4096, seed=0, stream=None, lifted=False):
+        self.lifted = lifted
+        dims = DIMS_LIFTED if lifted else DIMS
+        self.n_out = dims[-1]
+        self.net = nrto.MLP(dims, max_batch=max_batch, stream=stream)
         rng = np.random.default_rng(seed)
         flat = []
-        for din, dout in zip(DIMS[:-1], DIMS[1:]):
+        for din, dout in zip(dims[:-1], dims[1:]):
             s = 1.0 / np.sqrt(din)
             flat.append(rng.uniform(-s, s, size=dout * din))
             flat.append(rng.uniform(-s, s, size=dout))
         self.net.set_params(np.concatenate(flat).astype(np.float32))
         self.x_mu = np.zeros(N_IN)
         self.x_sd = np.ones(N_IN)
-        self.y_mu = np.zeros(N_OUT)
-        self.y_sd = np.ones(N_OUT)
+        self.y_mu = np.zeros(self.n_out)
+        self.y_sd = np.ones(self.n_out)
         self.deployed = False
 
     def fit(self, X, Y, Mk, steps=2000, batch=256, lr=1e-3, seed=0):
@@ -142,7 +172,11 @@ class WarmStart:
         out = []
         for i, inst in enumerate(insts):
             idx = row_index(inst)
-            out.append((Y[i, :N_K].reshape(T, NU, NX), Y[i, N_K + idx], Y[i, N_K + N_ROWS + idx]))
+            o = (Y[i, :N_K].reshape(T, NU, NX), Y[i, N_K + idx], Y[i, N_K + N_ROWS + idx])
+            if self.lifted:
+                o = o + (np.maximum(Y[i, O_TH + idx], 0.0), Y[i, O_LW + idx], Y[i, O_DU:O_DU + T * NU].reshape(T, NU),
+                         Y[i, O_LE:O_LE + T * NX].reshape(T, NX), float(np.exp(Y[i, O_RHO])))
+            out.append(o)
         return out
 
     def apply(self, prob, insts):
@@ -151,7 +185,11 @@ class WarmStart:
         if not self.deployed:
             raise RuntimeError("fit() the network first")
         row_map = np.concatenate([row_index(inst) for inst in insts]).astype(np.int32)
-        prob.set_warm_start_from_network(self.net, features(insts), row_map, 0, N_K, N_K + N_ROWS)
+        if self.lifted:
+            prob.set_warm_start_from_network_lifted(self.net, features(insts), row_map,
+                                                    [0, N_K, N_K + N_ROWS, O_TH, O_LW, O_DU, O_LE, O_RHO])
+        else:
+            prob.set_warm_start_from_network(self.net, features(insts), row_map, 0, N_K, N_K + N_ROWS)
 
     def apply_host(self, prob, insts):
         """Same warm start through host arrays (predict, then nrto_set_warm_start)."""
@@ -160,4 +198,7 @@ class WarmStart:
         pt = np.concatenate([p[1] for p in pred])
         lp = np.concatenate([p[2] for p in pred])
         prob.set_warm_start(K, pt, lp)
+        if self.lifted:
+            prob.set_warm_start_lifted([p[3] for p in pred], [p[4] for p in pred], [p[5] for p in pred],
+                                       [p[6] for p in pred], [p[7] for p in pred])
         return pred
