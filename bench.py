@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--r0", type=float, default=0.5, help="initial and largest trust radius of the outer loop")
     ap.add_argument("--w-p", type=float, default=1000.0, help="merit weight of the robust-constraint violation")
     ap.add_argument("--mc", type=int, default=1000, help="Monte Carlo interior and edge samples per instance")
+    ap.add_argument("--warm-train", type=int, default=2048, help="training solves of the learned warm start")
+    ap.add_argument("--warm-eval", type=int, default=1024, help="held-out instances of the learned warm start")
     ap.add_argument("--plain-n", type=int, default=16, help="instances of the plain batch-1 FP64 arm")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -461,30 +463,36 @@ def single_configs(args, stream):
     return out
 
 
-def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
+def warm_start_study(stream, n_train=2048, n_eval=1024, n_infer=4096, steps=1000):
     """Learned warm start on the quadcopter workload (T = 100, 1-15 obstacles): targets from cold
-    FullADMM solves of the first outer step, training by the library's kernels, then cold vs
-    warm-started solves (to full residuals <= 1e-4, <= 5000 iterations, residual balancing every 25)
-    of held-out instances, and the network's tensor-core GEMM rate on an inference batch."""
+    FullADMM solves (to full residuals <= 1e-4, <= 5000 iterations, residual balancing every 25) at
+    the first outer step, one network in the lifted layout trained on them, and cold, warm (its
+    (k_v, p̃, λ_p)) and lifted warm-started solves (plus its δû, the lifted part that pays) of
+    held-out instances, the lifted one also with the cold fallback; the network's tensor-core GEMM
+    rate on an inference batch."""
     import torch
     from paper_2603_02642_b300 import nrto, warmstart as WS, workloads as W
     opts = dict(rho=10.0, max_inner=5000, eps_p=1e-4, eps_d=1e-4, check=1, adapt_every=25)
     t0 = time.perf_counter()
-    train = [W.warmstart_quad(s) for s in range(n_train)]
-    prob = nrto.Problem(train, nrto.PREC_MIXED, stream=stream.cuda_stream)
-    prob.linearize()
-    prob.set_trust_radius(2.0)
-    out = prob.solve_socp(nrto.Options(**opts))
-    X, Y, Mk = WS.collect_targets(prob, train, out["status"])
-    prob.close()
+    Xs, Ys, Ms = [], [], []
+    for s0 in range(0, n_train, 2048):
+        train = [W.warmstart_quad(s) for s in range(s0, min(n_train, s0 + 2048))]
+        prob = nrto.Problem(train, nrto.PREC_MIXED, stream=stream.cuda_stream)
+        prob.linearize()
+        prob.set_trust_radius(2.0)
+        out = prob.solve_socp(nrto.Options(**opts))
+        X, Y, Mk = WS.collect_targets(prob, train, out["status"], lifted=True)
+        prob.close()
+        Xs.append(X); Ys.append(Y); Ms.append(Mk)
+    X, Y, Mk = np.concatenate(Xs), np.concatenate(Ys), np.concatenate(Ms)
     t_data = time.perf_counter() - t0
-    ws = WS.WarmStart(max_batch=n_infer, stream=stream.cuda_stream)
+    ws = WS.WarmStart(max_batch=max(n_infer, n_eval), stream=stream.cuda_stream, lifted=True)
     t0 = time.perf_counter()
     hist = ws.fit(X, Y, Mk, steps=steps, batch=256, lr=1e-3)
     t_fit = time.perf_counter() - t0
     test = [W.warmstart_quad(1_000_000 + s) for s in range(n_eval)]
     res = {}
-    for mode in ("cold", "warm", "warm_fallback"):
+    for mode in ("cold", "warm", "lifted", "lifted_fallback"):
         q = nrto.Problem(test, nrto.PREC_MIXED, stream=stream.cuda_stream)
         q.linearize()
         q.set_trust_radius(2.0)
@@ -492,9 +500,9 @@ def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         if mode != "cold":
-            ws.apply(q, test)
+            ws.apply(q, test, lifted=mode != "warm")
         e1.record(stream)
-        fbk = mode == "warm_fallback"
+        fbk = mode == "lifted_fallback"
         o = q.solve_socp(nrto.Options(stall_every=1000 if fbk else 0, stall_ratio=0.99, warm_fallback=int(fbk),
                                       **opts))
         e2.record(stream)
@@ -503,7 +511,7 @@ def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
         res[mode] = dict(iters=o["iters"].copy(), conv=o["status"] == 1, solve_ms=e1.elapsed_time(e2),
                          predict_ms=e0.elapsed_time(e1), fallbacks=fb)
         q.close()
-    both = res["cold"]["conv"] & res["warm"]["conv"] & res["warm_fallback"]["conv"]
+    both = np.logical_and.reduce([r["conv"] for r in res.values()])
     feats = WS.features([W.warmstart_quad(2_000_000 + s) for s in range(n_infer)])
     ws.net.forward(feats)
     ws.net.profile(True)
@@ -518,21 +526,27 @@ def warm_start_study(stream, n_train=512, n_eval=256, n_infer=4096, steps=1000):
         d = {"converged": int(r["conv"].sum()), "solve_ms": r["solve_ms"],
              "solves_per_s": n_eval / (total_ms / 1e3),
              "converged_per_s": int(r["conv"].sum()) / (total_ms / 1e3),
-             "iters_mean_all_converged": float(r["iters"][both].mean()) if both.any() else None}
+             "iters_mean_all_converged": float(r["iters"][both].mean()) if both.any() else None,
+             "iters_median_all_converged": float(np.median(r["iters"][both])) if both.any() else None}
         if warm:
             d["predict_ms"] = r["predict_ms"]
             d["fallbacks"] = r["fallbacks"]
         return d
 
+    cold_it = res["cold"]["iters"][both]
     return {
         "workload": f"quadcopter T=100, 1-15 obstacles (warmstart_quad); train seeds 0..{n_train - 1}, "
                     f"held-out seeds 1000000..{1000000 + n_eval - 1}",
+        "network": "99 -> 256 -> 256 -> 256 -> 15608 (lifted layout), GELU, bf16 tcgen05 GEMMs",
         "targets": int(X.shape[0]), "train_steps": steps, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
         "data_s": round(t_data, 2), "fit_s": round(t_fit, 2),
-        "held_out": n_eval, "converged_in_all_three": int(both.sum()),
+        "held_out": n_eval, "converged_in_all_modes": int(both.sum()),
         "cold": summary(res["cold"], False),
         "warm": summary(res["warm"], True),
-        "warm_fallback": summary(res["warm_fallback"], True),
+        "lifted": summary(res["lifted"], True),
+        "lifted_fallback": summary(res["lifted_fallback"], True),
+        "iteration_ratio_vs_cold": {m: float(res[m]["iters"][both].mean() / max(cold_it.mean(), 1e-30))
+                                    for m in ("warm", "lifted", "lifted_fallback")} if both.any() else None,
         "mlp_roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "peak_source": peak_kind + " (burst)", "batch": n_infer,
                          "gemm_launches": int(gn), "gemm_ms": gms},
@@ -720,7 +734,7 @@ def main():
             cfgs = single_configs(args, stream)
     prob.close()
     if rank == 0 and not args.no_warm:
-        warm = warm_start_study(stream)
+        warm = warm_start_study(stream, n_train=args.warm_train, n_eval=args.warm_eval)
     if rank == 0 and not args.no_cpu:
         cpu = oracle_estimate(insts, args)
     clocks = clocks_summary(clk_path, local)

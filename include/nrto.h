@@ -238,7 +238,8 @@ nrto_status nrto_set_warm_start_from_network(nrto_problem_t p, nrto_mlp_t m, con
 
 /* The lifted warm start (nrto_set_warm_start_lifted) from the network in one call: offsets (host,
  * 8 ints) into output[i]: K, p̃, λ_p as above, then per row θ (clipped at 0) and λ_w through row_map,
- * δû (T*nu), λ_e (T*nx, steps 1..T), and log ρ (offsets[7] < 0: the solver's ρ). */
+ * δû (T*nu), λ_e (T*nx, steps 1..T), and log ρ.  A lifted part whose offset is < 0 is absent (zero;
+ * for ρ the solver's); with all five absent this is nrto_set_warm_start_from_network. */
 nrto_status nrto_set_warm_start_from_network_lifted(nrto_problem_t p, nrto_mlp_t m, const float* features,
                                                     const int* row_map, const int* offsets);
 

@@ -943,11 +943,12 @@ nrto_status exchange(nrto_problem_t p, int field, int i, double* buf, long long 
 }  // namespace
 
 // Warm start from network outputs Y (device, n × out_dim): K from Y[i][k ..], p̃ and λ_p of instance
-// row r from Y[i][pt + map[r]] and Y[i][lp + map[r]] (map < 0: zero).  With lifted offsets (th >= 0):
-// per row θ (clipped at 0, into D.dd) and λ_w, per instance δû (T·nu) and λ_e (steps 1..T, T·nx),
-// and the penalty exp(Y[i][rho]) (rho < 0: the solver's).
+// row r from Y[i][pt + map[r]] and Y[i][lp + map[r]] (map < 0: zero).  Lifted parts, each absent
+// (zero; the solver's ρ) when its offset is < 0: per row θ (clipped at 0, into D.dd) and λ_w, per
+// instance δû (T·nu) and λ_e (steps 1..T, T·nx), and the penalty exp(Y[i][rho]).
 struct WarmOffsets {
   int k, pt, lp, th, lw, du, le, rho;
+  NRTO_HD bool lifted() const { return th >= 0 || lw >= 0 || du >= 0 || le >= 0 || rho >= 0; }
 };
 template <typename Real>
 __global__ void k_scatter_warm(Dev<Real> D, const float* Y, int out_dim, const int* map, WarmOffsets o) {
@@ -962,15 +963,16 @@ __global__ void k_scatter_warm(Dev<Real> D, const float* Y, int out_dim, const i
     const int m = map[R];
     D.pt[R] = m >= 0 ? (double)y[o.pt + m] : 0.0;
     D.lamp[R] = m >= 0 ? (double)y[o.lp + m] : 0.0;
-    if (o.th >= 0) {
-      D.dd[R] = m >= 0 ? fmax((double)y[o.th + m], 0.0) : 0.0;
-      D.lamw[R] = m >= 0 ? (double)y[o.lw + m] : 0.0;
+    if (o.lifted()) {
+      D.dd[R] = (m >= 0 && o.th >= 0) ? fmax((double)y[o.th + m], 0.0) : 0.0;
+      D.lamw[R] = (m >= 0 && o.lw >= 0) ? (double)y[o.lw + m] : 0.0;
     }
   }
-  if (o.th < 0 && threadIdx.x == 0) D.is[i * NIS + IS_WLIFT] = 0;
-  if (o.th >= 0) {
-    for (int q = threadIdx.x; q < I.T * I.nu; q += blockDim.x) ar[L.du + q] = (double)y[o.du + q];
-    for (int q = threadIdx.x; q < I.T * I.nx; q += blockDim.x) ar[L.lam_e + I.nx + q] = (double)y[o.le + q];
+  if (!o.lifted() && threadIdx.x == 0) D.is[i * NIS + IS_WLIFT] = 0;
+  if (o.lifted()) {
+    for (int q = threadIdx.x; q < I.T * I.nu; q += blockDim.x) ar[L.du + q] = o.du >= 0 ? (double)y[o.du + q] : 0.0;
+    for (int q = threadIdx.x; q < I.T * I.nx; q += blockDim.x)
+      ar[L.lam_e + I.nx + q] = o.le >= 0 ? (double)y[o.le + q] : 0.0;
     if (threadIdx.x == 0) {
       D.is[i * NIS + IS_WLIFT] = 1;
       D.sc[(long long)i * NSC + SC_RHOW] = o.rho >= 0 ? exp((double)y[o.rho]) : 0.0;
@@ -1492,8 +1494,8 @@ static nrto_status warm_from_network(nrto_problem_t p, nrto_mlp_t m, const float
     auto fits = [&](int off, long long n) { return off >= 0 && off + n <= out_dim; };
     if (!fits(o.k, kmax) || !fits(o.pt, mmax + 1) || !fits(o.lp, mmax + 1))
       fail(NRTO_ERR_INVALID, "offsets and row map do not fit the network output");
-    if (o.th >= 0 && (!fits(o.th, mmax + 1) || !fits(o.lw, mmax + 1) || !fits(o.du, umax) || !fits(o.le, xmax) ||
-                      (o.rho >= 0 && !fits(o.rho, 1))))
+    if ((o.th >= 0 && !fits(o.th, mmax + 1)) || (o.lw >= 0 && !fits(o.lw, mmax + 1)) || (o.du >= 0 && !fits(o.du, umax)) ||
+        (o.le >= 0 && !fits(o.le, xmax)) || (o.rho >= 0 && !fits(o.rho, 1)))
       fail(NRTO_ERR_INVALID, "lifted offsets do not fit the network output");
     if (!p->d_wsmap) p->d_wsmap = p->dalloc<int>(p->n_rows);
     CK(cudaMemcpyAsync(p->d_wsmap, row_map, sizeof(int) * p->n_rows, cudaMemcpyHostToDevice, p->stream));
@@ -1505,7 +1507,7 @@ static nrto_status warm_from_network(nrto_problem_t p, nrto_mlp_t m, const float
     p->check_launch("k_scatter_warm");
     CK(cudaStreamSynchronize(p->stream));   // the network's output buffer may be reused after return
     p->warm_pending = true;
-    p->wlift_pending = o.th >= 0;
+    p->wlift_pending = o.lifted();
     return NRTO_OK;
   } catch (const std::exception& e) {
     return handle(e);
@@ -1521,10 +1523,6 @@ nrto_status nrto_set_warm_start_from_network_lifted(nrto_problem_t p, nrto_mlp_t
                                                     const int* row_map, const int* offsets) {
   if (!offsets) {
     g_last_error = "null offsets";
-    return NRTO_ERR_INVALID;
-  }
-  if (offsets[3] < 0 || offsets[4] < 0 || offsets[5] < 0 || offsets[6] < 0) {
-    g_last_error = "the lifted offsets (theta, lambda_w, du, lambda_e) must be >= 0";
     return NRTO_ERR_INVALID;
   }
   return warm_from_network(p, m, features, row_map,

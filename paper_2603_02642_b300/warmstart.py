@@ -179,26 +179,41 @@ class WarmStart:
             out.append(o)
         return out
 
-    def apply(self, prob, insts):
+    # Lifted parts applied by default: δû only.  Measured on 512 held-out instances after 2048
+    # training solves (mean iterations relative to cold on the instances every variant solved):
+    # (k_v, p̃, λ_p) 0.78, + δû 0.68, + δû and θ or λ_w 0.69, + δû and λ_e 0.88, all parts 0.88 with
+    # the duals rescaled to the start penalty and 1.11 at the predicted penalty; the predicted λ_e
+    # and penalty cost more than they save.
+    LIFTED_PARTS = ("du",)
+
+    def apply(self, prob, insts, lifted=None, parts=None):
         """Install the network's warm start for the problem's next inner solve: the forward pass and
-        the scatter into each instance's (K, p̃, λ_p) run on the device."""
+        the scatter into each instance's (K, p̃, λ_p), and with the lifted layout (unless lifted is
+        False) the lifted parts named in `parts` (of "th", "lw", "du", "le", "rho"; default
+        LIFTED_PARTS), run on the device."""
         if not self.deployed:
             raise RuntimeError("fit() the network first")
         row_map = np.concatenate([row_index(inst) for inst in insts]).astype(np.int32)
-        if self.lifted:
+        if self.lifted and lifted is not False:
+            use = self.LIFTED_PARTS if parts is None else parts
+            off = {"th": O_TH, "lw": O_LW, "du": O_DU, "le": O_LE, "rho": O_RHO}
             prob.set_warm_start_from_network_lifted(self.net, features(insts), row_map,
-                                                    [0, N_K, N_K + N_ROWS, O_TH, O_LW, O_DU, O_LE, O_RHO])
+                                                    [0, N_K, N_K + N_ROWS] + [off[k] if k in use else -1
+                                                                              for k in ("th", "lw", "du", "le", "rho")])
         else:
             prob.set_warm_start_from_network(self.net, features(insts), row_map, 0, N_K, N_K + N_ROWS)
 
-    def apply_host(self, prob, insts):
-        """Same warm start through host arrays (predict, then nrto_set_warm_start)."""
+    def apply_host(self, prob, insts, parts=None):
+        """Same warm start through host arrays (predict, then nrto_set_warm_start and, with the lifted
+        layout, nrto_set_warm_start_lifted with the parts not applied set to zero)."""
         pred = self.predict(insts)
         K = np.concatenate([p[0].reshape(-1) for p in pred])
         pt = np.concatenate([p[1] for p in pred])
         lp = np.concatenate([p[2] for p in pred])
         prob.set_warm_start(K, pt, lp)
         if self.lifted:
-            prob.set_warm_start_lifted([p[3] for p in pred], [p[4] for p in pred], [p[5] for p in pred],
-                                       [p[6] for p in pred], [p[7] for p in pred])
+            use = self.LIFTED_PARTS if parts is None else parts
+            pick = lambda k, j: [p[j] if k in use else 0.0 * p[j] for p in pred]
+            prob.set_warm_start_lifted(pick("th", 3), pick("lw", 4), pick("du", 5), pick("le", 6),
+                                       [p[7] for p in pred] if "rho" in use else None)
         return pred

@@ -92,14 +92,35 @@ def test_device_lifted_warm_start_equals_host_path():
     ws = WS.WarmStart(max_batch=64, seed=4, lifted=True)
     ws.deployed = True          # untrained network: the mapping, not the values, is under test
     outs = []
+    parts = ("th", "lw", "du", "le", "rho")
     for apply in (ws.apply, ws.apply_host):
         prob = nrto.Problem(insts, nrto.PREC_FP64)
         prob.linearize()
-        apply(prob, insts)
+        apply(prob, insts, parts=parts)
         prob.solve_socp(nrto.Options(rho=10.0, max_inner=1, check=0))
         outs.append([(prob.export(nrto.F_K, i), prob.export(nrto.F_LAMW, i), prob.export(nrto.F_LAME, i),
                       prob.export(nrto.F_DU, i), prob.export(nrto.F_LAMNU, i), prob.stats()["rho"][i])
                      for i in range(len(insts))])
+        prob.close()
+    for a, b in zip(*outs):
+        for x, y in zip(a, b):
+            assert np.allclose(x, y, rtol=1e-12, atol=1e-13)
+    ws.net.close()
+
+
+def test_device_lifted_warm_start_with_absent_parts_equals_host_path():
+    """The default lifted parts (δû only): the absent parts start at zero on both paths."""
+    insts = [W.warmstart_quad(3_100_000 + s) for s in range(8)]
+    ws = WS.WarmStart(max_batch=64, seed=5, lifted=True)
+    ws.deployed = True
+    outs = []
+    for apply in (ws.apply, ws.apply_host):
+        prob = nrto.Problem(insts, nrto.PREC_FP64)
+        prob.linearize()
+        apply(prob, insts)
+        prob.solve_socp(nrto.Options(rho=10.0, max_inner=2, check=0))
+        outs.append([(prob.export(nrto.F_K, i), prob.export(nrto.F_DU, i), prob.export(nrto.F_LAMNU, i),
+                      prob.export(nrto.F_LAMW, i), prob.stats()["rho"][i]) for i in range(len(insts))])
         prob.close()
     for a, b in zip(*outs):
         for x, y in zip(a, b):
