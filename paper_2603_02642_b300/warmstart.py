@@ -129,18 +129,21 @@ class WarmStart:
     def fit(self, X, Y, Mk, steps=2000, batch=256, lr=1e-3, seed=0):
         """Adam on the standardized data; returns the loss history."""
         X = np.asarray(X, dtype=np.float64)
-        Y = np.asarray(Y, dtype=np.float64)
-        Mk = np.asarray(Mk, dtype=np.float64)
+        Y = np.asarray(Y, dtype=np.float32)
+        Mk32 = np.asarray(Mk, dtype=np.float32)
         self.x_mu = X.mean(axis=0)
         self.x_sd = X.std(axis=0)
         self.x_sd[self.x_sd < 1e-6] = 1.0
-        cnt = np.maximum(Mk.sum(axis=0), 1.0)
-        self.y_mu = (Mk * Y).sum(axis=0) / cnt
-        self.y_sd = np.sqrt((Mk * (Y - self.y_mu) ** 2).sum(axis=0) / cnt)
+        # target statistics in FP64, over row blocks (the target matrix can be several GB)
+        blocks = range(0, Y.shape[0], 4096)
+        cnt = np.maximum(sum(Mk32[b:b + 4096].astype(np.float64).sum(axis=0) for b in blocks), 1.0)
+        self.y_mu = sum((Mk32[b:b + 4096] * Y[b:b + 4096]).astype(np.float64).sum(axis=0) for b in blocks) / cnt
+        self.y_sd = np.sqrt(sum((Mk32[b:b + 4096] * (Y[b:b + 4096] - self.y_mu) ** 2).sum(axis=0) for b in blocks) / cnt)
         self.y_sd[self.y_sd < 1e-6] = 1.0
         Xn = ((X - self.x_mu) / self.x_sd).astype(np.float32)
-        Yn = (Mk * (Y - self.y_mu) / self.y_sd).astype(np.float32)
-        Mk32 = Mk.astype(np.float32)
+        Yn = np.empty_like(Y)
+        for b in blocks:
+            Yn[b:b + 4096] = (Mk32[b:b + 4096] * (Y[b:b + 4096] - self.y_mu) / self.y_sd).astype(np.float32)
         rng = np.random.default_rng(seed)
         n = X.shape[0]
         batch = min(batch, (n // 8) * 8)
