@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--max-inner", type=int, default=40, help="inner cap of the first n_outer-1 outer steps")
     ap.add_argument("--max-inner-final", type=int, default=2000, help="inner cap of the last outer step")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--rho", type=float, default=10.0)
+    ap.add_argument("--rho", type=float, default=1.0, help="initial FullADMM penalty")
     ap.add_argument("--adapt", type=int, default=25, help="residual-balancing period (0 = fixed rho)")
+    ap.add_argument("--adapt-mu", type=float, default=3.0, help="residual-balancing ratio threshold")
     ap.add_argument("--stall", type=int, default=100, help="stall-stop period (0 = off)")
     ap.add_argument("--carry", type=int, default=1, help="inner-state carry across outer steps")
     ap.add_argument("--feas-tol", type=float, default=1e-4)
@@ -95,6 +96,7 @@ def solver_options(args, carry=None):
     from paper_2603_02642_b300 import nrto
     return nrto.Options(rho=args.rho, max_inner=args.max_inner, max_inner_final=args.max_inner_final,
                         eps_p=1e-4, eps_d=1e-4, check=1, r0=args.r0, w_p=args.w_p, adapt_every=args.adapt,
+                        adapt_mu=args.adapt_mu,
                         stall_every=args.stall, stall_ratio=0.9, carry=args.carry if carry is None else carry)
 
 
@@ -123,7 +125,8 @@ def _oracle_task(task):
     res = O.solve(inst, O.OuterOptions(n_outer=prm["n_outer"], r0=prm["r0"], w_p=prm["w_p"], carry=bool(prm["carry"]),
                                        max_inner_final=prm["max_inner_final"]),
                   admm=F.FullADMMOptions(rho=prm["rho"], max_iter=prm["max_inner"], eps_p=1e-4, eps_d=1e-4,
-                                         adapt_every=prm["adapt"], stall_every=prm["stall"], stall_ratio=0.9))
+                                         adapt_every=prm["adapt"], adapt_mu=prm["adapt_mu"], stall_every=prm["stall"],
+                                         stall_ratio=0.9))
     t1 = time.perf_counter()
     ok = bool(res.accepted_inner_converged and res.max_violation <= prm["feas_tol"])
     return {"kind": "full", "S": sum(entries(inst)), "iters": int(sum(res.inner_iters)), "ok": ok, "t": t1 - t0}
@@ -151,7 +154,7 @@ def oracle_tasks(instances, args, cores):
     n_full = int(min(max(cores, 4), 16))
     prm = dict(rho=args.rho, k_it=4, n_outer=args.n_outer, max_inner=args.max_inner,
                max_inner_final=args.max_inner_final, adapt=args.adapt, stall=args.stall, carry=args.carry,
-               feas_tol=args.feas_tol, r0=args.r0, w_p=args.w_p)
+               feas_tol=args.feas_tol, r0=args.r0, w_p=args.w_p, adapt_mu=args.adapt_mu)
     return ([("full", instances[int(i)], prm) for i in order[:n_full]]
             + [("cost", instances[int(order[i])], prm) for i in q])
 
@@ -749,7 +752,7 @@ def main():
                        "n_outer": args.n_outer, "max_inner": args.max_inner, "max_inner_final": args.max_inner_final,
                        "precision": args.prec, "rho0": args.rho, "adapt_every": args.adapt,
                        "stall_every": args.stall, "carry": args.carry, "feas_tol": args.feas_tol,
-                       "r0": args.r0, "w_p": args.w_p,
+                       "r0": args.r0, "w_p": args.w_p, "adapt_mu": args.adapt_mu,
                        "l2": "inputs larger than L2 (row arrays of several GB)",
                        "counted": n_ok, "counted_frac": n_ok / prob.n,
                        "counted_by_kind": {"unicycle": int(ok[kinds == 0].sum()), "quadcopter": int(ok[kinds == 1].sum())},
