@@ -646,12 +646,17 @@ void check_row_groups(const KindLaunch& kl) {
   if (tpg > nt) fail(NRTO_ERR_INVALID, "horizon too long for the solver kernel's thread block");
 }
 
+// Largest chunk of row entries staged per bulk-copy round (the budget of shared memory may cut it).
+#ifndef NRTO_CHUNK_MAX
+#define NRTO_CHUNK_MAX 12288
+#endif
+
 template <typename Real>
 void choose_chunk(KindLaunch& kl) {
   check_row_groups<Real>(kl);
   const int nx = kind_nx(kl.kind);
   const int minc = ((kl.tmax + 1) * nx + 3) & ~3;
-  int chunk = 12288;
+  int chunk = NRTO_CHUNK_MAX;
   while (chunk > minc && smem_for<Real>(kl.kind, chunk, chunk / (2 * nx) + 2) > (size_t)smem_budget<Real>(kl.kind)) chunk -= 256;
   if (chunk < minc) chunk = minc;
   kl.chunk = chunk;

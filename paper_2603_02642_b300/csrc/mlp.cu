@@ -72,12 +72,15 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-template <int BN>
-constexpr size_t gemm_smem_bytes() { return 1024 + (size_t)GEMM_STAGES * (128 * 128 + BN * 128); }
+// STG pipeline stages; with two stages a CTA needs half the shared memory, so two CTAs share an SM
+// and one's epilogue overlaps the other's loads and MMAs (the short-K output layer).
+template <int BN, int STG = GEMM_STAGES>
+constexpr size_t gemm_smem_bytes() { return 1024 + (size_t)STG * (128 * 128 + BN * 128); }
 
-template <int BN, int EPI>
-__global__ void __launch_bounds__(128, 1)
+template <int BN, int EPI, int STG = GEMM_STAGES>
+__global__ void __launch_bounds__(128, STG == 2 ? 2 : 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K, EpiArgs ep) {
+  constexpr int GEMM_STAGES = STG;
   extern __shared__ uint8_t smem_raw[];
   constexpr int A_BYTES = 128 * 128, B_BYTES = BN * 128, STAGE = A_BYTES + B_BYTES;
   __shared__ __align__(8) uint64_t full[GEMM_STAGES], empty[GEMM_STAGES], accb;
@@ -141,8 +144,32 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
 
   // epilogue: TMEM → registers → global
   const int row = m0 + warp * 32 + lane;
+  if constexpr (EPI == EPI_BIAS || EPI == EPI_F32) {
+    // FP32 outputs: each warp turns its 32 × 32 slices around in shared memory (the stage buffers are
+    // idle once the accumulator is complete) so that a store instruction writes 32 consecutive
+    // columns of one row, with the bias added per column
+    float* tbuf = reinterpret_cast<float*>(base) + warp * (32 * 33);
 #pragma unroll 1
-  for (int c = 0; c < BN / 32; ++c) {
+    for (int c = 0; c < BN / 32; ++c) {
+      float v[32];
+      tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+      const int nb = n0 + c * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tbuf[lane * 33 + j] = v[j];
+      __syncwarp();
+      const int n = nb + lane;
+      float bv = 0.0f;
+      if constexpr (EPI == EPI_BIAS) bv = n < ep.N ? ep.bias[n] : 0.0f;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const int rr = m0 + warp * 32 + r;
+        if (rr < ep.M && n < ep.N) ep.out_f32[(long long)rr * ep.ld_f32 + n] = tbuf[r * 33 + lane] + bv;
+      }
+      __syncwarp();
+    }
+  }
+#pragma unroll 1
+  for (int c = 0; c < ((EPI == EPI_BIAS || EPI == EPI_F32) ? 0 : BN / 32); ++c) {
     float v[32];
     tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
     const int nb = n0 + c * 32;
@@ -347,19 +374,20 @@ CUtensorMap make_map(const bf16* ptr, long long rows, long long k_ext, long long
   return m;
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, int STG = GEMM_STAGES>
 void launch_gemm(cudaStream_t st, const bf16* A, long long lda, const bf16* B, long long ldb, int M, int N, int K,
                  const EpiArgs& ep) {
+  static_assert(STG >= 2 && (STG > 2 || BN <= 256), "two resident CTAs need BN <= 256 TMEM columns each");
   const CUtensorMap ta = make_map(A, M, K, lda, 128);
   const CUtensorMap tb = make_map(B, N, K, ldb, BN);
-  auto kern = k_gemm_bf16<BN, EPI>;
+  auto kern = k_gemm_bf16<BN, EPI, STG>;
   static bool attr_set = false;   // per template instance
   if (!attr_set) {
-    MK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes<BN>()));
+    MK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes<BN, STG>()));
     attr_set = true;
   }
   dim3 grid((M + 127) / 128, (N + BN - 1) / BN);
-  kern<<<grid, 128, gemm_smem_bytes<BN>(), st>>>(ta, tb, K, ep);
+  kern<<<grid, 128, gemm_smem_bytes<BN, STG>(), st>>>(ta, tb, K, ep);
   MK(cudaGetLastError());
 }
 
@@ -394,7 +422,7 @@ struct nrto_mlp {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gemm_events;   // around each GEMM launch
   double gemm_flops = 0.0;                                         // 2·M·N·K of the timed launches
 
-  template <int BN, int EPI>
+  template <int BN, int EPI, int STG = GEMM_STAGES>
   void gemm(const bf16* A, long long lda, const bf16* B, long long ldb, int M, int N, int K, const EpiArgs& ep) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (profiling) {
@@ -402,7 +430,7 @@ struct nrto_mlp {
       MK(cudaEventCreate(&e1));
       MK(cudaEventRecord(e0, stream));
     }
-    launch_gemm<BN, EPI>(stream, A, lda, B, ldb, M, N, K, ep);
+    launch_gemm<BN, EPI, STG>(stream, A, lda, B, ldb, M, N, K, ep);
     if (profiling) {
       MK(cudaEventRecord(e1, stream));
       gemm_events.push_back({e0, e1});
@@ -449,7 +477,9 @@ struct nrto_mlp {
         gemm<64, EPI_BIAS_GELU>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
       } else {
         ep.out_f32 = Y; ep.ld_f32 = dims[L];
-        gemm<256, EPI_BIAS>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
+        // the output layer (wide N, short K): two stages, two CTAs per SM
+        if (K <= 256) gemm<256, EPI_BIAS, 2>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
+        else gemm<256, EPI_BIAS>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
       }
       ++launches;
     }
