@@ -53,6 +53,10 @@ void mfail(nrto_status s, const std::string& m) { throw MlpError{s, m}; }
 // warps run the epilogue from TMEM (warp w owns accumulator rows 32w .. 32w+31).
 // ---------------------------------------------------------------------------------------------
 constexpr int GEMM_STAGES = 4;
+// column splits of the persistent output-layer GEMM's epilogue (4·NRTO_GEMM_CS epilogue warps)
+#ifndef NRTO_GEMM_CS
+#define NRTO_GEMM_CS 4
+#endif
 enum : int { EPI_BIAS_GELU = 0, EPI_BIAS = 1, EPI_GELU_BWD = 2, EPI_F32 = 3 };
 
 struct EpiArgs {
@@ -259,6 +263,154 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
 }
 
 // ---------------------------------------------------------------------------------------------
+// Persistent GEMM for FP32 outputs with a bias (the output layer, wide N and short K): one CTA per
+// SM walks the 128 × BN tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (m-blocks fastest, so the
+// CTAs working at a time share the B tile in L2).  Warp 4·CS (lane 0) issues the bulk tensor loads
+// through an STG-deep stage ring that runs on across tiles; warp 4·CS+1 (lane 0) issues the MMAs into
+// one of two TMEM accumulators (columns [0, BN) and [BN, 2 BN)); warps 0 .. 4·CS-1 run the epilogue
+// of tile i while the MMAs of tile i+1 run, warp w on TMEM lane quarter w % 4 and column split w / 4
+// (several warps per quarter, since the FP32 stores set the epilogue's pace).  Accumulator a is full
+// when the MMAs of its tile have completed (acc_full[a], tcgen05.commit) and empty again when every
+// epilogue warp has read it (acc_empty[a], 4·CS arrivals).  The epilogue turns each warp's 32 × 32
+// slices around in its shared buffer so that a store writes 32 consecutive columns of one row.
+// Results equal k_gemm_bf16's (the same MMA order per tile).  Every wait is bounded; after one
+// gives up, the CTA waits (bounded) for its issued loads and MMAs before it frees the TMEM.
+// ---------------------------------------------------------------------------------------------
+// CS column splits of the epilogue: 4·CS epilogue warps, then the producer and the MMA warps.
+template <int BN, int STG, int CS>
+constexpr size_t gemm_persistent_smem_bytes() { return 1024 + (size_t)STG * (128 * 128 + BN * 128) + 4 * CS * 32 * 33 * 4; }
+
+template <int BN, int STG, int CS>
+__global__ void __launch_bounds__(32 * (4 * CS + 2), 1)
+k_gemm_bf16_persistent(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K,
+                       int tiles_m, int tiles, EpiArgs ep) {
+  extern __shared__ uint8_t smem_raw[];
+  constexpr int A_BYTES = 128 * 128, B_BYTES = BN * 128, STAGE = A_BYTES + B_BYTES;
+  __shared__ __align__(8) uint64_t full[STG], empty[STG], acc_full[2], acc_empty[2], mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_err;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  float* tbuf_all = reinterpret_cast<float*>(base + (size_t)STG * STAGE);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nk = (K + 63) / 64;
+  constexpr int NEPI = 4 * CS, PROD = 32 * NEPI, MMA = 32 * NEPI + 32;   // lane 0 of the last two warps
+  static_assert((BN / 32) % CS == 0, "the column splits must divide the tile's 32-column chunks");
+  if (warp == NEPI) {
+    tmem_alloc(&tmem_base, 2 * BN);
+    tmem_relinquish();
+  }
+  if (tid == MMA) {
+    for (int s = 0; s < STG; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&acc_full[a], 1); mbar_init(&acc_empty[a], NEPI); }
+    mbar_init(&mma_done, 1);
+    fence_mbar_init();
+    s_err = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  int issued = 0;   // stages the producer has issued loads for
+  if (tid == PROD) {
+    int g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      const int m0 = (t % tiles_m) * 128, n0 = (t / tiles_m) * BN;
+      for (int k = 0; k < nk; ++k, ++g) {
+        const int s = g % STG;
+        if (g >= STG && !mbar_wait_bounded(&empty[s], (uint32_t)((g / STG) - 1) & 1u)) {
+          s_err = 1;
+          ok = false;
+          break;
+        }
+        uint8_t* sa = base + (size_t)s * STAGE;
+        mbar_arrive_expect_tx(&full[s], STAGE);
+        tma_load_2d(sa, &ta, k * 64, m0, &full[s]);
+        tma_load_2d(sa + A_BYTES, &tb, k * 64, n0, &full[s]);
+        issued = g + 1;
+      }
+    }
+  } else if (tid == MMA) {
+    constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
+    int g = 0, li = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++li) {
+      const int a = li & 1;
+      if (li >= 2 && !mbar_wait_bounded(&acc_empty[a], (uint32_t)((li >> 1) - 1) & 1u)) {
+        s_err = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(a * BN);
+      for (int k = 0; k < nk; ++k, ++g) {
+        const int s = g % STG;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)(g / STG) & 1u)) {
+          s_err = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(base + (size_t)s * STAGE), sb = sa + A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          umma_bf16(d, sdesc_k_sw128(sa + kk * 32), sdesc_k_sw128(sb + kk * 32), idesc, (k | kk) != 0 ? 1u : 0u);
+        umma_commit(&empty[s]);
+      }
+      if (ok) umma_commit(&acc_full[a]);
+    }
+    // every MMA this thread issued has completed once mma_done fires
+    umma_commit(&mma_done);
+    if (!mbar_wait_bounded(&mma_done, 0)) s_err = 1;
+  } else if (warp < NEPI) {
+    float* tbuf = tbuf_all + warp * (32 * 33);
+    const int q = warp & 3, h = warp >> 2;   // TMEM lane quarter, column split
+    constexpr int CPW = BN / 32 / CS;        // 32-column chunks per warp
+    int li = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++li) {
+      const int a = li & 1;
+      int got = 1;
+      if (lane == 0) got = mbar_wait_bounded(&acc_full[a], (uint32_t)(li >> 1) & 1u) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (!got) {
+        if (lane == 0) s_err = 1;
+        break;
+      }
+      tc_fence_after();
+      const int m0 = (t % tiles_m) * 128, n0 = (t / tiles_m) * BN;
+#pragma unroll 1
+      for (int c = h * CPW; c < (h + 1) * CPW; ++c) {
+        float v[32];
+        tmem_ld_32x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + c * 32), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tbuf[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int n = n0 + c * 32 + lane;
+        const float bv = n < ep.N ? ep.bias[n] : 0.0f;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+          const int rr = m0 + q * 32 + r;
+          if (rr < ep.M && n < ep.N) ep.out_f32[(long long)rr * ep.ld_f32 + n] = tbuf[r * 33 + lane] + bv;
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[a]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == PROD && s_err) {
+    for (int k = issued > STG ? issued - STG : 0; k < issued; ++k)
+      (void)mbar_wait_bounded(&full[k % STG], (uint32_t)(k / STG) & 1u);
+  }
+  __syncthreads();
+  if (warp == NEPI) tmem_dealloc(tmem, 2 * BN);
+  if (tid == 0 && s_err) atomicExch(ep.err, 1);
+}
+
+
+// ---------------------------------------------------------------------------------------------
 // elementwise / small kernels
 // ---------------------------------------------------------------------------------------------
 // fp32 [rows][cols] → bf16 [rows][ldo] with zero padding columns cols .. ldo-1
@@ -391,6 +543,29 @@ void launch_gemm(cudaStream_t st, const bf16* A, long long lda, const bf16* B, l
   MK(cudaGetLastError());
 }
 
+template <int BN, int STG, int CS>
+void launch_gemm_persistent(cudaStream_t st, const bf16* A, long long lda, const bf16* B, long long ldb, int M, int N,
+                            int K, const EpiArgs& ep) {
+  static_assert(2 * BN <= 512, "two accumulators of BN columns must fit the 512 TMEM columns");
+  const CUtensorMap ta = make_map(A, M, K, lda, 128);
+  const CUtensorMap tb = make_map(B, N, K, ldb, BN);
+  auto kern = k_gemm_bf16_persistent<BN, STG, CS>;
+  static bool attr_set = false;
+  static int n_sm = 0;
+  if (!attr_set) {
+    MK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)gemm_persistent_smem_bytes<BN, STG, CS>()));
+    int dev = 0;
+    MK(cudaGetDevice(&dev));
+    MK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    attr_set = true;
+  }
+  const int tiles_m = (M + 127) / 128, tiles = tiles_m * ((N + BN - 1) / BN);
+  const int grid = std::max(1, std::min(tiles, n_sm));
+  kern<<<grid, 32 * (4 * CS + 2), gemm_persistent_smem_bytes<BN, STG, CS>(), st>>>(ta, tb, K, tiles_m, tiles, ep);
+  MK(cudaGetLastError());
+}
+
 int round8(int x) { return (x + 7) & ~7; }
 
 }  // namespace
@@ -438,6 +613,21 @@ struct nrto_mlp {
     }
   }
 
+  void gemm_out(const bf16* A, long long lda, const bf16* B, long long ldb, int M, int N, int K, const EpiArgs& ep) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (profiling) {
+      MK(cudaEventCreate(&e0));
+      MK(cudaEventCreate(&e1));
+      MK(cudaEventRecord(e0, stream));
+    }
+    launch_gemm_persistent<256, 3, NRTO_GEMM_CS>(stream, A, lda, B, ldb, M, N, K, ep);
+    if (profiling) {
+      MK(cudaEventRecord(e1, stream));
+      gemm_events.push_back({e0, e1});
+      gemm_flops += 2.0 * M * N * K;
+    }
+  }
+
   template <typename T>
   T* dalloc(size_t count) {
     void* p = nullptr;
@@ -477,9 +667,8 @@ struct nrto_mlp {
         gemm<64, EPI_BIAS_GELU>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
       } else {
         ep.out_f32 = Y; ep.ld_f32 = dims[L];
-        // the output layer (wide N, short K): two stages, two CTAs per SM
-        if (K <= 256) gemm<256, EPI_BIAS, 2>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
-        else gemm<256, EPI_BIAS>(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
+        // the output layer (wide N, short K): the persistent GEMM, epilogue overlapped with the MMAs
+        gemm_out(A, lda, Wt[l], ldt[l], B, dims[l + 1], K, ep);
       }
       ++launches;
     }
