@@ -61,8 +61,8 @@ def parse():
     ap.add_argument("--r0", type=float, default=0.5, help="initial and largest trust radius of the outer loop")
     ap.add_argument("--w-p", type=float, default=1000.0, help="merit weight of the robust-constraint violation")
     ap.add_argument("--mc", type=int, default=1000, help="Monte Carlo interior and edge samples per instance")
-    ap.add_argument("--warm-train", type=int, default=2048, help="training solves of the learned warm start")
-    ap.add_argument("--warm-eval", type=int, default=1024, help="held-out instances of the learned warm start")
+    ap.add_argument("--warm-train", type=int, default=1024, help="training solves of the learned warm start")
+    ap.add_argument("--warm-eval", type=int, default=512, help="held-out instances of the learned warm start")
     ap.add_argument("--plain-n", type=int, default=16, help="instances of the plain batch-1 FP64 arm")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
