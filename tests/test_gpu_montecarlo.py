@@ -94,3 +94,20 @@ def test_monte_carlo_argument_checks():
     ok = prob.monte_carlo(0, 0)
     assert ok[0] == 0
     prob.close()
+
+
+def test_monte_carlo_parity_at_workload_sizes_fp64():
+    """The largest horizons of the batched workload (unicycle T = 200 with 20 obstacles, quadcopter
+    T = 150 with 15), seeded nominal and gains given to both sides: the per-sample worst values of
+    interior and edge samples at 1e-9."""
+    rng = np.random.default_rng(21)
+    insts = [W.unicycle(5, T=200, n_obs=20), W.quadcopter(6, T=150, n_obs=15)]
+    us = [x.u_init + 0.02 * rng.normal(size=x.u_init.shape) for x in insts]
+    Ks = [0.05 * rng.normal(size=(x.T, x.nu, x.nx)) for x in insts]
+    prob = nrto.Problem(insts, nrto.PREC_FP64)
+    prob.linearize(us)
+    ok, worst = prob.monte_carlo(4, 5, seed=77, K=Ks, per_sample=True)
+    for i, inst in enumerate(insts):
+        ook, ow = MC.check(inst, us[i], Ks[i], 77, i, 4, 5)
+        _compare(worst[i], ow, ok[i], ook)
+    prob.close()
