@@ -78,6 +78,21 @@ def dist_env():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_reduce(values, ops, ws, device):
+    """Replicas' results combined over the ranks: values[i] reduced with ops[i] ("max" for times,
+    "sum" for counts); a no-op on one rank.  device: where the collective's tensor lives (cuda under
+    NCCL, cpu under gloo)."""
+    import torch
+    import torch.distributed as dist
+    out = [float(v) for v in values]
+    if ws > 1:
+        for i, op in enumerate(ops):
+            t = torch.tensor([out[i]], dtype=torch.float64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+            out[i] = float(t.item())
+    return out
+
+
 def workload(n, rank):
     from paper_2603_02642_b300 import workloads as W
     return W.batched_mix(n, base_seed=10000 + rank * n)
@@ -658,20 +673,14 @@ def main():
     phases = prob.phase_cycles()
     tot = max(sum(v for k, v in phases.items() if k != "rows_copy_wait"), 1)
     phase_share = {k: round(v / tot, 4) for k, v in phases.items()}
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = rank_reduce([ms], ["max"], ws, "cuda")[0]
     step_s = ms_max / 1000.0 / args.steps
 
     # every step is the same computation: the last step's per-instance outcome holds for all
     st = prob.stats()
     ok = counted(st, args.feas_tol)
     n_ok = int(ok.sum())
-    tn = torch.tensor([float(n_ok)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(tn, op=dist.ReduceOp.SUM)
-    value = float(tn.item()) / step_s
+    value = rank_reduce([n_ok], ["sum"], ws, "cuda")[0] / step_s
     iters = st["cum_iters"]
     w = 4 if prec == nrto.PREC_MIXED else 8
     bytes_step = bytes_design = 0.0
@@ -710,11 +719,8 @@ def main():
             n_ok_e2e = int(counted(prob.stats(), args.feas_tol).sum())
         barrier()
         t1 = time.perf_counter()
-        tt = torch.tensor([t1 - t0, float(n_ok_e2e)], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(tt[:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        e2e = {"value": float(tt[1].item()) * n_e2e / float(tt[0].item()), "unit": UNIT,
+        e2e_s, e2e_ok = rank_reduce([t1 - t0, n_ok_e2e], ["max", "sum"], ws, "cuda")
+        e2e = {"value": e2e_ok * n_e2e / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
 
     # Monte Carlo robust-constraint satisfaction of the returned iterates (Sec. V, Methodology),
