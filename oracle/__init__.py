@@ -18,7 +18,8 @@ Modules (each function cites the passage of the paper it follows):
   mlp        FP64 reference MLP forward/backward for the learned warm start
 
 Parity status: every function here is pinned by `tests/test_oracle_*.py` against
-closed forms, invariants, brute force or an independent solver, except the outer
-loop's accept/reject rule, which the paper leaves to prior work: "parity unpinned"
-for `outer.solve` against the paper (it is pinned only to its own definition).
+closed forms, invariants, brute force or an independent solver.  The outer loop
+(`outer.solve`) is pinned on a convex case, where its end point is fixed by the
+mathematics; the constants of its accept/reject rule and radius schedule come from
+prior work that the paper does not restate, so they remain a reading.
 """

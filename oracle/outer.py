@@ -7,8 +7,9 @@ here is: merit φ(ū, K) = J(ū, K) + w_p Σ_j max(0, g_j(x̄) + b_jᵀ·0 + ‖
 with the linearization at the candidate itself; accept iff φ decreases; on accept
 r ← min(1.5 r, r_0), on reject r ← max(0.8 r, r_min).  J is the Problem 1 cost
 Σ_k (ū_k - u_ref)ᵀR_u(·) + ‖R_K K_k‖_F² plus the state-tracking term Σ_{t≥1}(x̄_t - x_goal)ᵀQ_x(·).
-Parity status: unpinned against the paper (its schedule constants are not given); pinned
-only to this definition.
+Parity status: pinned on a convex case (linear dynamics and linear constraints, where every
+linearization is exact and the loop must end at the optimum of Problem 1, which an independent
+barrier solve gives); the schedule's constants are not given in the paper and stay a reading.
 """
 from __future__ import annotations
 
