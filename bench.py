@@ -5,7 +5,8 @@ Workload: the 2048-instance batch (seeded; 50/50 unicycle T~U{20..200} with 1-20
 quadcopter T~U{50..150} with 1-15 obstacles).  One step = one complete NRTO solve of every instance:
 10 successive-linearization steps; the inner FullADMM solves of the first nine stop after the
 paper's 40 iterations (inexact, Supplementary Tables VI-VIII), the last one runs to full residuals
-<= 1e-4 (cap 2000), all with residual balancing every 25 iterations and the stall stop.
+<= 1e-4 (cap 2000), all with residual balancing every 25 iterations, the stall stop and the budget
+stop (a solve whose primal residual, at its observed rate, would miss 1e-4 within the cap ends early).
 
 A solve counts when (i) the inner solve that produced the returned (accepted) iterate terminated at
 full residuals r_p, r_d <= 1e-4 and (ii) every robust constraint holds there:
@@ -56,6 +57,8 @@ def parse():
     ap.add_argument("--adapt", type=int, default=25, help="residual-balancing period (0 = fixed rho)")
     ap.add_argument("--adapt-mu", type=float, default=3.0, help="residual-balancing ratio threshold")
     ap.add_argument("--stall", type=int, default=100, help="stall-stop period (0 = off)")
+    ap.add_argument("--stall-budget", type=float, default=1.0,
+                    help="budget-stop factor at the stall checkpoints (0 = off)")
     ap.add_argument("--carry", type=int, default=1, help="inner-state carry across outer steps")
     ap.add_argument("--feas-tol", type=float, default=1e-4)
     ap.add_argument("--r0", type=float, default=0.5, help="initial and largest trust radius of the outer loop")
@@ -112,7 +115,8 @@ def solver_options(args, carry=None):
     return nrto.Options(rho=args.rho, max_inner=args.max_inner, max_inner_final=args.max_inner_final,
                         eps_p=1e-4, eps_d=1e-4, check=1, r0=args.r0, w_p=args.w_p, adapt_every=args.adapt,
                         adapt_mu=args.adapt_mu,
-                        stall_every=args.stall, stall_ratio=0.9, carry=args.carry if carry is None else carry)
+                        stall_every=args.stall, stall_ratio=0.9, stall_budget=args.stall_budget,
+                        carry=args.carry if carry is None else carry)
 
 
 def counted(st, tol):
@@ -141,7 +145,7 @@ def _oracle_task(task):
                                        max_inner_final=prm["max_inner_final"]),
                   admm=F.FullADMMOptions(rho=prm["rho"], max_iter=prm["max_inner"], eps_p=1e-4, eps_d=1e-4,
                                          adapt_every=prm["adapt"], adapt_mu=prm["adapt_mu"], stall_every=prm["stall"],
-                                         stall_ratio=0.9))
+                                         stall_ratio=0.9, stall_budget=prm["stall_budget"]))
     t1 = time.perf_counter()
     ok = bool(res.accepted_inner_converged and res.max_violation <= prm["feas_tol"])
     return {"kind": "full", "S": sum(entries(inst)), "iters": int(sum(res.inner_iters)), "ok": ok, "t": t1 - t0}
@@ -169,7 +173,8 @@ def oracle_tasks(instances, args, cores):
     n_full = int(min(max(cores, 4), 16))
     prm = dict(rho=args.rho, k_it=4, n_outer=args.n_outer, max_inner=args.max_inner,
                max_inner_final=args.max_inner_final, adapt=args.adapt, stall=args.stall, carry=args.carry,
-               feas_tol=args.feas_tol, r0=args.r0, w_p=args.w_p, adapt_mu=args.adapt_mu)
+               feas_tol=args.feas_tol, r0=args.r0, w_p=args.w_p, adapt_mu=args.adapt_mu,
+               stall_budget=args.stall_budget)
     return ([("full", instances[int(i)], prm) for i in order[:n_full]]
             + [("cost", instances[int(order[i])], prm) for i in q])
 
@@ -603,7 +608,7 @@ def reference_arm(args):
             "config": {"workload": f"batch{args.n}_mixed_unicycle_quadcopter", "n_outer": args.n_outer,
                        "max_inner": args.max_inner, "max_inner_final": args.max_inner_final,
                        "instances_per_gpu": args.n, "adapt_every": args.adapt, "stall_every": args.stall,
-                       "carry": args.carry, "feas_tol": args.feas_tol,
+                       "stall_budget": args.stall_budget, "carry": args.carry, "feas_tol": args.feas_tol,
                        "step": "a 1/steps share of the oracle sample's tasks on all host cores"},
             "cpu_baseline": est,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -763,8 +768,8 @@ def main():
             "config": {"workload": f"batch{args.n}_mixed_unicycle_quadcopter", "instances_per_gpu": args.n,
                        "n_outer": args.n_outer, "max_inner": args.max_inner, "max_inner_final": args.max_inner_final,
                        "precision": args.prec, "rho0": args.rho, "adapt_every": args.adapt,
-                       "stall_every": args.stall, "carry": args.carry, "feas_tol": args.feas_tol,
-                       "r0": args.r0, "w_p": args.w_p, "adapt_mu": args.adapt_mu,
+                       "stall_every": args.stall, "stall_budget": args.stall_budget, "carry": args.carry,
+                       "feas_tol": args.feas_tol, "r0": args.r0, "w_p": args.w_p, "adapt_mu": args.adapt_mu,
                        "l2": "inputs larger than L2 (row arrays of several GB)",
                        "counted": n_ok, "counted_frac": n_ok / prob.n,
                        "counted_by_kind": {"unicycle": int(ok[kinds == 0].sum()), "quadcopter": int(ok[kinds == 1].sum())},

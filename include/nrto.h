@@ -136,6 +136,12 @@ typedef struct {
    * Other solver kinds reject kv_pcg_iters > 0. */
   int kv_pcg_iters;
   double kv_pcg_tol;
+  /* FullADMM budget stop, with stall_every > 0 (the library's scheduling rule; the paper runs a fixed
+   * budget): at a stall checkpoint where r_p is above eps_p but fell by at least the factor
+   * stall_ratio, stop (status 5) when stall_budget times the iterations that r_p would need to reach
+   * eps_p, at the rate it fell over the last period, exceeds the iterations left under the cap, so that
+   * a solve that cannot meet the tolerance within its cap ends early.  0 disables it; must be >= 0. */
+  double stall_budget;
 } nrto_solver_opts;
 
 /* Per-instance sizes, for sizing output buffers. */

@@ -24,6 +24,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import math
+
 import numpy as np
 
 from . import dr
@@ -54,6 +56,12 @@ class FullADMMOptions:
     # linearization.  0 disables it.
     stall_every: int = 0
     stall_ratio: float = 0.9
+    # Budget stop (a scheduling rule of the library; the paper runs a fixed budget): at the same
+    # checkpoints, when r_p^l > ε_p fell by at least stall_ratio, the geometric rate
+    # q = r_p^l / r_p^{l-stall_every} needs n = stall_every · log(ε_p / r_p^l) / log q more
+    # iterations to reach ε_p; stop (as stalled) when l + stall_budget · n exceeds the iteration cap.
+    # 0 disables it.
+    stall_budget: float = 0.0
     # k_v update by matrix-free Jacobi-preconditioned CG (problem.gain_solve_pcg) from the previous
     # gains, with this iteration cap and relative tolerance; 0 iterations: the exact per-step solve.
     kv_pcg_iters: int = 0
@@ -228,6 +236,11 @@ def iterate(inst, lin, opts: FullADMMOptions, state: FullADMMState | None = None
             if it >= 2 * S_ and r_p > opts.eps_p and r_p > opts.stall_ratio * rp_mark:
                 s.stalled = True
                 break
+            if it >= 2 * S_ and r_p > opts.eps_p and opts.stall_budget > 0:
+                need = S_ * math.log(opts.eps_p / r_p) / math.log(r_p / rp_mark)
+                if it + opts.stall_budget * need > L:
+                    s.stalled = True
+                    break
             rp_mark = r_p
     return s
 

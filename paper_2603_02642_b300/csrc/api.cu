@@ -567,6 +567,7 @@ void launch_solve(nrto_problem* P, const nrto_solver_opts& o) {
   sp.adapt_every = o.adapt_every; sp.stall_every = o.stall_every;
   sp.adapt_mu = o.adapt_mu; sp.adapt_tau = o.adapt_tau; sp.rho_min = o.rho_min; sp.rho_max = o.rho_max;
   sp.stall_ratio = o.stall_ratio;
+  sp.stall_budget = o.stall_budget;
   sp.fallback = o.warm_fallback;
   sp.kv_pcg_iters = o.solver == NRTO_SOLVER_FULLADMM ? o.kv_pcg_iters : 0;
   sp.kv_pcg_tol = o.kv_pcg_tol;
@@ -776,6 +777,7 @@ void check_opts(const nrto_solver_opts* o) {
   if (o->adapt_every > 0 && !(o->adapt_mu > 1 && o->adapt_tau > 1 && o->rho_min > 0 && o->rho_max >= o->rho_min))
     fail(NRTO_ERR_INVALID, "residual balancing needs mu > 1, tau > 1, 0 < rho_min <= rho_max");
   if (o->stall_every > 0 && !(o->stall_ratio > 0 && o->stall_ratio < 1)) fail(NRTO_ERR_INVALID, "stall_ratio must be in (0,1)");
+  if (!(o->stall_budget >= 0 && o->stall_budget < 1e300)) fail(NRTO_ERR_INVALID, "stall_budget must be finite and >= 0");
   if (o->carry != 0 && o->carry != 1) fail(NRTO_ERR_INVALID, "carry must be 0 or 1");
   if (o->max_inner_final < 0 || o->max_inner_final > 1000000) fail(NRTO_ERR_INVALID, "max_inner_final out of range");
   if (o->kv_pcg_iters < 0 || o->kv_pcg_iters > 1000000) fail(NRTO_ERR_INVALID, "kv_pcg_iters out of range");

@@ -37,6 +37,7 @@ struct SolveParams {
   int adapt_every, stall_every;         // residual balancing / stall stop periods (0 = off)
   int fallback;                         // warm start: rerun cold when the warm-started run stalls
   double adapt_mu, adapt_tau, rho_min, rho_max, stall_ratio;
+  double stall_budget;                  // budget stop factor at the stall checkpoints (0 = off)
 };
 
 // Solver CTA shape for the compute precision float (threads, resident CTAs per SM); FP64 uses 512 × 1.
@@ -1570,7 +1571,14 @@ __device__ void fulladmm_instance(const Dev<Real>& D, const SolveParams& sp, int
       if (bad) { status = ST_NUMERIC; break; }
       if (sp.check && r_p <= sp.eps_p && r_d <= sp.eps_d) { status = ST_CONVERGED; break; }
       if (sp.check && sp.stall_every > 0 && iters % sp.stall_every == 0) {
-        if (iters >= 2 * sp.stall_every && r_p > sp.eps_p && r_p > sp.stall_ratio * rp_mark) { status = ST_STALLED; break; }
+        if (iters >= 2 * sp.stall_every && r_p > sp.eps_p) {
+          if (r_p > sp.stall_ratio * rp_mark) { status = ST_STALLED; break; }
+          // budget stop: at the rate r_p fell over the last period it needs `need` more iterations
+          if (sp.stall_budget > 0.0) {
+            const double need = (double)sp.stall_every * log(sp.eps_p / r_p) / log(r_p / rp_mark);
+            if ((double)iters + sp.stall_budget * need > (double)Lmax) { status = ST_STALLED; break; }
+          }
+        }
         rp_mark = r_p;
       }
       if (b - 1 == Lmax) { status = ST_MAXITER; break; }

@@ -50,7 +50,7 @@ class SolverOpts(C.Structure):
                 ("rho_min", C.c_double), ("rho_max", C.c_double),
                 ("stall_every", C.c_int), ("stall_ratio", C.c_double), ("warm_fallback", C.c_int),
                 ("carry", C.c_int), ("max_inner_final", C.c_int),
-                ("kv_pcg_iters", C.c_int), ("kv_pcg_tol", C.c_double)]
+                ("kv_pcg_iters", C.c_int), ("kv_pcg_tol", C.c_double), ("stall_budget", C.c_double)]
 
 
 class InstanceInfo(C.Structure):
@@ -181,13 +181,14 @@ class Options:
     max_inner_final: int = 0
     kv_pcg_iters: int = 0
     kv_pcg_tol: float = 0.05
+    stall_budget: float = 0.0
 
     def c(self) -> SolverOpts:
         return SolverOpts(self.solver, self.rho, self.alpha, self.r_chi, self.sigma, self.eps_p, self.eps_d,
                           self.eps_dr, self.max_inner, self.max_dr, self.check, self.r0, self.r_min, self.w_p,
                           self.adapt_every, self.adapt_mu, self.adapt_tau, self.rho_min, self.rho_max,
                           self.stall_every, self.stall_ratio, self.warm_fallback, self.carry,
-                          self.max_inner_final, self.kv_pcg_iters, self.kv_pcg_tol)
+                          self.max_inner_final, self.kv_pcg_iters, self.kv_pcg_tol, self.stall_budget)
 
 
 _ZERO1 = np.zeros(1)

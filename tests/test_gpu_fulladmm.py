@@ -154,6 +154,26 @@ def test_stall_stop_matches_oracle():
     assert s.stalled and out["status"][0] == 5 and out["iters"][0] == s.iters
 
 
+def test_budget_stop_matches_oracle():
+    """The budget stop (stall_budget) ends the solve at the same checkpoint as the oracle's, with
+    status 5, on a case where the cap cannot reach the tolerance."""
+    from .test_oracle_fulladmm import tiny_unicycle
+    inst = tiny_unicycle()
+    lin = _lin_oracle(inst)
+    s = F.iterate(inst, lin, F.FullADMMOptions(rho=10.0, r_trust=0.5, eps_p=1e-9, eps_d=1e-9, max_iter=600,
+                                               stall_every=50, stall_budget=1.0))
+    prob = nrto.Problem([inst], nrto.PREC_FP64)
+    prob.linearize()
+    prob.set_trust_radius(0.5)
+    out = prob.solve_socp(nrto.Options(rho=10.0, max_inner=600, check=1, eps_p=1e-9, eps_d=1e-9, stall_every=50,
+                                       stall_budget=1.0))
+    assert s.stalled and s.iters < 600
+    assert out["status"][0] == 5 and out["iters"][0] == s.iters
+    out = prob.solve_socp(nrto.Options(rho=10.0, max_inner=600, check=1, eps_p=1e-9, eps_d=1e-9, stall_every=50))
+    assert out["status"][0] == 2 and out["iters"][0] == 600
+    prob.close()
+
+
 def test_warm_start_iterates_parity_fp64(cases):
     """nrto_set_warm_start (k_v, p̃, λ_p; λ_ν = 0) then 25 iterations: same iterates as the oracle
     started from warm_state."""

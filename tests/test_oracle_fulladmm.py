@@ -186,6 +186,28 @@ def test_stall_stop_on_infeasible_linearization():
     assert s.stalled and not s.converged and s.iters < 5000 and s.r_p > 1e-3
 
 
+def test_budget_stop_cuts_only_a_solve_that_misses_its_cap():
+    """The budget stop ends a solve at the first stall checkpoint where r_p, at the geometric rate it
+    fell over the last period, would reach ε_p only after the cap.  On this case (ε = 1e-9 with a
+    600-iteration cap) the solve without the rule indeed runs to the cap unconverged, so the early
+    stop gives up nothing; up to the stop both runs take the same path, and a vanishing factor only
+    stops at the cap itself."""
+    inst = tiny_unicycle()
+    lin = P.linearize(inst, inst.u_init)
+    base = dict(rho=10.0, r_trust=0.5, eps_p=1e-9, eps_d=1e-9, max_iter=600, stall_every=50)
+    full = F.iterate(inst, lin, F.FullADMMOptions(**base))
+    cut = F.iterate(inst, lin, F.FullADMMOptions(**base, stall_budget=1.0))
+    assert not full.converged and not full.stalled and full.iters == 600
+    assert cut.stalled and not cut.converged and 100 <= cut.iters < 600 and cut.iters % 50 == 0
+    assert cut.history == full.history[:cut.iters]
+    h = [x[0] for x in full.history]
+    reach = lambda l: l + 50 * np.log(1e-9 / h[l - 1]) / np.log(h[l - 1] / h[l - 51])
+    assert reach(cut.iters) > 600 and all(reach(l) <= 600 for l in range(100, cut.iters, 50))
+    assert all(h[l - 1] <= 0.9 * h[l - 51] for l in range(100, cut.iters + 1, 50))   # not the ratio rule
+    late = F.iterate(inst, lin, F.FullADMMOptions(**base, stall_budget=1e-9))
+    assert late.iters == 600 and late.history == full.history
+
+
 def test_warm_start_fallback_runs_the_cold_solve():
     """A warm start on an infeasible linearization stalls; the fallback then equals the cold solve
     with the full budget.  On a feasible problem, a warm start at the solution's (k_v, p̃, λ_p)
