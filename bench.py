@@ -265,17 +265,13 @@ def clocks_summary(path, dev_index):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) over algorithmic bytes of one
-# k_fulladmm launch per dynamics kind (0 unicycle, 1 quadcopter), from a full capture of 148 mixed
-# instances.  The launch at the benchmark size is scaled from it by its algorithmic bytes (traffic
-# grows with row entries x iterations).  Valid only for the kernel sources it was measured on: any
-# change to them makes the reported traffic null until it is measured again.
-# DRAM traffic of k_fulladmm per algorithmic byte (survey count), from the full ncu capture of the
-# 148-instance case (dram__bytes_read.sum + dram__bytes_write.sum over both kinds' launches, 40 iterations
-# each); valid while the kernel sources hash to sources_sha256.
-TRAFFIC = {"sources_sha256": "7780f1d5f90f4bf3e5424e3a385d42d4d3245bbaed454a22eb303490d3ccc48e",
-           "ratio": {"both": 1.020, "quadcopter": 1.095, "unicycle": 0.861},
-           "capture": "ncu --set full, batched_mix(148), one 40-iteration launch per kind"}
+# DRAM traffic of k_fulladmm per algorithmic byte (survey count), from an ncu capture of the
+# 148-instance case (dram__bytes_read.sum + dram__bytes_write.sum of both kinds' launches, 40
+# iterations each).  A launch at the benchmark size is scaled from it by its algorithmic bytes
+# (traffic grows with row entries x iterations).  Valid only while the kernel sources hash to
+# sources_sha256: any change to them makes the reported traffic null until it is measured again.
+TRAFFIC = {"sources_sha256": "ec54c81340f59e113f8cb4f168452863893e7939b8bb29888ab959e3935cd212",
+           "ratio": {"both": 1.017, "quadcopter": 1.095, "unicycle": 0.851}}
 KERNEL_SOURCES = ["fulladmm.cuh", "nrto_dev.cuh", "tma.cuh", "linearize.cuh", "dynamics.cuh"]
 
 
