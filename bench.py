@@ -266,7 +266,7 @@ def clocks_summary(path, dev_index):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM traffic of k_fulladmm per algorithmic byte (survey count), from an ncu capture of the
+# DRAM traffic of k_fulladmm per algorithmic byte ((3 S + 2 C) w), from an ncu capture of the
 # 148-instance case (dram__bytes_read.sum + dram__bytes_write.sum of both kinds' launches, 40
 # iterations each).  A launch at the benchmark size is scaled from it by its algorithmic bytes
 # (traffic grows with row entries x iterations).  Valid only while the kernel sources hash to
