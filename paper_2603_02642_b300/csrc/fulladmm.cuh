@@ -929,6 +929,42 @@ __device__ __forceinline__ void st_vec(Real* p, const Real (&v)[N]) {
   }
 }
 
+// Two FP32 values in one 64-bit register pair, and the paired FP32 arithmetic of sm_100-family
+// GPUs (PTX .f32x2) on them: each half is rounded as the scalar instruction would round it.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p f2_pack(float a, float b) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2p v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2p f2_fma(f2p a, f2p b, f2p c) {
+  f2p d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2p f2_add(f2p a, f2p b) {
+  f2p d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p f2_sub(f2p a, f2p b) {
+  f2p d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p f2_mul(f2p a, f2p b) {
+  f2p d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p f2_neg(f2p a) { return a ^ 0x8000000080000000ull; }
+// 8-byte shared-memory load / store of a pair (8-byte aligned by the chunk layout when W = 2)
+__device__ __forceinline__ f2p f2_ld(const float* p) { return *reinterpret_cast<const f2p*>(p); }
+__device__ __forceinline__ void f2_st(float* p, f2p v) { *reinterpret_cast<f2p*>(p) = v; }
+
 // Global store of N consecutive values with an L2 cache policy (the λ stream of the row pass is
 // written once per pass and marked first to evict).
 template <int N, typename Real>
@@ -949,6 +985,10 @@ __device__ __forceinline__ void st_vec_stream(Real* p, const Real (&v)[N], uint6
     for (int i = 0; i < N; ++i)
       asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p + i), "d"((double)v[i]), "l"(pol) : "memory");
   }
+}
+
+__device__ __forceinline__ void f2_st_stream(float* p, f2p v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
 }
 
 // Phase timer: thread 0 accumulates the SM cycles between consecutive marks (taken right after block
@@ -1003,6 +1043,19 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
   Real gc[PAIRS][NU][W], go[PAIRS][NU][W], z[PAIRS][NU][W];
   load_gt_regs<NX, NU, Real, PAIRS, W>(gtc, T, mk, ck, gc);
   load_gt_regs<NX, NU, Real, PAIRS, W>(gto, T, mk, ck, go);
+  // FP32 with two components per thread: sub-pass 1 runs on component pairs (paired FP32 ops), the
+  // gain tables packed once per pass
+  constexpr bool PK = sizeof(Real) == 4 && W == 2 && !C::EM;
+  [[maybe_unused]] f2p gcp[PAIRS][NU], gop[PAIRS][NU];
+  if constexpr (PK) {
+#pragma unroll
+    for (int k = 0; k < PAIRS; ++k)
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        gcp[k][u] = f2_pack(gc[k][u][0], gc[k][u][1]);
+        gop[k][u] = f2_pack(go[k][u][0], go[k][u][1]);
+      }
+  }
 #pragma unroll
   for (int k = 0; k < PAIRS; ++k)
 #pragma unroll
@@ -1134,6 +1187,44 @@ __device__ __forceinline__ bool fa_row_pass(const Dev<Real>& D, const LinSlot<Re
               const int e = rm.off + mk[k] * NX + ck;
               Real bv[NU], yb[W], l[W], lg[W];
               ld_vec<NU, Real>(bf.bb + rm.boff + mk[k] * NU, bv);
+              if constexpr (PK) {
+                // the scalar steps below on the pair (components ck, ck+1); the norm and residual
+                // sums stay scalar, in the same order
+                const f2p yb2 = f2_ld(bf.bhat + e);
+                f2p l2 = f2_ld(bf.lam + e);
+                f2p bd[NU];
+  #pragma unroll
+                for (int u = 0; u < NU; ++u) bd[u] = f2_pack(bv[u], bv[u]);
+                f2p y2 = yb2;
+  #pragma unroll
+                for (int u = 0; u < NU; ++u) y2 = f2_fma(gcp[k][u], bd[u], y2);
+                if (!first) {
+                  f2p yo2 = yb2;
+  #pragma unroll
+                  for (int u = 0; u < NU; ++u) yo2 = f2_fma(gop[k][u], bd[u], yo2);
+                  const f2p nu2 = f2_mul(f2_pack(so, so), f2_add(yo2, l2));
+                  const f2p ln2 = f2_sub(f2_add(l2, y2), nu2);
+                  float d0, d1, e0, e1;
+                  f2_unpack(f2_sub(y2, nu2), d0, d1);
+                  f2_unpack(f2_sub(y2, yo2), e0, e1);
+                  arp = fmaf(d0, d0, arp);
+                  arp = fmaf(d1, d1, arp);
+                  ard = fmaf(e0, e0, ard);
+                  ard = fmaf(e1, e1, ard);
+                  l2 = f2_mul(ln2, f2_pack(lscale, lscale));
+                  f2_st_stream(lam + cki.e0 + e, l2, spol);
+                }
+                const f2p et2 = f2_add(y2, l2);
+                float t0, t1;
+                f2_unpack(et2, t0, t1);
+                pn = fmaf(t0, t0, pn);
+                pn = fmaf(t1, t1, pn);
+                if (block1) {
+                  f2_st(bf.lam + e, et2);               // η̂, kept for sub-pass 2
+                  f2_st(bf.bhat + e, f2_add(yb2, l2));  // b̂ + λ, kept for sub-pass 2
+                }
+                continue;
+              }
               ld_vec<W, Real>(bf.bhat + e, yb);
               ld_vec<W, Real>(bf.lam + e, l);
   #pragma unroll
