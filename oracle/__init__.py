@@ -16,6 +16,8 @@ Modules (each function cites the passage of the paper it follows):
              (Sec. II-B, Sec. III, Supplementary Sec. II)
   outer      successive-linearization outer loop (Fig. 1, Problem 2)
   mlp        FP64 reference MLP forward/backward for the learned warm start
+  montecarlo robust-constraint satisfaction under sampled interior and edge disturbances
+             (Sec. V, Methodology), SplitMix64 counter-based random numbers
 
 Parity status: every function here is pinned by `tests/test_oracle_*.py` against
 closed forms, invariants, brute force or an independent solver.  The outer loop
