@@ -59,6 +59,9 @@ def test_invalid_descriptors_rejected_on_host():
     inst = W.unicycle(0, T=300)               # horizon beyond the model's limit
     with pytest.raises(nrto.NrtoError):
         nrto.Problem([inst])
+    with pytest.raises(nrto.NrtoError) as e:   # an empty batch
+        nrto.Problem([])
+    assert e.value.code == 1
 
 
 @pytest.mark.skipif(_has_gpu(), reason="checks the no-device error path")
