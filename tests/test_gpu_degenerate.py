@@ -1,12 +1,13 @@
 """GPU parity on the degenerate and extreme inputs the library accepts: an instance with no state
 rows (no obstacles and no state bounds, so the row pass has no chunks and only control rows carry
 cones), the shortest horizon T = 1, the longest horizon of the unicycle and the quadcopter kernels,
-and batches that mix such instances with ordinary ones.  FP64 at fixed iteration counts, with the
-tolerances of the other parity tests; batches bitwise equal to single-instance solves."""
+and batches that mix such instances with ordinary ones.  FullADMM and NRTO-DR inner solves and the
+outer loop, FP64, with the tolerances of the other parity tests; batches bitwise equal to
+single-instance solves."""
 import numpy as np
 import pytest
 
-from oracle import fulladmm as F, problem as P
+from oracle import dr as DRO, fulladmm as F, outer as O, problem as P
 from paper_2603_02642_b300 import nrto, workloads as W
 
 from .gpu_common import RTOL64, assert_close, ragged_from_dense
@@ -70,3 +71,45 @@ def test_batch_with_degenerate_members_equals_single_instances(prec):
         assert np.array_equal(ob["p"][i], os_["p"][0])
         single.close()
     batch.close()
+
+
+DEGENERATE = ["quad_T10_no_state_rows", "uni_T1"]
+
+
+@pytest.mark.parametrize("name", DEGENERATE)
+def test_degenerate_dr_iterates_parity_fp64(name):
+    inst = CASES[name]()
+    n_admm, n_dr, r = 2, 3, 0.5
+    lin = P.linearize(inst, inst.u_init)
+    o = DRO.DROptions(rho=40.0, alpha=0.9, r_chi=1.0, sigma=1.0, r_trust=r, max_admm=n_admm, max_dr=n_dr)
+    res = DRO.solve(inst, lin, o, n_admm=n_admm, n_dr=n_dr, check=False)
+    prob = nrto.Problem([inst], nrto.PREC_FP64)
+    prob.linearize()
+    prob.set_trust_radius(r)
+    out = prob.solve_socp(nrto.Options(solver=nrto.SOLVER_DR, rho=40.0, alpha=0.9, r_chi=1.0, sigma=1.0,
+                                       max_inner=n_admm, max_dr=n_dr, check=0))
+    assert out["iters"][0] == n_admm
+    assert_close(out["K"][0], res.K, RTOL64, "K")
+    assert_close(out["du"][0], res.du, RTOL64, "du")
+    assert_close(out["p"][0], res.p, RTOL64, "p")
+    assert_close(out["pt"][0], res.pt, RTOL64, "p~")
+    assert_close(prob.export(nrto.F_LAMP, 0), res.lam, RTOL64, "lambda")
+    assert_close(prob.export(nrto.F_DX, 0), res.dx, RTOL64, "dx")
+    assert_close(prob.export(nrto.F_LAMNU, 0), ragged_from_dense(lin, res.dr_state.etat), RTOL64, "eta~")
+    prob.close()
+
+
+@pytest.mark.parametrize("name", DEGENERATE)
+def test_degenerate_outer_loop_parity_fp64(name):
+    inst = CASES[name]()
+    res = O.solve(inst, O.OuterOptions(n_outer=3, r0=2.0, r_min=1e-3, w_p=10.0),
+                  admm=F.FullADMMOptions(rho=10.0, max_iter=40, eps_p=1e-4, eps_d=1e-4))
+    prob = nrto.Problem([inst], nrto.PREC_FP64)
+    out = prob.solve(nrto.Options(rho=10.0, max_inner=40, eps_p=1e-4, eps_d=1e-4, check=1, r0=2.0, r_min=1e-3,
+                                  w_p=10.0), n_outer=3)
+    st = prob.export(nrto.F_STATS, 0)
+    assert st[3] == sum(res.accepted)
+    assert_close(out["u_bar"][0], res.u_bar, RTOL64, "u_bar")
+    assert_close(out["K"][0], res.K, RTOL64, "K")
+    assert abs(out["merit"][0] - res.phi) <= RTOL64 * abs(res.phi)
+    prob.close()
