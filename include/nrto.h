@@ -362,6 +362,17 @@ nrto_status nrto_phase_cycles(nrto_problem_t p, long long* cycles, int n);
 /* Number of kernel launches the library issued since create (all of its own kernels). */
 long long nrto_kernel_launches(nrto_problem_t p);
 
+/* Self-test of the device-side watchdog (the paper has no counterpart: it describes no failure
+ * handling).  Every solver kernel waits for its bulk copies with a wait bounded by 2^32 SM cycles,
+ * about two seconds, after which the instance ends with per-instance status 4 instead of hanging.
+ * This call runs that wait on the current device against a barrier that nothing completes:
+ * *status_out receives 4 when the wait gave up as designed (1 would mean the barrier completed),
+ * *cycles_out (optional, may be NULL) the SM cycles waited.  It blocks for those two seconds,
+ * allocates and frees 16 bytes of device memory, and leaves the device usable.  stream: a
+ * cudaStream_t or NULL (legacy default stream).  NRTO_ERR_INVALID for a NULL status_out,
+ * NRTO_ERR_CUDA for a CUDA failure. */
+nrto_status nrto_selftest_bounded_wait(void* stream, int* status_out, long long* cycles_out);
+
 /* ---- Learned warm start: a GELU multilayer perceptron (the paper names learning a warm start
  * for the inner solver as future work and fixes no network; this is the library's own).
  * z_l = h_{l-1} W_lᵀ + b_l, h_l = gelu(z_l) = z_l Φ(z_l) for hidden layers, y = z_L.  Trained on the

@@ -116,6 +116,21 @@ __global__ void k_gather_field(const Inst* inst, const int* is, const double* ar
   for (long long q = threadIdx.x; q < cnt; q += blockDim.x) out[out_off[i] + q] = src[q];
 }
 
+// Self-test of the bounded wait that guards every bulk copy of the solver kernels: one thread waits
+// on an mbarrier that nothing arrives on.  The wait gives up after its cycle limit and the kernel
+// records status 4 (the per-instance status of a copy that did not arrive) and the cycles waited.
+__global__ void k_selftest_wait(long long* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    const long long t0 = clock64();
+    const bool arrived = mbar_wait_bounded(&bar, 0);
+    out[0] = arrived ? 1 : 4;
+    out[1] = clock64() - t0;
+  }
+}
+
 template <typename Real>
 __global__ void k_candidate(Dev<Real> D) {
   const int i = blockIdx.x;
@@ -1769,6 +1784,28 @@ nrto_status nrto_phase_cycles(nrto_problem_t p, long long* cycles, int n) {
 }
 
 long long nrto_kernel_launches(nrto_problem_t p) { return p ? p->launches : -1; }
+
+nrto_status nrto_selftest_bounded_wait(void* stream, int* status_out, long long* cycles_out) {
+  long long* d = nullptr;
+  try {
+    if (!status_out) fail(NRTO_ERR_INVALID, "status_out is required");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaMalloc(&d, 2 * sizeof(long long)));
+    k_selftest_wait<<<1, 32, 0, s>>>(d);
+    CK(cudaGetLastError());
+    long long h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaFree(d));
+    d = nullptr;
+    *status_out = (int)h[0];
+    if (cycles_out) *cycles_out = h[1];
+    return NRTO_OK;
+  } catch (const std::exception& e) {
+    if (d) cudaFree(d);
+    return handle(e);
+  }
+}
 
 }  // extern "C"
 

@@ -126,6 +126,8 @@ def load():
     lib.nrto_monte_carlo.restype = C.c_int
     lib.nrto_kernel_launches.argtypes = [P]
     lib.nrto_kernel_launches.restype = C.c_longlong
+    lib.nrto_selftest_bounded_wait.argtypes = [C.c_void_p, _ip, C.POINTER(C.c_longlong)]
+    lib.nrto_selftest_bounded_wait.restype = C.c_int
     lib.nrto_last_error.restype = C.c_char_p
     for name in ["nrto_problem_create", "nrto_problem_destroy", "nrto_problem_info", "nrto_problem_update",
                  "nrto_linearize", "nrto_set_trust_radius", "nrto_solve_socp", "nrto_outer_step", "nrto_solve",
@@ -443,6 +445,15 @@ def solve_noalloc(instances, opts: Options, n_outer=10, precision=PREC_FP64, str
         a += x.T * x.nu
         b += x.T * x.nu * x.nx
     return dict(u_bar=us, K=Ks, merit=m)
+
+
+def selftest_bounded_wait(stream=None):
+    """Run the solver kernels' bounded copy wait against a barrier that never completes
+    (nrto_selftest_bounded_wait): (status, SM cycles waited); status 4 means the wait gave up."""
+    st = C.c_int(0)
+    cyc = C.c_longlong(0)
+    _check(load().nrto_selftest_bounded_wait(C.c_void_p(stream), C.byref(st), C.byref(cyc)))
+    return st.value, cyc.value
 
 
 def _f32(a):
