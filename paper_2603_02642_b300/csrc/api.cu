@@ -17,6 +17,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/nrto.h"
 #include "fulladmm.cuh"
 #include "montecarlo.cuh"
@@ -41,6 +43,15 @@ struct NrtoError : std::runtime_error {
   } while (0)
 
 void fail(nrto_status s, const std::string& m) { throw NrtoError(s, m); }
+
+// NVTX range over one call of the C ABI (a profiler's timeline shows the host side of each call;
+// without a profiler attached the calls do nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int kind_nx(int k) { return k == KIND_UNICYCLE ? 3 : (k == KIND_QUADCOPTER ? 12 : 14); }
 int kind_nu(int k) { return k == KIND_UNICYCLE ? 2 : (k == KIND_QUADCOPTER ? 4 : 7); }
@@ -1262,6 +1273,7 @@ extern "C" {
 
 nrto_status nrto_problem_create(const nrto_problem_desc* descs, int n, int precision, void* stream,
                                 nrto_problem_t* out) {
+  NvtxRange nvtx_("nrto_problem_create");
   return create_problem(descs, n, precision, stream, nullptr, 0, out);
 }
 
@@ -1311,6 +1323,7 @@ nrto_status nrto_problem_update(nrto_problem_t p, const nrto_problem_desc* descs
 
 nrto_status nrto_linearize(nrto_problem_t p, const double* u_hat) {
   try {
+    NvtxRange nvtx_("nrto_linearize");
     if (!p) fail(NRTO_ERR_INVALID, "null problem");
     if (u_hat) {
       if (!finite_arr(u_hat, p->u_total)) fail(NRTO_ERR_NUMERIC, "u_hat not finite");
@@ -1354,6 +1367,7 @@ nrto_status nrto_set_trust_radius(nrto_problem_t p, const double* r) {
 
 nrto_status nrto_solve_socp(nrto_problem_t p, const nrto_solver_opts* o, nrto_socp_out* out) {
   try {
+    NvtxRange nvtx_("nrto_solve_socp");
     if (!p) fail(NRTO_ERR_INVALID, "null problem");
     check_opts(o);
     if (!p->linearized) fail(NRTO_ERR_STATE, "nrto_linearize must be called before nrto_solve_socp");
@@ -1367,6 +1381,7 @@ nrto_status nrto_solve_socp(nrto_problem_t p, const nrto_solver_opts* o, nrto_so
 
 nrto_status nrto_outer_step(nrto_problem_t p, const nrto_solver_opts* o, int* accepted) {
   try {
+    NvtxRange nvtx_("nrto_outer_step");
     if (!p) fail(NRTO_ERR_INVALID, "null problem");
     check_opts(o);
     if (!p->linearized) fail(NRTO_ERR_STATE, "nrto_linearize must be called before nrto_outer_step");
@@ -1386,6 +1401,7 @@ nrto_status nrto_outer_step(nrto_problem_t p, const nrto_solver_opts* o, int* ac
 nrto_status nrto_solve(nrto_problem_t p, const nrto_solver_opts* o, int n_outer, double* u_bar, double* K,
                        double* merit) {
   try {
+    NvtxRange nvtx_("nrto_solve");
     if (!p) fail(NRTO_ERR_INVALID, "null problem");
     check_opts(o);
     if (n_outer < 0) fail(NRTO_ERR_INVALID, "n_outer < 0");
@@ -1598,6 +1614,7 @@ nrto_status nrto_set_warm_start_lifted(nrto_problem_t p, const double* theta, co
 
 nrto_status nrto_monte_carlo(nrto_problem_t p, const double* K, int n_interior, int n_edge, unsigned long long seed,
                              double tol, int* n_ok, double* worst) {
+  NvtxRange nvtx_("nrto_monte_carlo");
   double* dK = nullptr;
   double* dw = nullptr;
   int* dok = nullptr;
@@ -1700,6 +1717,7 @@ nrto_status nrto_set_launch_mapping(nrto_problem_t p, int mapping) {
 nrto_status nrto_autotune(nrto_problem_t p, const nrto_solver_opts* o, int n_outer, int reps, double* ms_out,
                           int* chosen) {
   try {
+    NvtxRange nvtx_("nrto_autotune");
     if (!p) fail(NRTO_ERR_INVALID, "null problem");
     check_opts(o);
     if (n_outer < 1 || reps < 1) fail(NRTO_ERR_INVALID, "n_outer and reps must be >= 1");
